@@ -1,0 +1,372 @@
+"""FP64 CPU oracle for the Fourier-spectral multiple-scattering method.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports, links or
+executes this module: only the test suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It shares
+no code with the CUDA path: Bessel and Hankel values come from SciPy (AMOS),
+blocks are assembled densely from their printed definitions, systems are
+solved by LAPACK LU or by a plain restarted GMRES written here.
+
+Every function cites the part of the paper (mu-diff, arXiv 1409.8186) it
+restates.  Notation: disks p = 1..M with centre O_p, radius a_p; Fourier modes
+m = -N..N on every disk (n = 2N+1 per disk); b_pq = O_p - O_q is the vector
+from O_q to O_p and alpha_pq its polar angle (section 4.1); time dependence
+exp(-i omega t) and first-kind Hankel functions (section 2).
+
+Readings of the paper taken here:
+  * the Galerkin test uses the hermitian product (section 4.1), so the
+    right-hand side of row (p, m) is (u_inc, Phi^p_m) and the system is
+    A rho = -U (section 5);
+  * the angle alpha_pq of the separation matrix is the polar angle of
+    b_pq = O_p - O_q (the printed subscript "alpha_bq" is read as alpha_pq);
+  * sound-hard disks use the same single-layer representation u = L rho and
+    the exterior normal trace (-I/2 + N) rho = -d_n u_inc (jump relations of
+    Prop. 3.2), with the diagonal block (i pi k a_p / 2) J^p H'^p;
+  * the single-scattering preconditioner is P = block diagonal part of A
+    (section 5), applied on the left; GMRES starts from x0 = 0 and measures
+    relres = ||P^-1 (b - A x)|| / ||P^-1 b||;
+  * far field: the single-layer coefficient vector of section 4.4 (the a_L
+    formula); a_M is not used.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy import special
+
+DIRICHLET = 0
+NEUMANN = 1
+
+
+# --------------------------------------------------------------------------
+# Section 4.2: Bessel diagonals and the separation matrix
+# --------------------------------------------------------------------------
+
+def modes(N: int) -> np.ndarray:
+    """Fourier indices m = -N..N kept on a disk after truncation (section 5)."""
+    return np.arange(-N, N + 1)
+
+
+def bessel_diagonals(a, k: float, N: int):
+    """Section 4.2: the diagonal matrices J^p, J'^p, H^p, H'^p with entries
+    J_m(k a_p), J_m'(k a_p), H^(1)_m(k a_p), H^(1)_m'(k a_p), m = -N..N.
+    Returns four [M, 2N+1] arrays."""
+    a = np.atleast_1d(np.asarray(a, dtype=np.float64))
+    m = modes(N)[None, :]
+    x = k * a[:, None]
+    return (special.jv(m, x), special.jvp(m, x), special.hankel1(m, x),
+            special.h1vp(m, x))
+
+
+def pair_vector(Op, Oq):
+    """Section 4.1: b_pq = O_p - O_q (vector from O_q to O_p), its length and
+    its polar angle alpha_pq."""
+    v = np.asarray(Op, dtype=np.float64) - np.asarray(Oq, dtype=np.float64)
+    return v, float(np.hypot(v[0], v[1])), float(np.arctan2(v[1], v[0]))
+
+
+def separation_matrix(Op, Oq, k: float, N: int) -> np.ndarray:
+    """Section 4.2: S^pq_mn = H^(1)_{m-n}(k b_pq) exp(i (m-n) alpha_pq),
+    m, n = -N..N."""
+    _, b, alpha = pair_vector(Op, Oq)
+    m = modes(N)
+    d = m[:, None] - m[None, :]
+    return special.hankel1(d, k * b) * np.exp(1j * d * alpha)
+
+
+# --------------------------------------------------------------------------
+# Section 4.2 / section 5: the truncated operator blocks
+# --------------------------------------------------------------------------
+
+def block_L(O, a, k, N, p, q) -> np.ndarray:
+    """Section 4.2, single-layer block L^pq: (i pi a_p / 2) J^p H^p on the
+    diagonal, (i pi sqrt(a_p a_q) / 2) J^p (S^pq)^T J^q off it."""
+    J, _, H, _ = bessel_diagonals(a, k, N)
+    if p == q:
+        return np.diag(0.5j * np.pi * a[p] * J[p] * H[p])
+    S = separation_matrix(O[p], O[q], k, N)
+    return 0.5j * np.pi * np.sqrt(a[p] * a[q]) * (J[p][:, None] * S.T * J[q][None, :])
+
+
+def block_N(O, a, k, N, p, q) -> np.ndarray:
+    """Section 4.2, block N^pq of the normal-derivative trace of the
+    single-layer potential: I/2 + (i pi k a_p / 2) J^p H'^p on the diagonal,
+    (i k pi sqrt(a_p a_q) / 2) J'^p (S^pq)^T J^q off it."""
+    J, dJ, H, dH = bessel_diagonals(a, k, N)
+    if p == q:
+        return 0.5 * np.eye(2 * N + 1) + np.diag(0.5j * np.pi * k * a[p] * J[p] * dH[p])
+    S = separation_matrix(O[p], O[q], k, N)
+    return 0.5j * k * np.pi * np.sqrt(a[p] * a[q]) * (dJ[p][:, None] * S.T * J[q][None, :])
+
+
+def assemble(O, a, bc, k, N) -> np.ndarray:
+    """Section 5: the N_tot x N_tot block matrix.  Dirichlet rows p carry
+    the EFIE blocks L^pq; Neumann rows carry (-I/2 + N)^pq, the exterior
+    normal trace of the single-layer potential (Prop. 3.2)."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    A = np.zeros((M * n, M * n), dtype=np.complex128)
+    for p in range(M):
+        for q in range(M):
+            if bc[p] == DIRICHLET:
+                B = block_L(O, a, k, N, p, q)
+            else:
+                B = block_N(O, a, k, N, p, q)
+                if p == q:
+                    B = B - 0.5 * np.eye(n)
+            A[p * n:(p + 1) * n, q * n:(q + 1) * n] = B
+    return A
+
+
+# --------------------------------------------------------------------------
+# Prop. 4.1: plane-wave right-hand sides
+# --------------------------------------------------------------------------
+
+def planewave_coefficients(O, a, k, N, beta) -> np.ndarray:
+    """Prop. 4.1: d^p_m = sqrt(2 pi a_p) exp(i k beta_hat . b_p)
+    exp(i m (pi/2 - beta)), with b_p = O_p.  Returns [M, 2N+1]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    m = modes(N)[None, :]
+    phase = k * (np.cos(beta) * O[:, 0] + np.sin(beta) * O[:, 1])
+    return (np.sqrt(2 * np.pi * a)[:, None] * np.exp(1j * phase)[:, None]
+            * np.exp(1j * m * (np.pi / 2 - beta)))
+
+
+def rhs_planewave(O, a, bc, k, N, betas) -> np.ndarray:
+    """Prop. 4.1 and section 5: the right-hand side b = -U of A rho = b.
+    Dirichlet rows: U^p_m = d^p_m J_m(k a_p); Neumann rows:
+    dU^p_m = k d^p_m J_m'(k a_p).  Returns [N_tot, R] (one column per
+    incidence angle)."""
+    betas = np.atleast_1d(np.asarray(betas, dtype=np.float64))
+    J, dJ, _, _ = bessel_diagonals(a, k, N)
+    cols = []
+    for beta in betas:
+        d = planewave_coefficients(O, a, k, N, beta)
+        U = np.where(np.asarray(bc)[:, None] == DIRICHLET, d * J, k * d * dJ)
+        cols.append(-U.reshape(-1))
+    return np.stack(cols, axis=1)
+
+
+# --------------------------------------------------------------------------
+# Section 5: single-scattering preconditioner, direct and Krylov solves
+# --------------------------------------------------------------------------
+
+def diagonal_of_blocks(A, M, n) -> np.ndarray:
+    """The diagonal blocks A^pp are diagonal matrices (section 4.2); this
+    returns their diagonals as one vector of length N_tot."""
+    return np.diag(A).copy()
+
+
+def precondition(A, b, M, n):
+    """Section 5: left single-scattering preconditioning P^-1 A, P^-1 b with
+    P the block-diagonal part of A (here a plain diagonal)."""
+    P = diagonal_of_blocks(A, M, n)
+    return A / P[:, None], b / P[:, None] if b.ndim == 2 else b / P
+
+
+def solve_lu(A, b) -> np.ndarray:
+    """Section 5: direct solve by LU (LAPACK via numpy)."""
+    return np.linalg.solve(A, b)
+
+
+def gmres(matvec, b, restart=50, tol=1e-10, maxit=1000):
+    """Restarted GMRES(restart) for one right-hand side, as used in section 6.2
+    (x0 = 0).  Arnoldi with modified Gram-Schmidt, Givens rotations on the
+    Hessenberg matrix, least-squares update at the end of each cycle.
+    Returns x, flag (0 converged, 1 not), relres, total iterations, residual
+    history (relative)."""
+    b = np.asarray(b, dtype=np.complex128)
+    nb = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if nb == 0.0:
+        return x, 0, 0.0, 0, [0.0]
+    resvec = [1.0]
+    total = 0
+    while total < maxit:
+        r = b - matvec(x)
+        beta = np.linalg.norm(r)
+        if beta / nb <= tol:
+            return x, 0, beta / nb, total, resvec
+        m = restart
+        V = np.zeros((len(b), m + 1), dtype=np.complex128)
+        Hs = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m, dtype=np.complex128)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        V[:, 0] = r / beta
+        j_used = 0
+        for j in range(m):
+            w = matvec(V[:, j])
+            for i in range(j + 1):
+                Hs[i, j] = np.vdot(V[:, i], w)
+                w = w - Hs[i, j] * V[:, i]
+            Hs[j + 1, j] = np.linalg.norm(w)
+            if Hs[j + 1, j] != 0:
+                V[:, j + 1] = w / Hs[j + 1, j]
+            for i in range(j):
+                t = cs[i] * Hs[i, j] + sn[i] * Hs[i + 1, j]
+                Hs[i + 1, j] = -np.conj(sn[i]) * Hs[i, j] + np.conj(cs[i]) * Hs[i + 1, j]
+                Hs[i, j] = t
+            den = np.hypot(abs(Hs[j, j]), abs(Hs[j + 1, j]))
+            if den == 0:
+                cs[j], sn[j] = 1.0, 0.0
+            elif abs(Hs[j, j]) == 0:
+                cs[j], sn[j] = 0.0, np.conj(Hs[j + 1, j]) / abs(Hs[j + 1, j])
+            else:
+                ph = Hs[j, j] / abs(Hs[j, j])
+                cs[j] = abs(Hs[j, j]) / den
+                sn[j] = ph * np.conj(Hs[j + 1, j]) / den
+            Hs[j, j] = cs[j] * Hs[j, j] + sn[j] * Hs[j + 1, j]
+            Hs[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            total += 1
+            j_used = j + 1
+            resvec.append(abs(g[j + 1]) / nb)
+            if abs(g[j + 1]) / nb <= tol or total >= maxit:
+                break
+        y = np.linalg.solve(np.triu(Hs[:j_used, :j_used]), g[:j_used])
+        x = x + V[:, :j_used] @ y
+    r = b - matvec(x)
+    relres = np.linalg.norm(r) / nb
+    return x, (0 if relres <= tol else 1), relres, total, resvec
+
+
+def solve(cluster_O, a, bc, k, N, betas, method="lu", **gm):
+    """Assemble, precondition and solve for every incidence angle.
+    Returns rho [N_tot, R] and a dict of per-column solver statistics."""
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    A = assemble(cluster_O, a, bc, k, N)
+    b = rhs_planewave(cluster_O, a, bc, k, N, betas)
+    Ap, bp = precondition(A, b, M, n)
+    if method == "lu":
+        return solve_lu(Ap, bp), {}
+    cols, stats = [], []
+    for r in range(b.shape[1]):
+        x, flag, relres, it, rv = gmres(lambda v: Ap @ v, bp[:, r], **gm)
+        cols.append(x)
+        stats.append(dict(flag=flag, relres=relres, iters=it, resvec=rv))
+    return np.stack(cols, axis=1), stats
+
+
+# --------------------------------------------------------------------------
+# Matrix-free application of the preconditioned operator to selected rows
+# (for clusters whose dense matrix does not fit in host memory)
+# --------------------------------------------------------------------------
+
+def preconditioned_rows(O, a, bc, k, N, x, targets) -> np.ndarray:
+    """Rows p in `targets` of (P^-1 A) x, built block by block from the
+    section 4.2 definitions: y^p = x^p + (A^pp)^-1 sum_{q != p} A^pq x^q.
+    x is [N_tot, R]; returns [len(targets), 2N+1, R]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    X = np.asarray(x).reshape(M, n, -1)
+    J, dJ, H, dH = bessel_diagonals(a, k, N)
+    m = modes(N)
+    dmn = m[None, :] - m[:, None]          # n - m for entry (m, n) of (S^pq)^T
+    out = []
+    for p in targets:
+        qs = np.array([q for q in range(M) if q != p])
+        bv = O[p][None, :] - O[qs]
+        b = np.hypot(bv[:, 0], bv[:, 1])
+        al = np.arctan2(bv[:, 1], bv[:, 0])
+        # (S^pq)^T_mn = S^pq_nm = H_{n-m}(k b) exp(i (n-m) alpha)
+        ST = special.hankel1(dmn[None], k * b[:, None, None]) * np.exp(1j * dmn[None] * al[:, None, None])
+        coef = 0.5j * np.pi * np.sqrt(a[p] * a[qs])
+        if bc[p] == DIRICHLET:
+            left = J[p]
+            diag = 0.5j * np.pi * a[p] * J[p] * H[p]
+        else:
+            left = k * dJ[p]
+            diag = 0.5j * np.pi * k * a[p] * J[p] * dH[p]
+        blocks = coef[:, None, None] * left[None, :, None] * ST * J[qs][:, None, :]
+        acc = np.einsum("qmn,qnr->mr", blocks, X[qs])
+        out.append(X[p] + acc / diag[:, None])
+    return np.stack(out, axis=0)
+
+
+def preconditioned_rhs(O, a, bc, k, N, betas) -> np.ndarray:
+    """P^-1 b with P the diagonal of the blocks A^pp (section 5)."""
+    a = np.asarray(a, dtype=np.float64)
+    J, dJ, H, dH = bessel_diagonals(a, k, N)
+    diag = np.where(np.asarray(bc)[:, None] == DIRICHLET,
+                    0.5j * np.pi * a[:, None] * J * H,
+                    0.5j * np.pi * k * a[:, None] * J * dH).reshape(-1)
+    return rhs_planewave(O, a, bc, k, N, betas) / diag[:, None]
+
+
+# --------------------------------------------------------------------------
+# Section 4.4: potentials and far field
+# --------------------------------------------------------------------------
+
+def single_layer_potential(O, a, k, N, rho, points) -> np.ndarray:
+    """Prop. 4.3: (L rho)(x) = sum_p sum_m rho^p_m (i pi a_p / 2) J_m(k a_p)
+    H_m(k r_p(x)) exp(i m theta_p(x)) / sqrt(2 pi a_p), for x outside the
+    disks.  rho is [N_tot] or [N_tot, R]; points [P, 2]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    rho = np.asarray(rho)
+    squeeze = rho.ndim == 1
+    R = rho.reshape(M, n, -1)
+    pts = np.asarray(points, dtype=np.float64)
+    J = bessel_diagonals(a, k, N)[0]
+    m = modes(N)
+    u = np.zeros((len(pts), R.shape[2]), dtype=np.complex128)
+    for p in range(M):
+        d = pts - O[p][None, :]
+        r = np.hypot(d[:, 0], d[:, 1])
+        th = np.arctan2(d[:, 1], d[:, 0])
+        basis = special.hankel1(m[None, :], k * r[:, None]) * np.exp(1j * m[None, :] * th[:, None])
+        coef = 0.5j * np.pi * a[p] * J[p] / np.sqrt(2 * np.pi * a[p])
+        u += basis @ (coef[:, None] * R[p])
+    return u[:, 0] if squeeze else u
+
+
+def farfield_coefficients(O, a, k, N, theta) -> np.ndarray:
+    """Section 4.4: (a_L)^p_m(theta) = i e^{-i pi/4} sqrt(a_p) / (2 sqrt k)
+    exp(-i b_p k cos(theta - alpha_p)) J_m(k a_p) exp(i m (theta - pi/2)),
+    with b_p = |O_p| and alpha_p its polar angle.  Returns [N_tot]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    J = bessel_diagonals(a, k, N)[0]
+    m = modes(N)[None, :]
+    bp = np.hypot(O[:, 0], O[:, 1])
+    alp = np.arctan2(O[:, 1], O[:, 0])
+    c = (1j * np.exp(-1j * np.pi / 4) * np.sqrt(a) / (2 * np.sqrt(k)))[:, None] \
+        * np.exp(-1j * bp * k * np.cos(theta - alp))[:, None] * J * np.exp(1j * m * (theta - np.pi / 2))
+    return c.reshape(-1)
+
+
+def farfield(O, a, k, N, rho, thetas) -> np.ndarray:
+    """Section 4.4: a_L(theta) = (a_L(theta))^T rho for every sample angle.
+    rho [N_tot, R] -> F [T, R]."""
+    rho = np.asarray(rho)
+    if rho.ndim == 1:
+        rho = rho[:, None]
+    C = np.stack([farfield_coefficients(O, a, k, N, t) for t in np.atleast_1d(thetas)])
+    return C @ rho
+
+
+def rcs(F) -> np.ndarray:
+    """Section 4.4: RCS = 10 log10(2 pi |a|^2) in dB."""
+    return 10.0 * np.log10(2 * np.pi * np.abs(F) ** 2)
+
+
+# --------------------------------------------------------------------------
+# Section 5: truncation rule (eq. Np)
+# --------------------------------------------------------------------------
+
+def truncation_order(ka: float, eps: float) -> int:
+    """Eq. (Np): N_p = [k a_p + ((1/(2 sqrt 2)) ln(2 sqrt 2 pi k a_p / eps))^(2/3)
+    (k a_p)^(1/3) + 1], [.] the integer part."""
+    t = (np.log(2 * np.sqrt(2) * np.pi * ka / eps) / (2 * np.sqrt(2))) ** (2.0 / 3.0)
+    return int(np.floor(ka + t * ka ** (1.0 / 3.0) + 1))

@@ -1,0 +1,350 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks it against
+brute-force quadrature of the Galerkin integrals (section 4.2), high-precision
+special-function values, the textbook single-disk (Mie) series, physical
+identities of the far field (energy balance, reciprocity), the boundary
+condition on every circle, the large-r asymptotics of the near field, the
+equivalence of the direct and Krylov solves, spectral convergence in N, and
+translation/rotation covariance.  The last group plants mistakes in the
+oracle and checks that a pin catches each one.
+"""
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle.msd_oracle as O_
+from paper_1409_8186_gb300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ---------------------------------------------------------------- helpers
+
+def circle(Oc, a, Q):
+    t = 2 * np.pi * np.arange(Q) / Q
+    x = Oc[None, :] + a * np.stack([np.cos(t), np.sin(t)], axis=1)
+    return t, x
+
+
+def quadrature_block(Op, ap, Oq, aq, k, N, kind="L", Q=160):
+    """Galerkin entry (K Phi^q_n, Phi^p_m) (hermitian product, section 4.1)
+    by the trapezoidal rule on both circles.  K = L (kernel G) or N (kernel
+    d/dn_x G).  Smooth periodic integrand for p != q: spectral accuracy."""
+    tp, X = circle(Op, ap, Q)
+    tq, Y = circle(Oq, aq, Q)
+    D = X[:, None, :] - Y[None, :, :]
+    r = np.hypot(D[..., 0], D[..., 1])
+    if kind == "L":
+        K = 0.25j * special.hankel1(0, k * r)
+    else:
+        nx = np.stack([np.cos(tp), np.sin(tp)], axis=1)
+        cosang = (D[..., 0] * nx[:, None, 0] + D[..., 1] * nx[:, None, 1]) / r
+        K = -0.25j * k * special.hankel1(1, k * r) * cosang
+    m = np.arange(-N, N + 1)
+    phq = np.exp(1j * np.outer(tq, m)) / np.sqrt(2 * np.pi * aq) * (aq * 2 * np.pi / Q)
+    php = np.exp(1j * np.outer(tp, m)) / np.sqrt(2 * np.pi * ap) * (ap * 2 * np.pi / Q)
+    return php.conj().T @ K @ phq
+
+
+def mie_field(Oc, a, k, beta, pts, hard=False, terms=60):
+    """Textbook series of the field scattered by one disk (plane wave
+    exp(i k beta_hat . x), Jacobi-Anger expansion about the centre)."""
+    d = pts - Oc[None, :]
+    r = np.hypot(d[:, 0], d[:, 1])
+    th = np.arctan2(d[:, 1], d[:, 0])
+    m = np.arange(-terms, terms + 1)
+    ka = k * a
+    ratio = special.jvp(m, ka) / special.h1vp(m, ka) if hard else special.jv(m, ka) / special.hankel1(m, ka)
+    shift = np.exp(1j * k * (np.cos(beta) * Oc[0] + np.sin(beta) * Oc[1]))
+    series = (1j ** m)[None, :] * np.exp(-1j * m * beta)[None, :] * ratio[None, :] \
+        * special.hankel1(m[None, :], k * r[:, None]) * np.exp(1j * m[None, :] * th[:, None])
+    return -shift * series.sum(axis=1)
+
+
+def solve_lu(cl, betas):
+    rho, _ = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas, method="lu")
+    return rho
+
+
+def two_disks():
+    return W.Cluster(np.array([[0.3, -0.2], [-1.9, 1.1]]), np.array([0.7, 0.9]),
+                     np.array([0, 1], np.int8), 1.3, 6, "two")
+
+
+# ---------------------------------------------------------------- Bessel
+
+@pytest.mark.parametrize("x", [0.35, 1.5, 6.28, 31.4, 250.0])
+def test_bessel_diagonals_vs_mpmath(x):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    N = 22
+    k = 1.0
+    J, dJ, H, dH = O_.bessel_diagonals([x], k, N)
+    for i, m in enumerate(range(-N, N + 1)):
+        j = complex(mp.besselj(m, x))
+        y = complex(mp.bessely(m, x))
+        dj = complex(mp.besselj(m, x, derivative=1))
+        dy = complex(mp.bessely(m, x, derivative=1))
+        assert abs(J[0, i] - j) <= 1e-13 * max(1.0, abs(j))
+        assert abs(dJ[0, i] - dj) <= 1e-13 * max(1.0, abs(dj))
+        assert abs(H[0, i] - (j + 1j * y)) <= 1e-12 * abs(j + 1j * y)
+        assert abs(dH[0, i] - (dj + 1j * dy)) <= 1e-12 * abs(dj + 1j * dy)
+
+
+def test_separation_matrix_vs_mpmath():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    Op, Oq, k, N = np.array([1.0, 2.0]), np.array([-0.5, 0.25]), 2.0, 8
+    S = O_.separation_matrix(Op, Oq, k, N)
+    b = np.hypot(1.5, 1.75)
+    al = np.arctan2(1.75, 1.5)
+    for i, m in enumerate(range(-N, N + 1)):
+        for j, n in enumerate(range(-N, N + 1)):
+            ref = complex(mp.hankel1(m - n, k * b) * mp.exp(1j * (m - n) * al))
+            assert abs(S[i, j] - ref) <= 1e-12 * abs(ref)
+
+
+# ---------------------------------------------------------------- blocks
+
+@pytest.mark.parametrize("kind", ["L", "N"])
+def test_offdiagonal_blocks_vs_quadrature(kind):
+    cl = two_disks()
+    O, a, k, N = cl.centres, cl.radii, cl.k, cl.N
+    for p, q in [(0, 1), (1, 0)]:
+        ref = quadrature_block(O[p], a[p], O[q], a[q], k, N, kind)
+        blk = O_.block_L(O, a, k, N, p, q) if kind == "L" else O_.block_N(O, a, k, N, p, q)
+        assert np.abs(blk - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_index_reversal_symmetry():
+    """L^qp_{-n,-m} = L^pq_{mn}: Graf's theorem with b_qp = -b_pq."""
+    cl = two_disks()
+    B01 = O_.block_L(cl.centres, cl.radii, cl.k, cl.N, 0, 1)
+    B10 = O_.block_L(cl.centres, cl.radii, cl.k, cl.N, 1, 0)
+    assert np.abs(B10[::-1, ::-1].T - B01).max() <= 1e-14 * np.abs(B01).max()
+
+
+# ---------------------------------------------------------------- single disk
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_single_disk_matches_mie_series(hard):
+    Oc, a, k, beta, N = np.array([0.7, -0.4]), 1.1, 2.3, 0.6, 30
+    cl = W.Cluster(Oc[None, :], np.array([a]), np.array([1 if hard else 0], np.int8), k, N)
+    rho = solve_lu(cl, [beta])[:, 0]
+    ang = np.linspace(0, 2 * np.pi, 17, endpoint=False)
+    pts = np.concatenate([Oc[None, :] + r * np.stack([np.cos(ang), np.sin(ang)], 1) for r in (1.3, 2.5, 6.0)])
+    u = O_.single_layer_potential(cl.centres, cl.radii, k, N, rho, pts)
+    ref = mie_field(Oc, a, k, beta, pts, hard=hard)
+    assert np.abs(u - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- clusters
+
+def test_boundary_conditions_hold_on_every_circle():
+    # five sound-hard disks with gaps down to 0.31: N = 30 resolves the
+    # closest pair to ~1e-8 (the residual decays spectrally in N)
+    cl = W.small_mixed(seed=11, M=5, N=30, k=2.3)
+    cl.bc[[0, 4]] = W.DIRICHLET
+    beta = 0.7
+    rho = solve_lu(cl, [beta])[:, 0]
+    t = np.linspace(0, 2 * np.pi, 40, endpoint=False)
+    nrm = np.stack([np.cos(t), np.sin(t)], 1)
+
+    def utot(x):
+        return np.exp(1j * cl.k * (np.cos(beta) * x[:, 0] + np.sin(beta) * x[:, 1])) + \
+            O_.single_layer_potential(cl.centres, cl.radii, cl.k, cl.N, rho, x)
+
+    h = 2e-4
+    for s in range(cl.M):
+        x = cl.centres[s][None, :] + cl.radii[s] * nrm
+        if cl.bc[s] == W.DIRICHLET:
+            res = np.abs(utot(x)).max()
+            assert res < 1e-9, (s, res)
+        else:
+            # one-sided (exterior) 4th-order difference: the normal derivative of
+            # the single-layer potential jumps across the circle
+            f = [utot(x + j * h * nrm) for j in range(5)]
+            dn = (-25 * f[0] + 48 * f[1] - 36 * f[2] + 16 * f[3] - 3 * f[4]) / (12 * h)
+            res = np.abs(dn).max() / cl.k
+            assert res < 1e-7, (s, res)
+
+
+def test_farfield_is_large_r_limit_of_near_field():
+    """u(r theta_hat) = e^{ikr} r^{-1/2} a_L(theta) + O(r^{-3/2}) (section 4.4);
+    Richardson-extrapolated in r."""
+    cl = W.small_mixed(seed=5, M=4, N=14, k=1.7)
+    cl.bc[:] = 0
+    rho = solve_lu(cl, [0.3])[:, 0]
+    th = np.linspace(0, 2 * np.pi, 9, endpoint=False)
+    F = O_.farfield(cl.centres, cl.radii, cl.k, cl.N, rho, th)[:, 0]
+
+    def scaled(r):
+        pts = r * np.stack([np.cos(th), np.sin(th)], 1)
+        u = O_.single_layer_potential(cl.centres, cl.radii, cl.k, cl.N, rho, pts)
+        return u * np.exp(-1j * cl.k * r) * np.sqrt(r)
+
+    r = 2.0e6
+    est = 2 * scaled(2 * r) - scaled(r)
+    assert np.abs(est - F).max() <= 1e-6 * np.abs(F).max()
+
+
+def test_optical_theorem_and_reciprocity():
+    cl = W.four_disks()
+    T = 720
+    th = W.angles(T)
+    beta = 0.4
+    rho = solve_lu(cl, [beta, 1.9 + np.pi])
+    F = O_.farfield(cl.centres, cl.radii, cl.k, cl.N, rho, np.concatenate([th, [beta, 1.9, beta + np.pi]]))
+    # energy balance for a lossless obstacle: int |F|^2 = -2 sqrt(2 pi / k) Re(e^{i pi/4} F(beta))
+    lhs = np.sum(np.abs(F[:T, 0]) ** 2) * 2 * np.pi / T
+    rhs = -2 * np.sqrt(2 * np.pi / cl.k) * np.real(np.exp(1j * np.pi / 4) * F[T, 0])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    # reciprocity: F(theta; beta) = F(beta + pi; theta + pi)
+    f1 = F[T + 1, 0]          # theta = 1.9, incidence beta
+    f2 = F[T + 2, 1]          # theta = beta + pi, incidence 1.9 + pi
+    assert abs(f1 - f2) <= 1e-12 * abs(f1)
+
+
+def test_lu_and_gmres_agree():
+    for cl in (W.four_disks(), W.small_mixed(seed=3, M=6, N=10, k=2.0)):
+        beta = [0.0, 1.1]
+        x_lu = solve_lu(cl, beta)
+        x_gm, st = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, beta, method="gmres",
+                            restart=30, tol=1e-13, maxit=500)
+        assert all(s["flag"] == 0 for s in st)
+        assert np.abs(x_gm - x_lu).max() <= 1e-10 * np.abs(x_lu).max()
+
+
+def test_spectral_convergence_in_N():
+    base = W.four_disks()
+    errs = []
+    for N in (6, 10, 14):
+        res = []
+        for NN in (N, N + 10):
+            cl = W.Cluster(base.centres, base.radii, base.bc, base.k, NN)
+            rho = solve_lu(cl, [0.0])[:, 0].reshape(4, -1)
+            res.append(rho)
+        common = res[1][:, 10:10 + 2 * N + 1]   # modes |m| <= N of the N+10 solve
+        errs.append(np.abs(res[0] - common).max() / np.abs(common).max())
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] / errs[0] < 1e-2 and errs[2] < 1e-10
+
+
+def test_translation_and_rotation_covariance():
+    cl = W.small_mixed(seed=7, M=4, N=12, k=1.9)
+    beta, th = 0.8, W.angles(12)
+    rho = solve_lu(cl, [beta])
+    F = O_.farfield(cl.centres, cl.radii, cl.k, cl.N, rho, th)[:, 0]
+    # translation by t: densities gain exp(i k beta_hat . t)
+    t = np.array([1.3, -0.7])
+    cl_t = W.Cluster(cl.centres + t, cl.radii, cl.bc, cl.k, cl.N)
+    rho_t = solve_lu(cl_t, [beta])
+    ph = np.exp(1j * cl.k * (np.cos(beta) * t[0] + np.sin(beta) * t[1]))
+    assert np.abs(rho_t - ph * rho).max() <= 1e-11 * np.abs(rho).max()
+    # rotation by phi of geometry and incidence: F'(theta + phi) = F(theta)
+    phi = 0.37
+    Rm = np.array([[np.cos(phi), -np.sin(phi)], [np.sin(phi), np.cos(phi)]])
+    cl_r = W.Cluster(cl.centres @ Rm.T, cl.radii, cl.bc, cl.k, cl.N)
+    rho_r = solve_lu(cl_r, [beta + phi])
+    F_r = O_.farfield(cl_r.centres, cl_r.radii, cl.k, cl.N, rho_r, th + phi)[:, 0]
+    assert np.abs(F_r - F).max() <= 1e-11 * np.abs(F).max()
+
+
+def test_truncation_rule_example():
+    """Eq. (Np) evaluated for k a = 6 pi * 0.15 (Example I's largest disk)."""
+    N = O_.truncation_order(6 * np.pi * 0.15, 1e-10)
+    assert N == int(np.floor(6 * np.pi * 0.15 + (np.log(2 * np.sqrt(2) * np.pi * 6 * np.pi * 0.15 / 1e-10)
+                                                  / (2 * np.sqrt(2))) ** (2 / 3) * (6 * np.pi * 0.15) ** (1 / 3) + 1))
+    assert 8 <= N <= 14
+
+
+def test_preconditioned_rows_match_dense():
+    cl = W.small_mixed(seed=9, M=5, N=9, k=2.1)
+    A = O_.assemble(cl.centres, cl.radii, cl.bc, cl.k, cl.N)
+    b = O_.rhs_planewave(cl.centres, cl.radii, cl.bc, cl.k, cl.N, [0.2, 1.0])
+    Ap, bp = O_.precondition(A, b, cl.M, cl.n)
+    x = np.random.default_rng(0).standard_normal((cl.ntot, 3)) + 0j
+    y = O_.preconditioned_rows(cl.centres, cl.radii, cl.bc, cl.k, cl.N, x, range(cl.M))
+    assert np.abs(y.reshape(cl.ntot, 3) - Ap @ x).max() <= 1e-12 * np.abs(Ap @ x).max()
+    bp2 = O_.preconditioned_rhs(cl.centres, cl.radii, cl.bc, cl.k, cl.N, [0.2, 1.0])
+    assert np.abs(bp2 - bp).max() <= 1e-13 * np.abs(bp).max()
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def _flip_alpha(Op, Oq, k, N):
+    m = O_.modes(N)
+    d = m[:, None] - m[None, :]
+    v = np.asarray(Oq) - np.asarray(Op)   # wrong direction
+    b, al = np.hypot(*v), np.arctan2(v[1], v[0])
+    return special.hankel1(d, k * b) * np.exp(1j * d * al)
+
+
+def _transposed_S(Op, Oq, k, N):
+    v = np.asarray(Op) - np.asarray(Oq)
+    b, al = np.hypot(*v), np.arctan2(v[1], v[0])
+    m = O_.modes(N)
+    d = m[None, :] - m[:, None]            # n - m instead of m - n
+    return special.hankel1(d, k * b) * np.exp(1j * d * al)
+
+
+@pytest.mark.parametrize("bad", [_flip_alpha, _transposed_S])
+def test_planted_separation_mistakes_are_caught(monkeypatch, bad):
+    cl = two_disks()
+    ref = quadrature_block(cl.centres[0], cl.radii[0], cl.centres[1], cl.radii[1], cl.k, cl.N, "L")
+    monkeypatch.setattr(O_, "separation_matrix", bad)
+    blk = O_.block_L(cl.centres, cl.radii, cl.k, cl.N, 0, 1)
+    assert np.abs(blk - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_planted_rhs_phase_mistake_is_caught(monkeypatch):
+    good = O_.planewave_coefficients
+
+    def bad(O, a, k, N, beta):
+        return np.conj(good(O, a, k, N, beta)) * 0 + good(O, a, k, N, -beta)
+
+    monkeypatch.setattr(O_, "planewave_coefficients", bad)
+    Oc, a, k, beta, N = np.array([0.7, -0.4]), 1.1, 2.3, 0.6, 30
+    cl = W.Cluster(Oc[None, :], np.array([a]), np.array([0], np.int8), k, N)
+    rho = solve_lu(cl, [beta])[:, 0]
+    pts = Oc[None, :] + 2.0 * np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
+    u = O_.single_layer_potential(cl.centres, cl.radii, k, N, rho, pts)
+    ref = mie_field(Oc, a, k, beta, pts)
+    assert np.abs(u - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_planted_farfield_constant_mistake_is_caught(monkeypatch):
+    good = O_.farfield_coefficients
+    monkeypatch.setattr(O_, "farfield_coefficients",
+                        lambda O, a, k, N, th: good(O, a, k, N, th) * np.exp(1j * np.pi / 2))
+    cl = W.four_disks()
+    T = 360
+    rho = solve_lu(cl, [0.4])
+    F = O_.farfield(cl.centres, cl.radii, cl.k, cl.N, rho, np.concatenate([W.angles(T), [0.4]]))
+    lhs = np.sum(np.abs(F[:T, 0]) ** 2) * 2 * np.pi / T
+    rhs = -2 * np.sqrt(2 * np.pi / cl.k) * np.real(np.exp(1j * np.pi / 4) * F[T, 0])
+    assert abs(lhs - rhs) > 1e-3 * abs(lhs)
+
+
+def test_planted_neumann_diagonal_mistake_is_caught(monkeypatch):
+    """Dropping the -I/2 of the exterior normal trace breaks the sound-hard
+    single-disk series."""
+    good = O_.assemble
+
+    def bad(O, a, bc, k, N):
+        A = good(O, a, bc, k, N)
+        n = 2 * N + 1
+        for p in range(len(a)):
+            if bc[p] == 1:
+                A[p * n:(p + 1) * n, p * n:(p + 1) * n] += 0.5 * np.eye(n)
+        return A
+
+    monkeypatch.setattr(O_, "assemble", bad)
+    Oc, a, k, beta, N = np.array([0.7, -0.4]), 1.1, 2.3, 0.6, 30
+    cl = W.Cluster(Oc[None, :], np.array([a]), np.array([1], np.int8), k, N)
+    rho = solve_lu(cl, [beta])[:, 0]
+    pts = Oc[None, :] + 2.0 * np.array([[1.0, 0.0], [0.0, 1.0]])
+    u = O_.single_layer_potential(cl.centres, cl.radii, k, N, rho, pts)
+    ref = mie_field(Oc, a, k, beta, pts, hard=True)
+    assert np.abs(u - ref).max() > 1e-3 * np.abs(ref).max()
