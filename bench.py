@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark of the multiple-scattering hot path on GB300.
+
+One step = the whole hot path on the 400-disk workload (M = 400 sound-soft
+disks, radii U[0.5, 1.5] in a 100 x 100 square, gap 0.2, k = 2 pi, N = 20,
+16 400 unknowns, one plane wave): Bessel diagonals and Toeplitz generators
+(recomputed from the device-resident geometry), preconditioned right-hand
+side, restarted GMRES to relres 1e-10 with the block-Toeplitz product, and
+the far field at 360 angles.  The FP64 path is the timed step; the same
+steps are then timed with FP32 inner sweeps and FP64 refinement (MSD_MIXED)
+for the "FP64 vs mixed" half of the metric.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "block-matvec GB/s (% HBM peak) & solve time at relres 1e-10, FP64 vs mixed"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+WORKLOAD = ("random400_k2pi: M=400 sound-soft disks, a~U[0.5,1.5], centres U[-50,50]^2 gap 0.2, "
+            "k=2pi, N=20 (16400 unknowns), 1 plane wave, GMRES(100) to relres 1e-10, far field T=360")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def start_clock_sampler(dev: int):
+    try:
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        return subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def stop_clock_sampler(p):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except Exception:
+        p.kill()
+        return None
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 7:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[3:7]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def oracle_matvec_sample(cl, targets, seconds=10.0):
+    """Times the oracle's preconditioned block rows on a sample of target
+    disks; returns seconds per full product (scaled to all M rows)."""
+    import numpy as np
+    import oracle.msd_oracle as O_
+    x = (np.random.default_rng(0).standard_normal((cl.ntot, 1)) + 0j)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        for p in targets:
+            O_.preconditioned_rows(cl.centres, cl.radii, cl.bc, cl.k, cl.N, x, [p])
+            done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return dt / done * cl.M, done
+
+
+def algorithmic_bytes_fp64(cl, R=1):
+    M, L, n = cl.M, 4 * cl.N + 1, cl.n
+    return 16.0 * (M * (M - 1) * L + 2.0 * M * n * R)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1409_8186_gb300 import workloads as W
+    cl = W.random_cluster_400()
+    sample = list(range(0, cl.M, max(1, cl.M // 8)))[:8]
+    for _ in range(max(0, args.warmup)):
+        oracle_matvec_sample(cl, sample[:1], seconds=0.0)
+    times = []
+    for _ in range(args.steps):
+        t, _ = oracle_matvec_sample(cl, sample, seconds=2.0)
+        times.append(t)
+    t = statistics.median(times)
+    gbs = algorithmic_bytes_fp64(cl) / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "what": "oracle block-row products (FP64 NumPy/SciPy), one full "
+                       "product per step extrapolated from 8 sampled target disks"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "8 of 400 target block rows per step, scaled by 400/8"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1409_8186_gb300 import msd, workloads as W
+
+    cl = W.random_cluster_400()
+    beta = np.array([[cl.meta["beta"]]])
+    thetas = W.angles(360)
+    pb = msd.Problem(cl)
+    h = pb.handle
+    cen_d = torch.from_numpy(np.ascontiguousarray(cl.centres)).cuda()
+    rad_d = torch.from_numpy(np.ascontiguousarray(cl.radii)).cuda()
+    rho = torch.empty((cl.ntot, 1), dtype=torch.complex128, device="cuda")
+    F = torch.empty((1, 360, 1), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    stats = (msd.msd_stats * 1)()
+
+    def step(precision):
+        msd.msd_update_geometry(h, cen_d, rad_d, None)
+        o = msd.msd_opts(1e-10, 100, 3000, 0, 0.0, precision, 0)
+        st = msd.msd_solve_planewaves(h, 1, beta, o, rho, stats)
+        msd.msd_farfield(h, rho, 1, thetas, F)
+        return st
+
+    def timed(precision, K, W_):
+        for _ in range(W_):
+            step(precision)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        msd.msd_matvec_timing(h, 1)
+        l0 = msd.msd_kernel_launches()
+        sampler = start_clock_sampler(local) if precision == msd.MSD_FP64 else None
+        ms, iters, statuses = [], [], []
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            statuses.append(step(precision))
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            iters.append(stats[0].iters)
+        clocks = stop_clock_sampler(sampler)
+        launches = msd.msd_kernel_launches() - l0
+        kms, kl, kfl, kby = msd.msd_matvec_timing(h, 0)
+        if dist:
+            dist.barrier()
+        return dict(ms=ms, iters=iters, status=statuses, relres=stats[0].relres, clocks=clocks, launches=launches,
+                    kernel_ms=kms, kernel_launches=kl, kernel_flops=kfl, kernel_bytes=kby)
+
+    r64 = timed(msd.MSD_FP64, args.steps, args.warmup)
+    rmx = timed(msd.MSD_MIXED, args.steps, args.warmup)
+
+    total_ms = sum(r64["ms"])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # whole-job throughput: algorithmic bytes of every block product in the
+    # timed steps (all ranks) over the slowest rank's time
+    value = r64["kernel_bytes"] * world / (total_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (host->device inputs,
+    # device->host densities and far field inside the timed region)
+    cen_h = np.ascontiguousarray(cl.centres)
+    rad_h = np.ascontiguousarray(cl.radii)
+    rho_h = np.empty((cl.ntot, 1), np.complex128)
+    F_h = np.empty((1, 360, 1), np.complex128)
+
+    def step_e2e():
+        msd.msd_update_geometry(h, cen_h, rad_h, None)
+        o = msd.msd_opts(1e-10, 100, 3000, 0, 0.0, msd.MSD_FP64, 0)
+        msd.msd_solve_planewaves(h, 1, beta, o, rho_h, stats)
+        msd.msd_farfield(h, rho_h, 1, thetas, F_h)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    msd.msd_matvec_timing(h, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    _, _, _, e2e_bytes = msd.msd_matvec_timing(h, 0)
+    h2d = cen_h.nbytes + rad_h.nbytes + beta.nbytes + thetas.nbytes + rho_h.nbytes
+    d2h = rho_h.nbytes + F_h.nbytes
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kern_s = r64["kernel_ms"] * 1e-3
+    achieved_tf = r64["kernel_flops"] / kern_s / 1e12 if kern_s > 0 else 0.0
+    kern_gbs = r64["kernel_bytes"] / kern_s / 1e9 if kern_s > 0 else 0.0
+    mix_kern_s = rmx["kernel_ms"] * 1e-3
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sample = list(range(0, cl.M, cl.M // 8))[:8]
+        t_cpu, done = oracle_matvec_sample(cl, sample, seconds=12.0)
+        cpu_gbs = algorithmic_bytes_fp64(cl) / t_cpu / 1e9
+        cpu = {"value": cpu_gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} target block rows of the 400-disk product (FP64 NumPy/SciPy), "
+                         "scaled to one full product", "ms_per_matvec": t_cpu * 1e3}
+
+    ms_step = total_ms / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+                   "step": "K1 diagonals + K2 generators + K5 rhs + GMRES(100) with K3 products + K6 far field"},
+        "hbm_frac_whole_step": value / hbm,
+        "solve_ms_fp64": statistics.median(r64["ms"]), "solve_ms_mixed": statistics.median(rmx["ms"]),
+        "mixed_speedup": statistics.median(r64["ms"]) / statistics.median(rmx["ms"]),
+        "iters_fp64": r64["iters"][-1], "iters_mixed": rmx["iters"][-1],
+        "relres_fp64": r64["relres"], "relres_mixed": rmx["relres"],
+        "status_fp64": r64["status"][-1], "status_mixed": rmx["status"][-1],
+        "matvec_fp64": {"kernel_ms_avg": r64["kernel_ms"] / max(1, r64["kernel_launches"]),
+                        "launches": r64["kernel_launches"], "GB_s": kern_gbs, "hbm_frac": kern_gbs / hbm,
+                        "TFLOP_s": achieved_tf},
+        "matvec_fp32": {"kernel_ms_avg": rmx["kernel_ms"] / max(1, rmx["kernel_launches"]),
+                        "launches": rmx["kernel_launches"],
+                        "GB_s": rmx["kernel_bytes"] / 2 / mix_kern_s / 1e9 if mix_kern_s > 0 else None,
+                        "TFLOP_s": rmx["kernel_flops"] / mix_kern_s / 1e12 if mix_kern_s > 0 else None},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_bt_matvec<double2,1,1> (FP64 block-Toeplitz product)",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_bytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s / args.steps * 1e3},
+        "gpu_launches": int(r64["launches"]),
+        "clocks": r64["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * msd.h -- C ABI of the GB300 multiple-scattering-by-disks library (libmsd.so).
+ *
+ * The library solves the truncated Fourier-Galerkin boundary-integral system
+ * for M disks (paper: mu-diff, arXiv 1409.8186, section 5, eq. for
+ * L rho = -U and its sound-hard counterpart) on one GPU, with the
+ * block-Toeplitz matrix-vector product of section 5 as the hot path.
+ *
+ * Notation (section 4.1): disk p has centre O_p, radius a_p and a boundary
+ * condition flag; every disk of a configuration carries the Fourier modes
+ * m = -N..N (n = 2N+1 per disk).  A configuration with M disks has
+ * N_tot = M*n unknowns; several configurations may be batched in one
+ * problem, their unknowns concatenated in configuration order.
+ *
+ * Vector layout (all vectors in this ABI): element (row, r) at index
+ * row*R + r, row = row_offset(config) + p*n + (m + N), r = right-hand side
+ * (incidence angle) index.  Complex numbers are interleaved (re, im):
+ * complex128 = two doubles, complex64 = two floats.
+ *
+ * Pointers.  Arguments named *_host are host memory owned by the caller and
+ * only read (or written) during the call.  Arguments documented "host or
+ * device" may point to either; the library asks the CUDA runtime which it is
+ * and stages host buffers through device memory itself.  Device results are
+ * written asynchronously on the problem's stream unless stated otherwise;
+ * host results are complete when the call returns.  The caller keeps
+ * ownership of every buffer it passes; the library owns its work buffers
+ * and frees them in msd_destroy.
+ *
+ * Errors.  Every call returns an msd_status.  Negative values mean no
+ * result was produced; msd_last_error() then describes the failure (per
+ * thread).  Positive values (from the solver) mean a result was produced
+ * but the stopping test was not met.  Nothing aborts the process and no
+ * C++ exception crosses this boundary.  Every device-side wait or loop in
+ * the library is bounded.
+ */
+#ifndef MSD_H
+#define MSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msd_problem msd_problem;
+
+typedef enum {
+    MSD_OK = 0,              /* converged / completed                               */
+    MSD_NOT_CONVERGED = 1,   /* iteration limit reached before the tolerance        */
+    MSD_STAGNATED = 3,       /* refinement stopped reducing the FP64 residual        */
+    MSD_ERR_ARG = -1,        /* invalid argument (sizes, null pointers, N range)     */
+    MSD_ERR_OVERLAP = -2,    /* two disks of one configuration intersect             */
+    MSD_ERR_CUDA = -3,       /* a CUDA runtime call failed                            */
+    MSD_ERR_OOM = -4,        /* device allocation failed                              */
+    MSD_ERR_NONFINITE = -5,  /* a NaN/Inf appeared in an input or an iterate          */
+    MSD_ERR_RANGE = -6       /* a Hankel generator exceeds the complex64 range        */
+} msd_status;
+
+enum { MSD_DIRICHLET = 0, MSD_NEUMANN = 1 };          /* sound-soft / sound-hard   */
+enum { MSD_FP64 = 0, MSD_MIXED = 1, MSD_FP32 = 2 };   /* arithmetic of a product   */
+enum { MSD_GEN_AUTO = 0, MSD_GEN_STREAMED = 1, MSD_GEN_RECOMPUTE = 2 };
+
+/* Largest truncation order accepted (modes -N..N, n <= 127). */
+#define MSD_MAX_N 63
+
+/* Solver options (section 5 and the restarted GMRES call of section 6.2:
+ * RESTART, TOL, MAXIT).  Zero-initialised fields take the defaults in
+ * brackets. */
+typedef struct {
+    double tol;        /* stop when ||P^-1(b - A x)|| / ||P^-1 b|| <= tol   [1e-10]   */
+    int restart;       /* GMRES restart length m                            [100]     */
+    int maxit;         /* limit on Arnoldi steps over the whole solve       [3000]    */
+    int max_refine;    /* MSD_MIXED: limit on FP64 refinement sweeps        [60]      */
+    double inner_tol;  /* MSD_MIXED: relative tolerance of each FP32 sweep  [2e-6]    */
+    int precision;     /* MSD_FP64 (all FP64) or MSD_MIXED                  [FP64]    */
+    int gen_mode;      /* MSD_GEN_*: generators stored in HBM or recomputed [auto]    */
+} msd_opts;
+
+/* Per-system statistics (one per configuration and right-hand side). */
+typedef struct {
+    int flag;          /* MSD_OK, MSD_NOT_CONVERGED or MSD_STAGNATED                    */
+    int iters;         /* Arnoldi steps taken by this system (all sweeps)               */
+    int refine_steps;  /* FP64 residual evaluations after the first (MSD_MIXED)         */
+    int reserved;
+    double relres;     /* final FP64 relative residual of the preconditioned system     */
+} msd_stats;
+
+/* Create a problem.  Section 4.1 (geometry), section 5 (truncation).
+ *   C            number of batched configurations (>= 1)
+ *   disk_off     [C+1] host: configuration c owns disks disk_off[c]..disk_off[c+1]-1
+ *   centres      [disk_off[C]][2] host: O_p = (x, y)
+ *   radii        [disk_off[C]] host: a_p > 0
+ *   bc           [disk_off[C]] host: MSD_DIRICHLET or MSD_NEUMANN per disk
+ *   k            [C] host: wavenumber per configuration (> 0)
+ *   N            [C] host: truncation order per configuration (1..MSD_MAX_N)
+ *   cuda_stream  cudaStream_t used for every later call (NULL: legacy stream)
+ *   out          receives the problem handle
+ * Copies the geometry to the device and evaluates the Bessel diagonals of
+ * section 4.2 (kernel K1).  Returns MSD_ERR_OVERLAP if two disks of one
+ * configuration intersect. */
+msd_status msd_create(int C, const int* disk_off, const double* centres,
+                      const double* radii, const int8_t* bc, const double* k,
+                      const int* N, void* cuda_stream, msd_problem** out);
+
+void msd_destroy(msd_problem* pb);
+
+/* Total unknowns (sum over configurations of M*n) and the row offset of a
+ * configuration; -1 on a bad handle or index. */
+int64_t msd_num_unknowns(const msd_problem* pb);
+int64_t msd_row_offset(const msd_problem* pb, int config);
+
+/* Section 4.2: the diagonals J^p, J'^p, H^p, H'^p at k a_p for every unknown
+ * row, as complex128 [4][N_tot] (J and J' carry zero imaginary parts).
+ * out: host or device, caller-allocated. */
+msd_status msd_disk_diagonals(msd_problem* pb, void* out);
+
+/* Section 4.2: the Toeplitz generators g^pq_l = H^(1)_l(k b_pq) e^{i l alpha_pq},
+ * l = -2N..2N, of configuration `config` (kernel K2), as complex128
+ * [q][p][l + 2N] (M*M*(4N+1) values, zeros on p == q).  These are the
+ * entries of (S^pq)^T: (S^pq)^T_mn = g^pq_{n-m}.  out: host or device. */
+msd_status msd_pair_generators(msd_problem* pb, int config, void* out);
+
+/* Prop. 4.1 and section 5: the preconditioned plane-wave right-hand side
+ * P^-1(-U) (Dirichlet rows) or P^-1(-dU) (Neumann rows), complex128
+ * [N_tot][R].  betas: [C][R] host incidence angles (kernel K5).
+ * out: host or device. */
+msd_status msd_rhs_planewave(msd_problem* pb, int R, const double* betas_host, void* out);
+
+/* Section 5 (hot path, kernel K3): y = P^-1 A x, the single-scattering
+ * left-preconditioned operator, applied to R columns at once:
+ *   y^p_m = x^p_m + l^p_m sum_{q != p} sum_n g^pq_{n-m} r^q_n x^q_n,
+ * with r^q_n = sqrt(a_q) J_n(k a_q), l^p_m = 1/(sqrt(a_p) H_m(k a_p))
+ * (Dirichlet) or J'_m/(sqrt(a_p) J_m H'_m) (Neumann).
+ *   precision  MSD_FP64: x, y complex128; MSD_FP32: complex64 with FP32
+ *              accumulation (the inner product of MSD_MIXED solves)
+ *   x, y       device, [N_tot][R]; x and y must not overlap
+ * Asynchronous on the problem's stream. */
+msd_status msd_matvec(msd_problem* pb, int R, int precision, const void* x_dev, void* y_dev);
+
+/* Section 5 / section 6.2: solve A rho = -U for R plane waves per
+ * configuration with left-preconditioned restarted GMRES on the device
+ * (x0 = 0), FP64 throughout (MSD_FP64) or FP32 inner sweeps with FP64
+ * residuals and corrections (MSD_MIXED).
+ *   betas_host  [C][R] incidence angles
+ *   opts        may be NULL (defaults)
+ *   rho_out     host or device, complex128 [N_tot][R]: the density
+ *               coefficients rho^p_m (identical for A and P^-1 A)
+ *   stats_host  may be NULL, else [C*R] (system index c*R + r)
+ * Synchronises the stream.  Returns MSD_OK when every system met opts->tol,
+ * MSD_NOT_CONVERGED / MSD_STAGNATED otherwise (rho_out still written). */
+msd_status msd_solve_planewaves(msd_problem* pb, int R, const double* betas_host,
+                                const msd_opts* opts, void* rho_out, msd_stats* stats_host);
+
+/* Section 4.4: far field a_L(theta_t) = (a_L(theta_t))^T rho for every
+ * configuration, sample angle and column (kernel K6).
+ *   rho     host or device, complex128 [N_tot][R]
+ *   thetas  [T] host sample angles (shared by all configurations)
+ *   F_out   host or device, complex128 [C][T][R] */
+msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T,
+                        const double* thetas_host, void* F_out);
+
+/* Replace the geometry of every configuration (same disk counts, N and
+ * boundary flags) and recompute the Bessel diagonals (K1) and any stored
+ * Toeplitz generators (K2).  Any argument may be NULL to keep it.
+ *   centres  host or device, [disk_off[C]][2]
+ *   radii    host or device, [disk_off[C]]
+ *   k_host   host, [C]
+ * The disks are not re-checked for overlap.  Synchronises the stream. */
+msd_status msd_update_geometry(msd_problem* pb, const double* centres, const double* radii,
+                               const double* k_host);
+
+/* Kernel timing of the block-Toeplitz product.  enable = 1 starts recording
+ * a CUDA event pair around every K3 kernel launched on the problem's
+ * stream (the column scaling and the split reduction around it are
+ * excluded), enable = 0 stops, enable = -1 only reads.  On return the
+ * totals since the last start: summed kernel time in ms, number of
+ * launches, algorithmic flops (8 per complex multiply-add of the
+ * off-diagonal blocks) and algorithmic bytes (generators of every ordered
+ * pair plus x and y) of those launches.  Any output may be NULL.
+ * Synchronises on the recorded events. */
+msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int64_t* launches,
+                             double* flops, double* bytes);
+
+/* Total number of CUDA kernels launched by this library in this process. */
+int64_t msd_kernel_launches(void);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char* msd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSD_H */

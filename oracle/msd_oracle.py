@@ -64,6 +64,15 @@ def pair_vector(Op, Oq):
     return v, float(np.hypot(v[0], v[1])), float(np.arctan2(v[1], v[0]))
 
 
+def separation_generator(Op, Oq, k: float, N: int) -> np.ndarray:
+    """Section 4.2: the entries of S^pq depend on m - n only; this returns
+    the 4N+1 values H^(1)_l(k b_pq) exp(i l alpha_pq), l = -2N..2N, so that
+    S^pq_mn = g[(m - n) + 2N] and (S^pq)^T_mn = g[(n - m) + 2N]."""
+    _, b, alpha = pair_vector(Op, Oq)
+    l = np.arange(-2 * N, 2 * N + 1)
+    return special.hankel1(l, k * b) * np.exp(1j * l * alpha)
+
+
 def separation_matrix(Op, Oq, k: float, N: int) -> np.ndarray:
     """Section 4.2: S^pq_mn = H^(1)_{m-n}(k b_pq) exp(i (m-n) alpha_pq),
     m, n = -N..N."""
@@ -259,37 +268,52 @@ def solve(cluster_O, a, bc, k, N, betas, method="lu", **gm):
 # (for clusters whose dense matrix does not fit in host memory)
 # --------------------------------------------------------------------------
 
-def preconditioned_rows(O, a, bc, k, N, x, targets) -> np.ndarray:
-    """Rows p in `targets` of (P^-1 A) x, built block by block from the
-    section 4.2 definitions: y^p = x^p + (A^pp)^-1 sum_{q != p} A^pq x^q.
-    x is [N_tot, R]; returns [len(targets), 2N+1, R]."""
+def preconditioned_block_row(O, a, bc, k, N, p) -> np.ndarray:
+    """Row block p of P^-1 A as a dense [2N+1, M(2N+1)] array, built from
+    the section 4.2 blocks A^pq (L^pq or N^pq, whose (S^pq)^T factor is read
+    from the separation generator) divided by the diagonal of A^pp."""
     O = np.asarray(O, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
     M = len(a)
     n = 2 * N + 1
-    X = np.asarray(x).reshape(M, n, -1)
     J, dJ, H, dH = bessel_diagonals(a, k, N)
     m = modes(N)
-    dmn = m[None, :] - m[:, None]          # n - m for entry (m, n) of (S^pq)^T
-    out = []
-    for p in targets:
-        qs = np.array([q for q in range(M) if q != p])
+    idx = (m[None, :] - m[:, None]) + 2 * N      # (n - m) + 2N for entry (m, n)
+    if bc[p] == DIRICHLET:
+        left = J[p]
+        diag = 0.5j * np.pi * a[p] * J[p] * H[p]
+    else:
+        left = k * dJ[p]
+        diag = 0.5j * np.pi * k * a[p] * J[p] * dH[p]
+    row = np.zeros((n, M, n), dtype=np.complex128)
+    l = np.arange(-2 * N, 2 * N + 1)
+    qs = np.array([q for q in range(M) if q != p], dtype=int)
+    if len(qs):
         bv = O[p][None, :] - O[qs]
         b = np.hypot(bv[:, 0], bv[:, 1])
         al = np.arctan2(bv[:, 1], bv[:, 0])
-        # (S^pq)^T_mn = S^pq_nm = H_{n-m}(k b) exp(i (n-m) alpha)
-        ST = special.hankel1(dmn[None], k * b[:, None, None]) * np.exp(1j * dmn[None] * al[:, None, None])
+        g = special.hankel1(l[None, :], k * b[:, None]) * np.exp(1j * l[None, :] * al[:, None])
+        ST = g[:, idx]                                  # [q, m, n] = (S^pq)^T_mn
         coef = 0.5j * np.pi * np.sqrt(a[p] * a[qs])
-        if bc[p] == DIRICHLET:
-            left = J[p]
-            diag = 0.5j * np.pi * a[p] * J[p] * H[p]
-        else:
-            left = k * dJ[p]
-            diag = 0.5j * np.pi * k * a[p] * J[p] * dH[p]
         blocks = coef[:, None, None] * left[None, :, None] * ST * J[qs][:, None, :]
-        acc = np.einsum("qmn,qnr->mr", blocks, X[qs])
-        out.append(X[p] + acc / diag[:, None])
-    return np.stack(out, axis=0)
+        row[:, qs, :] = np.transpose(blocks / diag[None, :, None], (1, 0, 2))
+    row[:, p, :] = np.eye(n)
+    return row.reshape(n, M * n)
+
+
+def preconditioned_rows(O, a, bc, k, N, x, targets) -> np.ndarray:
+    """Rows p in `targets` of (P^-1 A) x (see preconditioned_block_row).
+    x is [N_tot, R]; returns [len(targets), 2N+1, R]."""
+    x = np.asarray(x)
+    if x.ndim == 1:
+        x = x[:, None]
+    return np.stack([preconditioned_block_row(O, a, bc, k, N, p) @ x for p in targets], axis=0)
+
+
+def preconditioned_dense(O, a, bc, k, N) -> np.ndarray:
+    """P^-1 A assembled block row by block row (same definition as
+    precondition(assemble(...)), faster for a few thousand unknowns)."""
+    return np.concatenate([preconditioned_block_row(O, a, bc, k, N, p) for p in range(len(a))], axis=0)
 
 
 def preconditioned_rhs(O, a, bc, k, N, betas) -> np.ndarray:

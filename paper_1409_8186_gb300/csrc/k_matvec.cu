@@ -1,0 +1,277 @@
+// K3: block-Toeplitz product of the single-scattering-preconditioned
+// operator (section 5, built from the blocks of section 4.2):
+//
+//   y^p_m = x^p_m + l^p_m * s^p_m,   s^p_m = sum_{q != p} sum_n g^pq_{n-m} xs^q_n,
+//   xs^q_n = r^q_n x^q_n,
+//
+// for R right-hand sides at once.  Each off-diagonal block is the Toeplitz
+// matrix (S^pq)^T with generator g^pq (4N+1 values), scaled by the Bessel
+// diagonals; the dense block (n^2 entries) is never formed.
+//
+// Work decomposition: a CTA owns a tile of 32 target disks (one per lane),
+// a contiguous range of source disks q, and RT columns.  Warps split the
+// target modes into blocks of B consecutive m (and the columns into groups
+// of RB).  Per source q the CTA stages, with cp.async and double buffering,
+// the 32 generator rows g^{p q}_{.} (contiguous in the [q][p][l] layout) and
+// the RT-column slab of xs^q into shared memory.  Each thread then sweeps n
+// with a register window of B generator values (one new value per n, since
+// neighbouring m need neighbouring l = n - m) and accumulates B x RB complex
+// sums.  Generator rows are padded in shared memory to an odd length so the
+// 32 lanes (32 different rows) hit 32 different banks; the xs slab is a
+// broadcast.  Raw sums go to a per-split partial buffer; a finalize kernel
+// adds the splits, applies l^p_m and adds x.
+#include "msd_internal.cuh"
+
+namespace {
+
+constexpr int kB = 8;  // target modes per thread (register window length)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async(void* dst, const float2* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async(void* dst, const double2* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int n>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(n)); }
+
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+
+// Shared-memory footprint (elements) of one stage.
+__host__ __device__ inline int stage_g_elems(int L) { return MSD_TILE_P * (L + 2 * kB); }
+__host__ __device__ inline int stage_x_elems(int n, int RT) {
+    int I = (n + kB - 1) / kB;
+    return I * kB * RT;
+}
+
+template <typename V, int RT, int RB>
+__global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
+                                                   const MatvecWork* __restrict__ works,
+                                                   const V* __restrict__ G, const V* __restrict__ xs,
+                                                   V* __restrict__ part, long long Ntot, int R, int rtiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* smem = reinterpret_cast<V*>(smem_raw);
+
+    const int wi = blockIdx.x / rtiles;
+    const int rt = blockIdx.x % rtiles;
+    const MatvecWork w = works[wi];
+    const MsdConfig c = cfgs[w.cfg];
+    const int N = c.N, n = c.n, L = c.L;
+    const int Ls = L + 2 * kB;
+    const int I = (n + kB - 1) / kB;
+    const int npad = I * kB;
+    const int gsz = stage_g_elems(L), xsz = stage_x_elems(n, RT);
+    V* gbuf[2] = {smem, smem + gsz + xsz};
+    V* xbuf[2] = {smem + gsz, smem + 2 * gsz + xsz};
+
+    const int lane = threadIdx.x;  // target p0 + lane
+    const int warp = threadIdx.y;
+    const int nthreads = blockDim.x * blockDim.y;
+    const int tid = warp * 32 + lane;
+    // the launch sizes warps for the largest N of the batch: blocks beyond
+    // this configuration's I m-blocks only help with staging
+    const int Imax = blockDim.y / (RT / RB);
+    const int mblk = warp % Imax;
+    const int rgrp = warp / Imax;
+    const bool mact = mblk < I;
+    const int m0 = mblk * kB;
+    const int c0 = rgrp * RB;         // first column of this thread within the tile
+    const int col0 = rt * RT;         // first column of the tile
+
+    // zero the padding of both stages once (staging never writes it)
+    for (int s = 0; s < 2; ++s) {
+        for (int t = tid; t < MSD_TILE_P * 2 * kB; t += nthreads) {
+            int row = t / (2 * kB), j = t % (2 * kB);
+            int pos = j < kB ? j : (L + j);
+            gbuf[s][row * Ls + pos] = vzero<V>();
+        }
+        for (int t = n * RT + tid; t < npad * RT; t += nthreads) xbuf[s][t] = vzero<V>();
+    }
+
+    const V* gsrc_cfg = G + c.gen_off + (long long)w.p0 * L;
+    auto stage = [&](int q, int s) {
+        const V* src = gsrc_cfg + (long long)q * c.Mp * L;
+        V* dst = gbuf[s];
+        for (int t = tid; t < MSD_TILE_P * L; t += nthreads) {
+            int row = t / L, j = t - row * L;
+            cp_async(dst + row * Ls + kB + j, src + t);
+        }
+        const V* xsrc = xs + (c.row_off + (long long)q * n) * R + col0;
+        V* xd = xbuf[s];
+        for (int t = tid; t < n * RT; t += nthreads) {
+            int rr = t / RT, cc = t - rr * RT;
+            cp_async(xd + t, xsrc + (long long)rr * R + cc);
+        }
+    };
+
+    V acc[kB][RB];
+#pragma unroll
+    for (int b = 0; b < kB; ++b)
+#pragma unroll
+        for (int r = 0; r < RB; ++r) acc[b][r] = vzero<V>();
+
+    if (w.q0 < w.q1) stage(w.q0, 0);
+    cp_commit();
+    const int base = kB + 2 * N - m0;  // smem position of l' = n - m0 + 2N at n = 0
+    for (int it = 0, q = w.q0; q < w.q1; ++it, ++q) {
+        if (q + 1 < w.q1) stage(q + 1, (it + 1) & 1);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        if (mact) {
+        const V* gs = gbuf[it & 1] + lane * Ls + base;
+        const V* xsl = xbuf[it & 1] + c0;
+        V win[kB];
+#pragma unroll
+        for (int j = 1; j < kB; ++j) win[kB - j] = gs[-j];
+        for (int nb = 0; nb < npad; nb += kB) {
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                win[u] = gs[nb + u];
+                V xv[RB];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) xv[r] = xsl[(nb + u) * RT + r];
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const V gv = win[(u - b + kB) % kB];
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) cfma(acc[b][r], gv, xv[r]);
+                }
+            }
+        }
+        }
+        __syncthreads();
+    }
+    cp_wait<0>();
+
+    const int p = w.p0 + lane;
+    if (mact && p < c.M) {
+        V* out = part + (long long)w.split * Ntot * R;
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            const int mi = m0 + b;
+            if (mi < n) {
+                const long long row = c.row_off + (long long)p * n + mi;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) out[row * R + col0 + c0 + r] = acc[b][r];
+            }
+        }
+    }
+}
+
+// xs = rf .* x   (columns scaled by the column factor r^q_n of their row)
+template <typename V, typename S>
+__global__ void k_scale_cols(long long Ntot, int R, const S* __restrict__ rf, const V* __restrict__ x,
+                             V* __restrict__ xs) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ntot * R) return;
+    const S f = rf[i / R];
+    const V v = x[i];
+    xs[i] = V{v.x * f, v.y * f};
+}
+
+// y = x + lf .* sum_s part[s]
+template <typename V>
+__global__ void k_finalize(long long Ntot, int R, int nsplit, const V* __restrict__ lf,
+                           const V* __restrict__ x, const V* __restrict__ part, V* __restrict__ y) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ntot * R) return;
+    V s = part[i];
+    for (int k = 1; k < nsplit; ++k) {
+        const V t = part[(long long)k * Ntot * R + i];
+        s.x += t.x;
+        s.y += t.y;
+    }
+    const V l = lf[i / R];
+    const V v = x[i];
+    y[i] = V{v.x + (l.x * s.x - l.y * s.y), v.y + (l.x * s.y + l.y * s.x)};
+}
+
+template <typename V, int RT, int RB>
+void launch_bt(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const V* G,
+               const V* xs, V* part, long long Ntot, int R, cudaStream_t s) {
+    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
+    const int I = (n + kB - 1) / kB;
+    const int rtiles = R / RT;
+    dim3 block(32, I * (RT / RB));
+    size_t smem = 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * sizeof(V);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_bt_matvec<V, RT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+        attr_set = true;
+    }
+    k_bt_matvec<V, RT, RB><<<(unsigned)(nwork * rtiles), block, smem, s>>>(d_cfg, d_work, G, xs, part,
+                                                                          Ntot, R, rtiles);
+}
+
+}  // namespace
+
+// Column tile RT for R columns: the largest power of two dividing R such
+// that the CTA stays within 16 warps (I m-blocks x RT/RB column groups).
+int matvec_col_tile(int R, int Nmax, bool fp64) {
+    const int n = 2 * Nmax + 1;
+    const int I = (n + kB - 1) / kB;
+    const int rb_max = fp64 ? 2 : 4;
+    int best = 1;
+    for (int rt = 1; rt <= 16; rt *= 2) {
+        if (R % rt) break;
+        int rb = rt < rb_max ? rt : rb_max;
+        if (I * (rt / rb) <= 16) best = rt;
+    }
+    return best;
+}
+
+size_t matvec_smem_bytes(int R, int Nmax, bool fp64) {
+    const int RT = matvec_col_tile(R, Nmax, fp64);
+    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
+    return 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * (fp64 ? 16 : 8);
+}
+
+void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
+                       const double2* G, const double* rf, const double2* lf, long long Ntot, int R,
+                       const double2* x, double2* xs, double2* part, int nsplit, double2* y, cudaStream_t s,
+                       cudaEvent_t ev0, cudaEvent_t ev1) {
+    const long long tot = Ntot * R;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((tot + th - 1) / th);
+    k_scale_cols<double2, double><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
+    if (ev0) cudaEventRecord(ev0, s);
+    switch (matvec_col_tile(R, Nmax, true)) {
+        case 1: launch_bt<double2, 1, 1>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        case 2: launch_bt<double2, 2, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        case 4: launch_bt<double2, 4, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        case 8: launch_bt<double2, 8, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        default: launch_bt<double2, 16, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+    }
+    if (ev1) cudaEventRecord(ev1, s);
+    k_finalize<double2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
+    g_msd_launches += 3;
+}
+
+void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
+                       const float2* G, const float* rf, const float2* lf, long long Ntot, int R,
+                       const float2* x, float2* xs, float2* part, int nsplit, float2* y, cudaStream_t s,
+                       cudaEvent_t ev0, cudaEvent_t ev1) {
+    const long long tot = Ntot * R;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((tot + th - 1) / th);
+    k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
+    if (ev0) cudaEventRecord(ev0, s);
+    switch (matvec_col_tile(R, Nmax, false)) {
+        case 1: launch_bt<float2, 1, 1>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        case 2: launch_bt<float2, 2, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        case 4: launch_bt<float2, 4, 4>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        case 8: launch_bt<float2, 8, 4>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+        default: launch_bt<float2, 16, 4>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
+    }
+    if (ev1) cudaEventRecord(ev1, s);
+    k_finalize<float2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
+    g_msd_launches += 3;
+}

@@ -1,0 +1,795 @@
+// C ABI of libmsd (declared in include/msd.h) and the host-side runtime:
+// problem plans (row/generator offsets, matvec work lists, reduction
+// chunks), device work buffers, and the restarted-GMRES driver that chains
+// the kernels of K3/K4 on the problem's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "msd_internal.cuh"
+
+// ---------------------------------------------------------------- launchers from other units
+
+int matvec_col_tile(int R, int Nmax, bool fp64);
+size_t matvec_smem_bytes(int R, int Nmax, bool fp64);
+
+// ---------------------------------------------------------------- errors
+
+std::atomic<long long> g_msd_launches{0};
+
+namespace {
+thread_local std::string g_err;
+
+struct MsdError {
+    msd_status st;
+};
+
+void fail(msd_status st, const std::string& msg) {
+    g_err = msg;
+    throw MsdError{st};
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError();                                                                   \
+            fail(e_ == cudaErrorMemoryAllocation ? MSD_ERR_OOM : MSD_ERR_CUDA,                    \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+        }                                                                                         \
+    } while (0)
+
+#define CK_LAUNCH() CK(cudaGetLastError())
+
+template <typename F>
+msd_status guarded(F&& f) {
+    try {
+        g_err.clear();
+        return f();
+    } catch (const MsdError& e) {
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        g_err = "host allocation failed";
+        return MSD_ERR_OOM;
+    } catch (...) {
+        g_err = "unexpected internal error";
+        return MSD_ERR_CUDA;
+    }
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Growable device buffer owned by the library.
+struct DBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    void* get(size_t bytes) {
+        if (bytes > cap) {
+            if (p) cudaFree(p);
+            p = nullptr;
+            cap = 0;
+            CK(cudaMalloc(&p, bytes ? bytes : 16));
+            cap = bytes;
+        }
+        return p;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+template <typename T>
+T* dalloc_copy(const T* h, size_t n) {
+    T* d = nullptr;
+    CK(cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T)));
+    if (n) CK(cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+}
+template <typename T>
+T* dalloc(size_t n) {
+    T* d = nullptr;
+    CK(cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T)));
+    return d;
+}
+
+const int kTargetCtas = 4 * 152;  // a few CTAs per SM of the GB300
+
+}  // namespace
+
+// ---------------------------------------------------------------- problem
+
+struct MatvecPlan {
+    std::vector<MatvecWork> work;
+    MatvecWork* d_work = nullptr;
+    int nsplit = 1;
+};
+
+struct msd_problem {
+    cudaStream_t stream = nullptr;
+    int C = 0, Mtot = 0, Nmax = 0, Mmax = 0;
+    long long Ntot = 0;
+    std::vector<MsdConfig> cfg;
+    MsdConfig* d_cfg = nullptr;
+    double2* d_centre = nullptr;
+    double* d_radius = nullptr;
+    int8_t* d_bc = nullptr;
+    int* d_disk_cfg = nullptr;
+    double2 *d_J = nullptr, *d_dJ = nullptr, *d_H = nullptr, *d_dH = nullptr;
+    double2 *d_lf64 = nullptr, *d_rhs_scale = nullptr;
+    double* d_rf64 = nullptr;
+    float2* d_lf32 = nullptr;
+    float* d_rf32 = nullptr;
+    int* d_flags = nullptr;
+    long long gen_elems = 0;
+    double2* d_G64 = nullptr;
+    float2* d_G32 = nullptr;
+    std::map<long long, MatvecPlan> plans;  // key: R*4 + precision
+    std::vector<RowChunk> chunks;
+    RowChunk* d_chunks = nullptr;
+    int* d_cfg_chunk_off = nullptr;
+    int* h_pinned = nullptr;  // small pinned host flags
+    DBuf xs, part, sbuf[24];
+    // algorithmic size of one product with one column (section 5 storage):
+    // sum over ordered pairs of the generator length, and of n^2
+    double offdiag_L = 0, offdiag_n2 = 0;
+    // optional timing of the block-Toeplitz kernel (msd_matvec_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    double timed_ms = 0, timed_flops = 0, timed_bytes = 0;
+    long long timed_launches = 0;
+};
+
+namespace {
+
+// Fold the recorded kernel-event pairs into the running totals.
+void flush_timing(msd_problem* pb) {
+    if (pb->ev_used == 0) return;
+    CK(cudaEventSynchronize(pb->events[pb->ev_used - 1]));
+    for (size_t i = 0; i + 1 < pb->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, pb->events[i], pb->events[i + 1]));
+        pb->timed_ms += ms;
+        pb->timed_launches += 1;
+    }
+    pb->ev_used = 0;
+}
+
+void check_flags(msd_problem* pb, const char* where) {
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, pb->d_flags, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
+    CK(cudaStreamSynchronize(pb->stream));
+    if (f & 1) fail(MSD_ERR_NONFINITE, std::string(where) + ": non-finite Bessel factor (k a_p at a zero of J_m for a Neumann disk?)");
+    if (f & 2) fail(MSD_ERR_RANGE, std::string(where) + ": a Hankel generator exceeds the complex64 range; use MSD_FP64");
+}
+
+void ensure_generators(msd_problem* pb, bool fp64) {
+    if (fp64 && pb->d_G64) return;
+    if (!fp64 && pb->d_G32) return;
+    if (fp64) pb->d_G64 = dalloc<double2>(pb->gen_elems);
+    else pb->d_G32 = dalloc<float2>(pb->gen_elems);
+    launch_pair_generators(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, fp64 ? pb->d_G64 : nullptr,
+                           fp64 ? nullptr : pb->d_G32, pb->d_flags, pb->stream);
+    CK_LAUNCH();
+    check_flags(pb, "pair generators");
+}
+
+MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
+    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
+    auto it = pb->plans.find(key);
+    if (it != pb->plans.end()) return it->second;
+    MatvecPlan plan;
+    const int RT = matvec_col_tile(R, pb->Nmax, fp64);
+    const int rtiles = R / RT;
+    long long tiles = 0;
+    for (auto& c : pb->cfg) tiles += c.Mp / MSD_TILE_P;
+    long long want = (kTargetCtas + tiles * rtiles - 1) / (tiles * rtiles);
+    int ns = (int)std::max<long long>(1, std::min<long long>(want, std::max(1, pb->Mmax / 4)));
+    // keep the partial-sum buffer within 2 GB
+    const size_t elem = fp64 ? 16 : 8;
+    while (ns > 1 && (size_t)ns * pb->Ntot * R * elem > (2ull << 30)) --ns;
+    plan.nsplit = ns;
+    for (int ci = 0; ci < pb->C; ++ci) {
+        const MsdConfig& c = pb->cfg[ci];
+        for (int p0 = 0; p0 < c.Mp; p0 += MSD_TILE_P)
+            for (int s = 0; s < ns; ++s) {
+                MatvecWork w;
+                w.cfg = ci;
+                w.p0 = p0;
+                w.q0 = (int)((long long)c.M * s / ns);
+                w.q1 = (int)((long long)c.M * (s + 1) / ns);
+                w.split = s;
+                w.pad = 0;
+                plan.work.push_back(w);
+            }
+    }
+    plan.d_work = dalloc_copy(plan.work.data(), plan.work.size());
+    return pb->plans.emplace(key, std::move(plan)).first->second;
+}
+
+// y = P^-1 A x on the problem's stream (device pointers).
+void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
+    if (matvec_smem_bytes(R, pb->Nmax, fp64) > 227 * 1024)
+        fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
+    ensure_generators(pb, fp64);
+    MatvecPlan& plan = get_plan(pb, R, fp64);
+    const size_t elem = fp64 ? 16 : 8;
+    void* xs = pb->xs.get((size_t)pb->Ntot * R * elem);
+    void* part = pb->part.get((size_t)plan.nsplit * pb->Ntot * R * elem);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (pb->timing) {
+        // events bracket the block-Toeplitz kernel alone (not the scaling or
+        // the split reduction around it)
+        while (pb->events.size() < 256) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            pb->events.push_back(e);
+        }
+        if (pb->ev_used + 2 > pb->events.size()) flush_timing(pb);  // waits, then reuses the pool
+        e0 = pb->events[pb->ev_used++];
+        e1 = pb->events[pb->ev_used++];
+        const double sc = fp64 ? 16.0 : 8.0;
+        pb->timed_flops += 8.0 * (double)R * pb->offdiag_n2;
+        pb->timed_bytes += sc * ((double)pb->offdiag_L + 2.0 * (double)pb->Ntot * R);
+    }
+    if (fp64)
+        launch_matvec_f64(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G64, pb->d_rf64,
+                          pb->d_lf64, pb->Ntot, R, (const double2*)x, (double2*)xs, (double2*)part,
+                          plan.nsplit, (double2*)y, pb->stream, e0, e1);
+    else
+        launch_matvec_f32(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G32, pb->d_rf32,
+                          pb->d_lf32, pb->Ntot, R, (const float2*)x, (float2*)xs, (float2*)part,
+                          plan.nsplit, (float2*)y, pb->stream, e0, e1);
+    CK_LAUNCH();
+}
+
+// Stage a caller buffer that may live on the host: returns a device pointer
+// (the caller's if it is device memory, else a library buffer filled from it).
+const void* stage_in(msd_problem* pb, DBuf& buf, const void* p, size_t bytes) {
+    if (is_device_ptr(p)) return p;
+    void* d = buf.get(bytes);
+    CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, pb->stream));
+    return d;
+}
+
+struct OutStage {
+    msd_problem* pb;
+    void* user;
+    void* dev;
+    size_t bytes;
+    bool host;
+    OutStage(msd_problem* pb_, DBuf& buf, void* p, size_t n) : pb(pb_), user(p), bytes(n) {
+        host = !is_device_ptr(p);
+        dev = host ? buf.get(n) : p;
+    }
+    void finish() {
+        if (host) {
+            CK(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, pb->stream));
+            CK(cudaStreamSynchronize(pb->stream));
+        }
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- GMRES driver
+
+namespace {
+
+struct SolveCtx {
+    msd_problem* pb;
+    GmresDims d;
+    int m;
+    // FP64 vectors [Ntot][R]
+    double2 *b, *x, *r, *Ax;
+    // per-system arrays
+    double2 *h1, *h2, *wn2, *H, *cs, *sn, *g, *y;
+    double *beta, *vscale, *tol_abs, *tol_cycle;
+    int *active, *kconv, *iters, *flags;  // flags[0] any_active, flags[1] nonfinite
+    int hstride;
+};
+
+template <typename V>
+void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* steps_taken) {
+    msd_problem* pb = cx.pb;
+    cudaStream_t s = pb->stream;
+    const GmresDims& d = cx.d;
+    const long long vstride = pb->Ntot * d.R;
+    double2* part = (double2*)pb->sbuf[0].get((size_t)d.nchunk * (cx.m + 1) * d.R * sizeof(double2));
+    // r . r -> rr (reuse wn2)
+    gm_multidot<double2>(d, pb->d_chunks, pb->d_cfg_chunk_off, cx.r, vstride, 1, cx.r, part, cx.wn2,
+                         cx.hstride, 0, s);
+    CK(cudaMemsetAsync(cx.flags, 0, 2 * sizeof(int), s));
+    gm_start(d, cx.wn2, cx.hstride, cx.tol_abs, cx.beta, cx.vscale, cx.g, cx.active, cx.kconv, cx.flags, s);
+    gm_scale<double2, V>(d, pb->d_chunks, cx.r, cx.vscale, cx.active, Vb, s);
+    CK_LAUNCH();
+    int any = 0;
+    CK(cudaMemcpyAsync(pb->h_pinned, cx.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    any = pb->h_pinned[0];
+    int j = 0;
+    for (; any && j < cx.m && j < maxit_left; ++j) {
+        V* vj = Vb + (long long)j * vstride;
+        matvec_dev(pb, d.R, fp64, vj, w);
+        gm_multidot<V>(d, pb->d_chunks, pb->d_cfg_chunk_off, Vb, vstride, j + 1, w, part, cx.h1, cx.hstride, 0, s);
+        gm_update<V>(d, pb->d_chunks, Vb, vstride, j + 1, cx.h1, cx.hstride, w, s);
+        gm_multidot<V>(d, pb->d_chunks, pb->d_cfg_chunk_off, Vb, vstride, j + 1, w, part, cx.h2, cx.hstride, 0, s);
+        gm_update<V>(d, pb->d_chunks, Vb, vstride, j + 1, cx.h2, cx.hstride, w, s);
+        gm_multidot<V>(d, pb->d_chunks, pb->d_cfg_chunk_off, w, vstride, 1, w, part, cx.wn2, cx.hstride, 0, s);
+        CK(cudaMemsetAsync(cx.flags, 0, sizeof(int), s));
+        // a step that would exceed the iteration budget ends the cycle for everyone
+        gm_givens(d, j, cx.h1, cx.h2, cx.hstride, cx.wn2, cx.tol_cycle, cx.H, cx.cs, cx.sn, cx.g, cx.vscale,
+                  cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, s);
+        gm_scale<V, V>(d, pb->d_chunks, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(pb->h_pinned, cx.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        any = pb->h_pinned[0];
+        if (pb->h_pinned[1]) fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+    }
+    if (any) {
+        // budget exhausted mid-cycle: close the still-active systems at j columns
+        // (their kconv is set here; converged ones keep theirs)
+        std::vector<int> act(d.S), kc(d.S);
+        CK(cudaMemcpyAsync(act.data(), cx.active, d.S * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(kc.data(), cx.kconv, d.S * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < d.S; ++i)
+            if (act[i]) kc[i] = j;
+        CK(cudaMemcpyAsync(cx.kconv, kc.data(), d.S * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    *steps_taken = j;
+    gm_lsq(d, cx.H, cx.g, cx.kconv, cx.y, s);
+    gm_xupdate<V>(d, pb->d_chunks, Vb, vstride, cx.y, cx.kconv, cx.x, s);
+    CK_LAUNCH();
+}
+
+msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts_in,
+                      void* rho_out, msd_stats* stats_host) {
+    if (!pb || R <= 0 || !betas_host || !rho_out) fail(MSD_ERR_ARG, "msd_solve_planewaves: bad argument");
+    msd_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts_in) o = *opts_in;
+    if (o.tol <= 0) o.tol = 1e-10;
+    if (o.restart <= 0) o.restart = 100;
+    if (o.maxit <= 0) o.maxit = 3000;
+    if (o.max_refine <= 0) o.max_refine = 60;
+    if (o.inner_tol <= 0) o.inner_tol = 2e-6;
+    if (o.precision != MSD_FP64 && o.precision != MSD_MIXED) fail(MSD_ERR_ARG, "msd_solve_planewaves: precision");
+    const bool mixed = o.precision == MSD_MIXED;
+    cudaStream_t s = pb->stream;
+
+    SolveCtx cx;
+    cx.pb = pb;
+    cx.m = o.restart;
+    cx.d.Ntot = pb->Ntot;
+    cx.d.R = R;
+    cx.d.C = pb->C;
+    cx.d.S = pb->C * R;
+    cx.d.m = o.restart;
+    cx.d.nchunk = (int)pb->chunks.size();
+    cx.hstride = o.restart + 2;
+    const int S = cx.d.S, m = o.restart;
+    const size_t nv = (size_t)pb->Ntot * R;
+
+    int bi = 1;
+    auto sb = [&](size_t bytes) { return pb->sbuf[bi++].get(bytes); };
+    cx.b = (double2*)sb(nv * 16);
+    cx.x = (double2*)sb(nv * 16);
+    cx.r = (double2*)sb(nv * 16);
+    cx.Ax = (double2*)sb(nv * 16);
+    cx.h1 = (double2*)sb((size_t)S * cx.hstride * 16);
+    cx.h2 = (double2*)sb((size_t)S * cx.hstride * 16);
+    cx.wn2 = (double2*)sb((size_t)S * cx.hstride * 16);
+    cx.H = (double2*)sb((size_t)S * m * (m + 1) * 16);
+    cx.cs = (double2*)sb((size_t)S * m * 16);
+    cx.sn = (double2*)sb((size_t)S * m * 16);
+    cx.g = (double2*)sb((size_t)S * (m + 1) * 16);
+    cx.y = (double2*)sb((size_t)S * m * 16);
+    double* dsys = (double*)sb((size_t)S * 4 * 8);
+    cx.beta = dsys;
+    cx.vscale = dsys + S;
+    cx.tol_abs = dsys + 2 * S;
+    cx.tol_cycle = dsys + 3 * S;
+    int* isys = (int*)sb((size_t)(S * 3 + 2) * 4);
+    cx.active = isys;
+    cx.kconv = isys + S;
+    cx.iters = isys + 2 * S;
+    cx.flags = isys + 3 * S;
+    const size_t velem = mixed ? 8 : 16;
+    void* Vb = sb((size_t)(m + 1) * nv * velem);
+    void* w = sb(nv * velem);
+    double* d_betas = (double*)sb((size_t)pb->C * R * 8);
+    double2* part = (double2*)pb->sbuf[0].get((size_t)cx.d.nchunk * (m + 1) * R * sizeof(double2));
+
+    CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
+    launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
+                         pb->Nmax, R, d_betas, cx.b, s);
+    CK_LAUNCH();
+    ensure_generators(pb, true);
+    if (mixed) ensure_generators(pb, false);
+    gm_zero(nv, cx.x, s);
+    CK(cudaMemsetAsync(cx.iters, 0, S * sizeof(int), s));
+    // ||b|| per system
+    gm_multidot<double2>(cx.d, pb->d_chunks, pb->d_cfg_chunk_off, cx.b, nv, 1, cx.b, part, cx.wn2, cx.hstride, 0, s);
+    std::vector<double2> hb((size_t)S * cx.hstride);
+    CK(cudaMemcpyAsync(hb.data(), cx.wn2, hb.size() * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> bnorm(S), tol_abs(S), relres(S, 1.0), prev(S, 1e300), tol_cycle(S);
+    for (int i = 0; i < S; ++i) {
+        bnorm[i] = std::sqrt(std::max(hb[(size_t)i * cx.hstride].x, 0.0));
+        tol_abs[i] = o.tol * bnorm[i];
+        if (!std::isfinite(bnorm[i])) fail(MSD_ERR_NONFINITE, "right-hand side is not finite");
+    }
+    CK(cudaMemcpyAsync(cx.tol_abs, tol_abs.data(), S * 8, cudaMemcpyHostToDevice, s));
+
+    int total = 0, sweeps = 0;
+    bool stagnated = false;
+    const int max_sweeps = mixed ? o.max_refine : 1 << 30;
+    while (true) {
+        // FP64 residual of the current iterate
+        if (sweeps == 0) {
+            CK(cudaMemcpyAsync(cx.r, cx.b, nv * 16, cudaMemcpyDeviceToDevice, s));
+        } else {
+            matvec_dev(pb, R, true, cx.x, cx.Ax);
+            gm_residual(nv, cx.b, cx.Ax, cx.r, s);
+        }
+        gm_multidot<double2>(cx.d, pb->d_chunks, pb->d_cfg_chunk_off, cx.r, nv, 1, cx.r, part, cx.wn2,
+                             cx.hstride, 0, s);
+        CK(cudaMemcpyAsync(hb.data(), cx.wn2, hb.size() * 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool all = true, improved = false;
+        for (int i = 0; i < S; ++i) {
+            const double rn = std::sqrt(std::max(hb[(size_t)i * cx.hstride].x, 0.0));
+            if (!std::isfinite(rn)) fail(MSD_ERR_NONFINITE, "GMRES: non-finite residual");
+            relres[i] = bnorm[i] > 0 ? rn / bnorm[i] : 0.0;
+            if (relres[i] > o.tol) {
+                all = false;
+                // a sweep that leaves the FP64 residual of every unconverged
+                // system where it was has stagnated (FP32 sweeps can stall
+                // on the rounding of the inner product)
+                if (relres[i] < (1.0 - 1e-3) * prev[i]) improved = true;
+            }
+            tol_cycle[i] = mixed ? std::max(tol_abs[i], o.inner_tol * rn) : tol_abs[i];
+        }
+        if (all) break;
+        if (mixed && sweeps > 0 && !improved) {
+            stagnated = true;
+            break;
+        }
+        if (sweeps >= max_sweeps || total >= o.maxit) break;
+        prev = relres;
+        CK(cudaMemcpyAsync(cx.tol_cycle, tol_cycle.data(), S * 8, cudaMemcpyHostToDevice, s));
+        int steps = 0;
+        if (mixed)
+            arnoldi_cycle<float2>(cx, (float2*)Vb, (float2*)w, false, o.maxit - total, &steps);
+        else
+            arnoldi_cycle<double2>(cx, (double2*)Vb, (double2*)w, true, o.maxit - total, &steps);
+        total += steps;
+        ++sweeps;
+        if (steps == 0) break;
+    }
+
+    // densities out
+    {
+        const size_t bytes = nv * 16;
+        if (is_device_ptr(rho_out)) {
+            CK(cudaMemcpyAsync(rho_out, cx.x, bytes, cudaMemcpyDeviceToDevice, s));
+        } else {
+            CK(cudaMemcpyAsync(rho_out, cx.x, bytes, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    std::vector<int> it(S);
+    CK(cudaMemcpyAsync(it.data(), cx.iters, S * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    msd_status st = MSD_OK;
+    for (int i = 0; i < S; ++i) {
+        int flag = relres[i] <= o.tol ? MSD_OK : (stagnated ? MSD_STAGNATED : MSD_NOT_CONVERGED);
+        if (flag != MSD_OK && st == MSD_OK) st = (msd_status)flag;
+        if (stats_host) {
+            stats_host[i].flag = flag;
+            stats_host[i].iters = it[i];
+            stats_host[i].refine_steps = sweeps > 0 ? sweeps - 1 : 0;
+            stats_host[i].reserved = 0;
+            stats_host[i].relres = relres[i];
+        }
+    }
+    return st;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* msd_last_error(void) { return g_err.c_str(); }
+
+msd_status msd_create(int C, const int* disk_off, const double* centres, const double* radii,
+                      const int8_t* bc, const double* k, const int* N, void* cuda_stream, msd_problem** out) {
+    return guarded([&]() -> msd_status {
+        if (!out) fail(MSD_ERR_ARG, "msd_create: out is NULL");
+        *out = nullptr;
+        if (C < 1 || !disk_off || !centres || !radii || !bc || !k || !N)
+            fail(MSD_ERR_ARG, "msd_create: bad argument");
+        if (disk_off[0] != 0) fail(MSD_ERR_ARG, "msd_create: disk_off[0] must be 0");
+        for (int c = 0; c < C; ++c) {
+            if (disk_off[c + 1] <= disk_off[c]) fail(MSD_ERR_ARG, "msd_create: every configuration needs a disk");
+            if (!(k[c] > 0) || !std::isfinite(k[c])) fail(MSD_ERR_ARG, "msd_create: k must be positive");
+            if (N[c] < 1 || N[c] > MSD_MAX_N) fail(MSD_ERR_ARG, "msd_create: N out of range");
+        }
+        const int Mtot = disk_off[C];
+        for (int d = 0; d < Mtot; ++d) {
+            if (!(radii[d] > 0) || !std::isfinite(radii[d]) || !std::isfinite(centres[2 * d]) ||
+                !std::isfinite(centres[2 * d + 1]))
+                fail(MSD_ERR_ARG, "msd_create: radii must be positive and centres finite");
+            if (bc[d] != MSD_DIRICHLET && bc[d] != MSD_NEUMANN) fail(MSD_ERR_ARG, "msd_create: bc flag");
+        }
+        // overlap test (disjoint closed disks), per configuration: sort by x, sweep
+        for (int c = 0; c < C; ++c) {
+            const int a0 = disk_off[c], a1 = disk_off[c + 1];
+            std::vector<int> idx(a1 - a0);
+            double rmax = 0;
+            for (int i = a0; i < a1; ++i) {
+                idx[i - a0] = i;
+                rmax = std::max(rmax, radii[i]);
+            }
+            std::sort(idx.begin(), idx.end(), [&](int u, int v) { return centres[2 * u] < centres[2 * v]; });
+            for (size_t i = 0; i < idx.size(); ++i)
+                for (size_t j = i + 1; j < idx.size(); ++j) {
+                    const int u = idx[i], v = idx[j];
+                    const double dx = centres[2 * v] - centres[2 * u];
+                    if (dx > 2 * rmax) break;
+                    const double dy = centres[2 * v + 1] - centres[2 * u + 1];
+                    if (std::hypot(dx, dy) <= radii[u] + radii[v])
+                        fail(MSD_ERR_OVERLAP, "msd_create: disks " + std::to_string(u) + " and " +
+                                                  std::to_string(v) + " intersect");
+                }
+        }
+        msd_problem* pb = new msd_problem();
+        try {
+            pb->stream = (cudaStream_t)cuda_stream;
+            pb->C = C;
+            pb->Mtot = Mtot;
+            long long row = 0, gen = 0;
+            std::vector<int> disk_cfg(Mtot);
+            for (int c = 0; c < C; ++c) {
+                MsdConfig m;
+                memset(&m, 0, sizeof(m));
+                m.k = k[c];
+                m.N = N[c];
+                m.n = 2 * N[c] + 1;
+                m.L = 4 * N[c] + 1;
+                m.M = disk_off[c + 1] - disk_off[c];
+                m.Mp = (m.M + MSD_TILE_P - 1) / MSD_TILE_P * MSD_TILE_P;
+                m.disk_off = disk_off[c];
+                m.row_off = row;
+                m.gen_off = gen;
+                row += (long long)m.M * m.n;
+                gen += (long long)m.M * m.Mp * m.L;
+                pb->offdiag_L += (double)m.M * (m.M - 1) * m.L;
+                pb->offdiag_n2 += (double)m.M * (m.M - 1) * (double)m.n * m.n;
+                pb->cfg.push_back(m);
+                pb->Nmax = std::max(pb->Nmax, m.N);
+                pb->Mmax = std::max(pb->Mmax, m.M);
+                for (int d = disk_off[c]; d < disk_off[c + 1]; ++d) disk_cfg[d] = c;
+            }
+            pb->Ntot = row;
+            pb->gen_elems = gen;
+            std::vector<double2> cen(Mtot);
+            for (int d = 0; d < Mtot; ++d) cen[d] = make_double2(centres[2 * d], centres[2 * d + 1]);
+            pb->d_cfg = dalloc_copy(pb->cfg.data(), C);
+            pb->d_centre = dalloc_copy(cen.data(), Mtot);
+            pb->d_radius = dalloc_copy(radii, Mtot);
+            pb->d_bc = dalloc_copy(bc, Mtot);
+            pb->d_disk_cfg = dalloc_copy(disk_cfg.data(), Mtot);
+            pb->d_J = dalloc<double2>(row);
+            pb->d_dJ = dalloc<double2>(row);
+            pb->d_H = dalloc<double2>(row);
+            pb->d_dH = dalloc<double2>(row);
+            pb->d_lf64 = dalloc<double2>(row);
+            pb->d_rhs_scale = dalloc<double2>(row);
+            pb->d_rf64 = dalloc<double>(row);
+            pb->d_lf32 = dalloc<float2>(row);
+            pb->d_rf32 = dalloc<float>(row);
+            pb->d_flags = dalloc<int>(4);
+            CK(cudaMemsetAsync(pb->d_flags, 0, 4 * sizeof(int), pb->stream));
+            CK(cudaMallocHost((void**)&pb->h_pinned, 64));
+            // reduction chunks: ~kTargetCtas chunks overall, never across configurations
+            const long long target_rows = std::max<long long>(256, row / kTargetCtas);
+            std::vector<int> coff(C + 1, 0);
+            for (int c = 0; c < C; ++c) {
+                const MsdConfig& m = pb->cfg[c];
+                const long long rows = (long long)m.M * m.n;
+                for (long long r0 = 0; r0 < rows; r0 += target_rows) {
+                    RowChunk ch;
+                    ch.cfg = c;
+                    ch.pad = 0;
+                    ch.row0 = m.row_off + r0;
+                    ch.row1 = m.row_off + std::min(rows, r0 + target_rows);
+                    pb->chunks.push_back(ch);
+                }
+                coff[c + 1] = (int)pb->chunks.size();
+            }
+            pb->d_chunks = dalloc_copy(pb->chunks.data(), pb->chunks.size());
+            pb->d_cfg_chunk_off = dalloc_copy(coff.data(), coff.size());
+            launch_disk_diagonals(pb->d_cfg, Mtot, pb->d_disk_cfg, pb->d_radius, pb->d_bc, pb->Nmax, pb->d_J,
+                                  pb->d_dJ, pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rf64, pb->d_lf32, pb->d_rf32,
+                                  pb->d_rhs_scale, pb->d_flags, pb->stream);
+            CK_LAUNCH();
+            check_flags(pb, "disk diagonals");
+        } catch (...) {
+            msd_destroy(pb);
+            throw;
+        }
+        *out = pb;
+        return MSD_OK;
+    });
+}
+
+void msd_destroy(msd_problem* pb) {
+    if (!pb) return;
+    if (pb->stream) cudaStreamSynchronize(pb->stream);
+    void* ptrs[] = {pb->d_cfg, pb->d_centre, pb->d_radius, pb->d_bc, pb->d_disk_cfg, pb->d_J, pb->d_dJ,
+                    pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rhs_scale, pb->d_rf64, pb->d_lf32, pb->d_rf32,
+                    pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& kv : pb->plans)
+        if (kv.second.d_work) cudaFree(kv.second.d_work);
+    if (pb->h_pinned) cudaFreeHost(pb->h_pinned);
+    for (cudaEvent_t e : pb->events) cudaEventDestroy(e);
+    pb->xs.release();
+    pb->part.release();
+    for (auto& b : pb->sbuf) b.release();
+    delete pb;
+}
+
+int64_t msd_num_unknowns(const msd_problem* pb) { return pb ? pb->Ntot : -1; }
+
+int64_t msd_row_offset(const msd_problem* pb, int config) {
+    if (!pb || config < 0 || config > pb->C) return -1;
+    return config == pb->C ? pb->Ntot : pb->cfg[config].row_off;
+}
+
+msd_status msd_disk_diagonals(msd_problem* pb, void* out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !out) fail(MSD_ERR_ARG, "msd_disk_diagonals: bad argument");
+        const size_t bytes = (size_t)pb->Ntot * 16;
+        OutStage o(pb, pb->sbuf[20], out, 4 * bytes);
+        const double2* src[4] = {pb->d_J, pb->d_dJ, pb->d_H, pb->d_dH};
+        for (int i = 0; i < 4; ++i)
+            CK(cudaMemcpyAsync((char*)o.dev + i * bytes, src[i], bytes, cudaMemcpyDeviceToDevice, pb->stream));
+        o.finish();
+        return MSD_OK;
+    });
+}
+
+msd_status msd_pair_generators(msd_problem* pb, int config, void* out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !out || config < 0 || config >= pb->C) fail(MSD_ERR_ARG, "msd_pair_generators: bad argument");
+        ensure_generators(pb, true);
+        const MsdConfig& c = pb->cfg[config];
+        const size_t rowb = (size_t)c.M * c.L * 16;
+        OutStage o(pb, pb->sbuf[20], out, rowb * c.M);
+        CK(cudaMemcpy2DAsync(o.dev, rowb, pb->d_G64 + c.gen_off, (size_t)c.Mp * c.L * 16, rowb, c.M,
+                             cudaMemcpyDeviceToDevice, pb->stream));
+        o.finish();
+        return MSD_OK;
+    });
+}
+
+msd_status msd_rhs_planewave(msd_problem* pb, int R, const double* betas_host, void* out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || !betas_host || !out) fail(MSD_ERR_ARG, "msd_rhs_planewave: bad argument");
+        double* d_betas = (double*)pb->sbuf[21].get((size_t)pb->C * R * 8);
+        CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, pb->stream));
+        OutStage o(pb, pb->sbuf[20], out, (size_t)pb->Ntot * R * 16);
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
+                             pb->Nmax, R, d_betas, (double2*)o.dev, pb->stream);
+        CK_LAUNCH();
+        o.finish();
+        return MSD_OK;
+    });
+}
+
+msd_status msd_matvec(msd_problem* pb, int R, int precision, const void* x_dev, void* y_dev) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || !x_dev || !y_dev) fail(MSD_ERR_ARG, "msd_matvec: bad argument");
+        if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_matvec: precision");
+        if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev)) fail(MSD_ERR_ARG, "msd_matvec: x and y must be device memory");
+        if (x_dev == y_dev) fail(MSD_ERR_ARG, "msd_matvec: x and y must not overlap");
+        matvec_dev(pb, R, precision == MSD_FP64, x_dev, y_dev);
+        return MSD_OK;
+    });
+}
+
+msd_status msd_solve_planewaves(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts,
+                                void* rho_out, msd_stats* stats_host) {
+    return guarded([&]() -> msd_status { return solve_impl(pb, R, betas_host, opts, rho_out, stats_host); });
+}
+
+msd_status msd_update_geometry(msd_problem* pb, const double* centres, const double* radii, const double* k_host) {
+    return guarded([&]() -> msd_status {
+        if (!pb) fail(MSD_ERR_ARG, "msd_update_geometry: bad handle");
+        if (k_host) {
+            for (int c = 0; c < pb->C; ++c) {
+                if (!(k_host[c] > 0) || !std::isfinite(k_host[c])) fail(MSD_ERR_ARG, "msd_update_geometry: k must be positive");
+                pb->cfg[c].k = k_host[c];
+            }
+            CK(cudaMemcpyAsync(pb->d_cfg, pb->cfg.data(), pb->C * sizeof(MsdConfig), cudaMemcpyHostToDevice, pb->stream));
+        }
+        if (centres)
+            CK(cudaMemcpyAsync(pb->d_centre, centres, (size_t)pb->Mtot * 16,
+                               is_device_ptr(centres) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pb->stream));
+        if (radii)
+            CK(cudaMemcpyAsync(pb->d_radius, radii, (size_t)pb->Mtot * 8,
+                               is_device_ptr(radii) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pb->stream));
+        CK(cudaMemsetAsync(pb->d_flags, 0, sizeof(int), pb->stream));
+        launch_disk_diagonals(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_radius, pb->d_bc, pb->Nmax, pb->d_J,
+                              pb->d_dJ, pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rf64, pb->d_lf32, pb->d_rf32,
+                              pb->d_rhs_scale, pb->d_flags, pb->stream);
+        CK_LAUNCH();
+        if (pb->d_G64 || pb->d_G32)
+            launch_pair_generators(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_G64, pb->d_G32,
+                                   pb->d_flags, pb->stream);
+        CK_LAUNCH();
+        check_flags(pb, "msd_update_geometry");
+        return MSD_OK;
+    });
+}
+
+msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int64_t* launches,
+                             double* flops, double* bytes) {
+    return guarded([&]() -> msd_status {
+        if (!pb) fail(MSD_ERR_ARG, "msd_matvec_timing: bad handle");
+        flush_timing(pb);
+        if (kernel_ms) *kernel_ms = pb->timed_ms;
+        if (launches) *launches = pb->timed_launches;
+        if (flops) *flops = pb->timed_flops;
+        if (bytes) *bytes = pb->timed_bytes;
+        if (enable >= 0) {
+            pb->timing = enable != 0;
+            pb->timed_ms = pb->timed_flops = pb->timed_bytes = 0;
+            pb->timed_launches = 0;
+        }
+        return MSD_OK;
+    });
+}
+
+int64_t msd_kernel_launches(void) { return g_msd_launches.load(); }
+
+msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T, const double* thetas_host, void* F_out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !rho || R <= 0 || T <= 0 || !thetas_host || !F_out) fail(MSD_ERR_ARG, "msd_farfield: bad argument");
+        double* d_th = (double*)pb->sbuf[21].get((size_t)T * 8);
+        CK(cudaMemcpyAsync(d_th, thetas_host, (size_t)T * 8, cudaMemcpyHostToDevice, pb->stream));
+        const double2* d_rho = (const double2*)stage_in(pb, pb->sbuf[22], rho, (size_t)pb->Ntot * R * 16);
+        OutStage o(pb, pb->sbuf[23], F_out, (size_t)pb->C * T * R * 16);
+        launch_farfield(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_radius, pb->d_J, R, T, d_th, d_rho,
+                        nullptr, (double2*)o.dev, pb->stream);
+        CK_LAUNCH();
+        o.finish();
+        return MSD_OK;
+    });
+}
+
+}  // extern "C"

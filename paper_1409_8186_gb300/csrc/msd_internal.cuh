@@ -1,0 +1,165 @@
+// Internal declarations shared by the CUDA translation units of libmsd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/msd.h"
+
+// ---------------------------------------------------------------- complex helpers
+
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
+    return make_double2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) {
+    return make_double2(a.x * s, a.y * s);
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm (avoids overflow of |b|^2 for large |b|)
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.y + b.x * r;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+__host__ __device__ __forceinline__ double2 cinv(double2 b) { return cdiv(make_double2(1.0, 0.0), b); }
+
+// acc += a * b (complex multiply-accumulate, 4 FMAs)
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------- problem layout
+
+// One batched configuration.  Rows of configuration c occupy
+// [row_off, row_off + M*n); generators of c occupy M*Mp*L complex values
+// starting at gen_off, laid out [q][p][l + 2N] with p padded to Mp.
+struct MsdConfig {
+    double k;
+    int N, n, L;      // truncation, modes per disk (2N+1), generator length (4N+1)
+    int M, Mp;        // disks, disks padded to a multiple of 32
+    int disk_off;     // first global disk index
+    int pad0;
+    long long row_off;  // first unknown row
+    long long gen_off;  // first generator element
+};
+
+// One CTA of the block-Toeplitz product: a tile of 32 target disks
+// [p0, p0+32) of configuration cfg, summed over sources [q0, q1), writing
+// its raw sums into partial slot `split`.
+struct MatvecWork {
+    int cfg, p0, q0, q1, split, pad;
+};
+
+// A contiguous range of rows of one configuration (reduction chunk).
+struct RowChunk {
+    int cfg;
+    int pad;
+    long long row0, row1;
+};
+
+#define MSD_TILE_P 32
+
+// Number of kernels the library has launched (host-side counter, all threads).
+extern std::atomic<long long> g_msd_launches;
+
+// ---------------------------------------------------------------- launchers (one per kernel family)
+
+// K1: Bessel diagonals and the row/column factors of the preconditioned operator.
+void launch_disk_diagonals(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
+                           const double* d_radius, const int8_t* d_bc, int Nmax,
+                           double2* J, double2* dJ, double2* H, double2* dH,
+                           double2* lf64, double* rf64, float2* lf32, float* rf32,
+                           double2* rhs_scale, int* d_flags, cudaStream_t s);
+
+// K2: Toeplitz generators of every ordered pair, complex128 and/or complex64.
+void launch_pair_generators(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
+                            const double2* d_centre, double2* G64, float2* G32,
+                            int* d_flags, cudaStream_t s);
+
+// K5: preconditioned plane-wave right-hand sides.
+void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
+                          const double2* d_centre, const double* d_radius,
+                          const double2* rhs_scale, int Nmax, int R, const double* d_betas,
+                          double2* out, cudaStream_t s);
+
+// K3: block-Toeplitz product y = x + l .* sum_q T(g^pq) (r .* x).
+void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
+                       const double2* G, const double* rf, const double2* lf, long long Ntot,
+                       int R, const double2* x, double2* xs, double2* part, int nsplit,
+                       double2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
+                       const float2* G, const float* rf, const float2* lf, long long Ntot,
+                       int R, const float2* x, float2* xs, float2* part, int nsplit,
+                       float2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+
+// K6: far field.
+void launch_farfield(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
+                     const double2* d_centre, const double* d_radius, const double2* J,
+                     int R, int T, const double* d_thetas, const double2* rho,
+                     double2* part, double2* F, cudaStream_t s);
+
+// ---------------------------------------------------------------- K4 (GMRES) pieces
+// A "system" is one (configuration, column) pair: s = cfg*R + r.
+
+struct GmresDims {
+    long long Ntot;   // rows
+    int R;            // columns
+    int C;            // configurations
+    int S;            // systems = C*R
+    int m;            // restart length
+    int nchunk;       // reduction chunks
+};
+
+// h[s][i] = sum over the rows of cfg(s) of conj(V_i[row][r]) w[row][r], i < nv (FP64 sums).
+template <typename V>
+void gm_multidot(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb,
+                 long long vstride, int nv, const V* w, double2* part, double2* h, int hstride,
+                 int accumulate, cudaStream_t s);
+// w[row][r] -= sum_i V_i[row][r] h[s][i]
+template <typename V>
+void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv,
+               const double2* h, int hstride, V* w, cudaStream_t s);
+// v = w * scale[s] for active systems, 0 otherwise
+template <typename Vin, typename Vout>
+void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale,
+              const int* active, Vout* v, cudaStream_t s);
+// x[row][r] += sum_{i < kconv[s]} V_i[row][r] y[s][i]
+template <typename V>
+void gm_xupdate(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride,
+                const double2* y, const int* kconv, double2* x, cudaStream_t s);
+void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* tol_abs, double* beta,
+              double* vscale, double2* g, int* active, int* kconv, int* any_active, cudaStream_t s);
+void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride,
+               const double2* wn2, const double* tol_cycle, double2* H, double2* cs, double2* sn,
+               double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
+               int* nonfinite, cudaStream_t s);
+void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y,
+            cudaStream_t s);
+void gm_residual(long long n, const double2* b, const double2* Ax, double2* r, cudaStream_t s);
+void gm_zero(long long n, double2* x, cudaStream_t s);
+void gm_cast_f32(long long n, const double2* a, float2* b, cudaStream_t s);

@@ -1,0 +1,292 @@
+"""Thin Python binding of libmsd's C ABI (include/msd.h).
+
+Functions named ``msd_*`` mirror the C entry points one to one and only
+marshal arguments (NumPy arrays for host data, torch tensors for device
+memory and the current CUDA stream).  ``Problem`` bundles the handle with
+the geometry it was created from.  Every computation runs in the CUDA
+library; if ``libmsd.so`` cannot be loaded this module raises at import.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmsd.so")
+
+MSD_OK = 0
+MSD_NOT_CONVERGED = 1
+MSD_STAGNATED = 3
+MSD_DIRICHLET, MSD_NEUMANN = 0, 1
+MSD_FP64, MSD_MIXED, MSD_FP32 = 0, 1, 2
+MSD_GEN_AUTO, MSD_GEN_STREAMED, MSD_GEN_RECOMPUTE = 0, 1, 2
+MSD_MAX_N = 63
+
+STATUS_NAMES = {0: "MSD_OK", 1: "MSD_NOT_CONVERGED", 3: "MSD_STAGNATED", -1: "MSD_ERR_ARG",
+                -2: "MSD_ERR_OVERLAP", -3: "MSD_ERR_CUDA", -4: "MSD_ERR_OOM",
+                -5: "MSD_ERR_NONFINITE", -6: "MSD_ERR_RANGE"}
+
+
+class MsdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class msd_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("precision", ctypes.c_int), ("gen_mode", ctypes.c_int)]
+
+
+class msd_stats(ctypes.Structure):
+    _fields_ = [("flag", ctypes.c_int), ("iters", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("relres", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libmsd.so not built ({_LIB_PATH}); run paper_1409_8186_gb300.build.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    sig = {
+        "msd_create": (I, [I, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_void_p)]),
+        "msd_destroy": (V, [P]),
+        "msd_num_unknowns": (ctypes.c_int64, [P]),
+        "msd_row_offset": (ctypes.c_int64, [P, I]),
+        "msd_disk_diagonals": (I, [P, P]),
+        "msd_pair_generators": (I, [P, I, P]),
+        "msd_rhs_planewave": (I, [P, I, P, P]),
+        "msd_matvec": (I, [P, I, I, P, P]),
+        "msd_solve_planewaves": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P]),
+        "msd_farfield": (I, [P, P, I, I, P, P]),
+        "msd_update_geometry": (I, [P, P, P, P]),
+        "msd_matvec_timing": (I, [P, I, P, P, P, P]),
+        "msd_kernel_launches": (ctypes.c_int64, []),
+        "msd_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "msd_disk_diagonals",
+            "msd_pair_generators", "msd_rhs_planewave", "msd_matvec", "msd_solve_planewaves",
+            "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
+            "msd_last_error")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _check(st: int, allow_positive: bool = False) -> int:
+    if st < 0 or (st > 0 and not allow_positive):
+        raise MsdError(st, msd_last_error())
+    return st
+
+
+def _ptr(a) -> int:
+    """Address of a NumPy array or a torch tensor (host or device)."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------- C entry points
+
+def msd_last_error() -> str:
+    return _lib.msd_last_error().decode()
+
+
+def msd_create(disk_off, centres, radii, bc, k, N, stream=None) -> int:
+    disk_off = np.ascontiguousarray(disk_off, dtype=np.int32)
+    centres = np.ascontiguousarray(centres, dtype=np.float64)
+    radii = np.ascontiguousarray(radii, dtype=np.float64)
+    bc = np.ascontiguousarray(bc, dtype=np.int8)
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(_lib.msd_create(len(k), _ptr(disk_off), _ptr(centres), _ptr(radii), _ptr(bc), _ptr(k),
+                           _ptr(N), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def msd_destroy(h) -> None:
+    _lib.msd_destroy(h)
+
+
+def msd_num_unknowns(h) -> int:
+    return int(_lib.msd_num_unknowns(h))
+
+
+def msd_row_offset(h, config: int) -> int:
+    return int(_lib.msd_row_offset(h, config))
+
+
+def msd_disk_diagonals(h, out) -> None:
+    _check(_lib.msd_disk_diagonals(h, _ptr(out)))
+
+
+def msd_pair_generators(h, config: int, out) -> None:
+    _check(_lib.msd_pair_generators(h, config, _ptr(out)))
+
+
+def msd_rhs_planewave(h, R: int, betas, out) -> None:
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    _check(_lib.msd_rhs_planewave(h, R, _ptr(betas), _ptr(out)))
+
+
+def msd_matvec(h, R: int, precision: int, x, y) -> None:
+    _check(_lib.msd_matvec(h, R, precision, _ptr(x), _ptr(y)))
+
+
+def msd_solve_planewaves(h, R: int, betas, opts: msd_opts | None, rho_out, stats_out=None) -> int:
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    return _check(_lib.msd_solve_planewaves(h, R, _ptr(betas), ctypes.byref(opts) if opts else None,
+                                            _ptr(rho_out), ctypes.addressof(stats_out) if stats_out is not None else None),
+                  allow_positive=True)
+
+
+def msd_farfield(h, rho, R: int, thetas, F_out) -> None:
+    thetas = np.ascontiguousarray(thetas, dtype=np.float64)
+    _check(_lib.msd_farfield(h, _ptr(rho), R, len(thetas), _ptr(thetas), _ptr(F_out)))
+
+
+def msd_update_geometry(h, centres=None, radii=None, k=None) -> None:
+    def arg(a):
+        if a is None:
+            return None
+        return a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, dtype=np.float64)
+    c, r, kk = arg(centres), arg(radii), arg(k)
+    _check(_lib.msd_update_geometry(h, _ptr(c) if c is not None else None,
+                                    _ptr(r) if r is not None else None,
+                                    _ptr(kk) if kk is not None else None))
+
+
+def msd_matvec_timing(h, enable: int):
+    """Returns (kernel_ms, launches, flops, bytes) accumulated since the last start."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    fl, by = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.msd_matvec_timing(h, enable, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                  ctypes.byref(by)))
+    return ms.value, n.value, fl.value, by.value
+
+
+def msd_kernel_launches() -> int:
+    return int(_lib.msd_kernel_launches())
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+@dataclass
+class SolveResult:
+    rho: object          # torch complex128 [N_tot, R] (device) or numpy (host)
+    status: int
+    flags: np.ndarray
+    iters: np.ndarray
+    refine_steps: np.ndarray
+    relres: np.ndarray
+
+
+class Problem:
+    """A batch of clusters (objects with centres, radii, bc, k, N) on the GPU."""
+
+    def __init__(self, clusters, stream=None):
+        if not isinstance(clusters, (list, tuple)):
+            clusters = [clusters]
+        self.clusters = list(clusters)
+        Ms = [len(c.radii) for c in self.clusters]
+        self.disk_off = np.concatenate([[0], np.cumsum(Ms)]).astype(np.int32)
+        cen = np.concatenate([np.asarray(c.centres, np.float64) for c in self.clusters])
+        rad = np.concatenate([np.asarray(c.radii, np.float64) for c in self.clusters])
+        bc = np.concatenate([np.asarray(c.bc, np.int8) for c in self.clusters])
+        k = np.array([c.k for c in self.clusters], np.float64)
+        N = np.array([c.N for c in self.clusters], np.int32)
+        self.C = len(self.clusters)
+        self.handle = msd_create(self.disk_off, cen, rad, bc, k, N, stream)
+        self.ntot = msd_num_unknowns(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            msd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def row_offset(self, c: int) -> int:
+        return msd_row_offset(self.handle, c)
+
+    def _betas(self, betas):
+        b = np.asarray(betas, np.float64)
+        if b.ndim == 1:
+            b = np.broadcast_to(b, (self.C, b.shape[0]))
+        return np.ascontiguousarray(b)
+
+    def diagonals(self):
+        import torch
+        out = torch.empty((4, self.ntot), dtype=torch.complex128, device="cuda")
+        msd_disk_diagonals(self.handle, out)
+        return out
+
+    def generators(self, c: int = 0):
+        import torch
+        cl = self.clusters[c]
+        M, L = len(cl.radii), 4 * cl.N + 1
+        out = torch.empty((M, M, L), dtype=torch.complex128, device="cuda")
+        msd_pair_generators(self.handle, c, out)
+        return out
+
+    def rhs(self, betas):
+        import torch
+        b = self._betas(betas)
+        out = torch.empty((self.ntot, b.shape[1]), dtype=torch.complex128, device="cuda")
+        msd_rhs_planewave(self.handle, b.shape[1], b, out)
+        return out
+
+    def matvec(self, x, precision: int = MSD_FP64, out=None):
+        import torch
+        R = x.shape[1] if x.dim() == 2 else 1
+        want = torch.complex128 if precision == MSD_FP64 else torch.complex64
+        if x.dtype != want or not x.is_contiguous() or not x.is_cuda:
+            raise ValueError(f"x must be a contiguous CUDA {want} tensor of shape [N_tot, R]")
+        y = torch.empty_like(x) if out is None else out
+        msd_matvec(self.handle, R, precision, x, y)
+        return y
+
+    def solve(self, betas, tol=1e-10, restart=100, maxit=3000, precision=MSD_FP64, max_refine=0,
+              inner_tol=0.0, out=None) -> SolveResult:
+        import torch
+        b = self._betas(betas)
+        R = b.shape[1]
+        o = msd_opts(tol, restart, maxit, max_refine, inner_tol, precision, MSD_GEN_AUTO)
+        rho = torch.empty((self.ntot, R), dtype=torch.complex128, device="cuda") if out is None else out
+        stats = (msd_stats * (self.C * R))()
+        st = msd_solve_planewaves(self.handle, R, b, o, rho, stats)
+        return SolveResult(rho, st, np.array([s.flag for s in stats]), np.array([s.iters for s in stats]),
+                           np.array([s.refine_steps for s in stats]), np.array([s.relres for s in stats]))
+
+    def farfield(self, rho, thetas, out=None):
+        import torch
+        th = np.ascontiguousarray(thetas, np.float64)
+        R = rho.shape[1]
+        F = torch.empty((self.C, len(th), R), dtype=torch.complex128, device="cuda") if out is None else out
+        msd_farfield(self.handle, rho, R, th, F)
+        return F
