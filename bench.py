@@ -168,7 +168,7 @@ def main():
 
     def step(precision):
         msd.msd_update_geometry(h, cen_d, rad_d, None)
-        o = msd.msd_opts(1e-10, 100, 3000, 0, 0.0, precision, 0)
+        o = msd.msd_opts(1e-10, 0, 3000, 0, 0.0, precision, 0)
         st = msd.msd_solve_planewaves(h, 1, beta, o, rho, stats)
         msd.msd_farfield(h, rho, 1, thetas, F)
         return st
@@ -223,7 +223,7 @@ def main():
 
     def step_e2e():
         msd.msd_update_geometry(h, cen_h, rad_h, None)
-        o = msd.msd_opts(1e-10, 100, 3000, 0, 0.0, msd.MSD_FP64, 0)
+        o = msd.msd_opts(1e-10, 0, 3000, 0, 0.0, msd.MSD_FP64, 0)
         msd.msd_solve_planewaves(h, 1, beta, o, rho_h, stats)
         msd.msd_farfield(h, rho_h, 1, thetas, F_h)
 

@@ -68,7 +68,7 @@ enum { MSD_GEN_AUTO = 0, MSD_GEN_STREAMED = 1, MSD_GEN_RECOMPUTE = 2 };
  * brackets. */
 typedef struct {
     double tol;        /* stop when ||P^-1(b - A x)|| / ||P^-1 b|| <= tol   [1e-10]   */
-    int restart;       /* GMRES restart length m                            [100]     */
+    int restart;       /* GMRES restart length m          [auto: as long as HBM allows] */
     int maxit;         /* limit on Arnoldi steps over the whole solve       [3000]    */
     int max_refine;    /* MSD_MIXED: limit on FP64 refinement sweeps        [60]      */
     double inner_tol;  /* MSD_MIXED: relative tolerance of each FP32 sweep  [2e-6]    */

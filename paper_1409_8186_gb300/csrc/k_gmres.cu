@@ -20,7 +20,9 @@ template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return mak
 // Column lanes: RC = min(R, 32) (power of two not required), rows lanes RY.
 __host__ __device__ inline int col_lanes(int R) { return R < 32 ? R : 32; }
 
-// Partial sums of conj(V_i) * w over one chunk of rows, for i in [i0, i0+kIChunk).
+// Partial sums of conj(V_i) * w over one chunk of rows (blockIdx.x), for the
+// kIChunk basis vectors i in [blockIdx.z * kIChunk, ...), columns of group
+// blockIdx.y.  Each block reads its w chunk once per vector group.
 template <typename V>
 __global__ void k_multidot_part(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb,
                                 long long vstride, int nv, const V* __restrict__ w,
@@ -31,38 +33,37 @@ __global__ void k_multidot_part(const RowChunk* __restrict__ chunks, int R, cons
     while (RY * 2 * RC <= (int)blockDim.x) RY *= 2;
     const int tx = threadIdx.x % RC, ty = threadIdx.x / RC;
     const int r = blockIdx.y * RC + tx;
+    const int i0 = blockIdx.z * kIChunk;
     __shared__ double2 red[kThreads];
-    for (int i0 = 0; i0 < nv; i0 += kIChunk) {
-        double2 acc[kIChunk];
+    double2 acc[kIChunk];
 #pragma unroll
-        for (int ii = 0; ii < kIChunk; ++ii) acc[ii] = make_double2(0.0, 0.0);
-        if (ty < RY && r < R) {
-            for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-                const double2 wv = to_d2(w[row * R + r]);
+    for (int ii = 0; ii < kIChunk; ++ii) acc[ii] = make_double2(0.0, 0.0);
+    if (ty < RY && r < R) {
+        for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
+            const double2 wv = to_d2(w[row * R + r]);
 #pragma unroll
-                for (int ii = 0; ii < kIChunk; ++ii) {
-                    if (i0 + ii < nv) {
-                        const double2 vv = to_d2(Vb[(long long)(i0 + ii) * vstride + row * R + r]);
-                        acc[ii].x += vv.x * wv.x + vv.y * wv.y;  // conj(v) * w
-                        acc[ii].y += vv.x * wv.y - vv.y * wv.x;
-                    }
+            for (int ii = 0; ii < kIChunk; ++ii) {
+                if (i0 + ii < nv) {
+                    const double2 vv = to_d2(Vb[(long long)(i0 + ii) * vstride + row * R + r]);
+                    acc[ii].x += vv.x * wv.x + vv.y * wv.y;  // conj(v) * w
+                    acc[ii].y += vv.x * wv.y - vv.y * wv.x;
                 }
             }
         }
-        for (int ii = 0; ii < kIChunk && i0 + ii < nv; ++ii) {
-            red[threadIdx.x] = acc[ii];
-            __syncthreads();
-            for (int st = RY / 2; st > 0; st /= 2) {
-                if (ty < st) {
-                    double2 o = red[threadIdx.x + st * RC];
-                    red[threadIdx.x].x += o.x;
-                    red[threadIdx.x].y += o.y;
-                }
-                __syncthreads();
+    }
+    for (int ii = 0; ii < kIChunk && i0 + ii < nv; ++ii) {
+        red[threadIdx.x] = acc[ii];
+        __syncthreads();
+        for (int st = RY / 2; st > 0; st /= 2) {
+            if (ty < st) {
+                double2 o = red[threadIdx.x + st * RC];
+                red[threadIdx.x].x += o.x;
+                red[threadIdx.x].y += o.y;
             }
-            if (ty == 0 && r < R) part[((long long)blockIdx.x * nv + (i0 + ii)) * R + r] = red[tx];
             __syncthreads();
         }
+        if (ty == 0 && r < R) part[((long long)blockIdx.x * nv + (i0 + ii)) * R + r] = red[tx];
+        __syncthreads();
     }
 }
 
@@ -103,14 +104,29 @@ __global__ void k_update(const RowChunk* __restrict__ chunks, int R, const V* __
     if (ty >= RY || r >= R) return;
     const double2* hs = h + (long long)(ch.cfg * R + r) * hstride;
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-        double2 acc = to_d2(w[row * R + r]);
-        for (int i = 0; i < nv; ++i) {
-            const double2 vv = to_d2(Vb[(long long)i * vstride + row * R + r]);
-            const double2 hh = hs[i];
-            acc.x -= vv.x * hh.x - vv.y * hh.y;
-            acc.y -= vv.x * hh.y + vv.y * hh.x;
+        // four independent partial sums keep several loads of V in flight
+        double2 a[4] = {to_d2(w[row * R + r]), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                        make_double2(0.0, 0.0)};
+        const V* vp = Vb + row * R + r;
+        int i = 0;
+        for (; i + 4 <= nv; i += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double2 vv = to_d2(vp[(long long)(i + u) * vstride]);
+                const double2 hh = hs[i + u];
+                a[u].x -= vv.x * hh.x - vv.y * hh.y;
+                a[u].y -= vv.x * hh.y + vv.y * hh.x;
+            }
         }
-        w[row * R + r] = V{(decltype(V{}.x))acc.x, (decltype(V{}.x))acc.y};
+        for (; i < nv; ++i) {
+            const double2 vv = to_d2(vp[(long long)i * vstride]);
+            const double2 hh = hs[i];
+            a[0].x -= vv.x * hh.x - vv.y * hh.y;
+            a[0].y -= vv.x * hh.y + vv.y * hh.x;
+        }
+        const double ax = (a[0].x + a[1].x) + (a[2].x + a[3].x);
+        const double ay = (a[0].y + a[1].y) + (a[2].y + a[3].y);
+        w[row * R + r] = V{(decltype(V{}.x))ax, (decltype(V{}.x))ay};
     }
 }
 
@@ -285,7 +301,9 @@ template <typename V>
 void gm_multidot(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb,
                  long long vstride, int nv, const V* w, double2* part, double2* h, int hstride,
                  int accumulate, cudaStream_t s) {
-    k_multidot_part<V><<<grid_for(d), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, w, part);
+    dim3 g = grid_for(d);
+    g.z = (nv + kIChunk - 1) / kIChunk;
+    k_multidot_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, w, part);
     const int tot = d.S * nv;
     k_multidot_fin<<<blocks_for(tot, 128), 128, 0, s>>>(d.C, d.R, nv, cfg_chunk_off, part, h, hstride,
                                                         accumulate);

@@ -50,8 +50,64 @@ __host__ __device__ inline int stage_x_elems(int n, int RT) {
     return I * kB * RT;
 }
 
+// Complex multiply-accumulate policies over a B x RB register tile.
+// Mac4: the textbook product, 4 real FMAs per complex MAC (FP32 path).
+template <typename V, int RB>
+struct Mac4 {
+    struct G { V g; };
+    struct X { V x; };
+    V acc[kB][RB];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int b = 0; b < kB; ++b)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[b][r] = vzero<V>();
+    }
+    __device__ __forceinline__ static G gen(V v) { return G{v}; }
+    __device__ __forceinline__ static X src(V v) { return X{v}; }
+    __device__ __forceinline__ void mac(int b, int r, const G& g, const X& x) { cfma(acc[b][r], g.g, x.x); }
+    __device__ __forceinline__ V result(int b, int r) const { return acc[b][r]; }
+};
+
+// Mac3: Gauss's three-multiplication form, accumulated in three real sums
+// (FP64 path, where the FP64 pipe is the bound).  With g = c + i d and
+// x = a + i b:  k1 += c (a + b),  k2 += a (d - c),  k3 += b (c + d);
+// then Re = k1 - k3, Im = k1 + k2.  The sums c+d, d-c are formed once per
+// generator value entering the register window and a+b once per source
+// value, so a complex MAC costs 3 FMAs instead of 4.
+template <typename V, int RB>
+struct Mac3 {
+    struct G { double c, u, v; };
+    struct X { double a, b, s; };
+    double k1[kB][RB], k2[kB][RB], k3[kB][RB];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int b = 0; b < kB; ++b)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) k1[b][r] = k2[b][r] = k3[b][r] = 0.0;
+    }
+    __device__ __forceinline__ static G gen(V v) { return G{v.x, v.y - v.x, v.x + v.y}; }
+    __device__ __forceinline__ static X src(V v) { return X{v.x, v.y, v.x + v.y}; }
+    __device__ __forceinline__ void mac(int b, int r, const G& g, const X& x) {
+        k1[b][r] = fma(g.c, x.s, k1[b][r]);
+        k2[b][r] = fma(x.a, g.u, k2[b][r]);
+        k3[b][r] = fma(x.b, g.v, k3[b][r]);
+    }
+    __device__ __forceinline__ V result(int b, int r) const {
+        return V{k1[b][r] - k3[b][r], k1[b][r] + k2[b][r]};
+    }
+};
+
+template <typename V, int RB> struct MacFor { typedef Mac4<V, RB> type; };
+template <int RB> struct MacFor<double2, RB> { typedef Mac3<double2, RB> type; };
+
+// Threads per CTA at most: 512 for FP32 (<= 128 registers), 256 for FP64 so
+// that the three-sum accumulators and the converted window stay in registers.
+template <typename V> struct MaxThreads { static constexpr int value = 512; };
+template <> struct MaxThreads<double2> { static constexpr int value = 256; };
+
 template <typename V, int RT, int RB>
-__global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
+__global__ void __launch_bounds__(MaxThreads<V>::value) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
                                                    const MatvecWork* __restrict__ works,
                                                    const V* __restrict__ G, const V* __restrict__ xs,
                                                    V* __restrict__ part, long long Ntot, int R, int rtiles) {
@@ -110,11 +166,9 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
         }
     };
 
-    V acc[kB][RB];
-#pragma unroll
-    for (int b = 0; b < kB; ++b)
-#pragma unroll
-        for (int r = 0; r < RB; ++r) acc[b][r] = vzero<V>();
+    typedef typename MacFor<V, RB>::type Mac;
+    Mac acc;
+    acc.init();
 
     if (w.q0 < w.q1) stage(w.q0, 0);
     cp_commit();
@@ -127,21 +181,20 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
         if (mact) {
         const V* gs = gbuf[it & 1] + lane * Ls + base;
         const V* xsl = xbuf[it & 1] + c0;
-        V win[kB];
+        typename Mac::G win[kB];
 #pragma unroll
-        for (int j = 1; j < kB; ++j) win[kB - j] = gs[-j];
+        for (int j = 1; j < kB; ++j) win[kB - j] = Mac::gen(gs[-j]);
         for (int nb = 0; nb < npad; nb += kB) {
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
-                win[u] = gs[nb + u];
-                V xv[RB];
+                win[u] = Mac::gen(gs[nb + u]);
+                typename Mac::X xv[RB];
 #pragma unroll
-                for (int r = 0; r < RB; ++r) xv[r] = xsl[(nb + u) * RT + r];
+                for (int r = 0; r < RB; ++r) xv[r] = Mac::src(xsl[(nb + u) * RT + r]);
 #pragma unroll
                 for (int b = 0; b < kB; ++b) {
-                    const V gv = win[(u - b + kB) % kB];
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) cfma(acc[b][r], gv, xv[r]);
+                    for (int r = 0; r < RB; ++r) acc.mac(b, r, win[(u - b + kB) % kB], xv[r]);
                 }
             }
         }
@@ -159,7 +212,7 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
             if (mi < n) {
                 const long long row = c.row_off + (long long)p * n + mi;
 #pragma unroll
-                for (int r = 0; r < RB; ++r) out[row * R + col0 + c0 + r] = acc[b][r];
+                for (int r = 0; r < RB; ++r) out[row * R + col0 + c0 + r] = acc.result(b, r);
             }
         }
     }
@@ -216,9 +269,12 @@ void launch_bt(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int 
 // Column tile RT for R columns: the largest power of two dividing R such
 // that the CTA stays within 16 warps (I m-blocks x RT/RB column groups).
 int matvec_col_tile(int R, int Nmax, bool fp64) {
+    // FP64: one column per CTA (the FP64 pipe, not the generator traffic,
+    // bounds the product; more columns per thread would spill registers)
+    if (fp64) return 1;
     const int n = 2 * Nmax + 1;
     const int I = (n + kB - 1) / kB;
-    const int rb_max = fp64 ? 2 : 4;
+    const int rb_max = 4;
     int best = 1;
     for (int rt = 1; rt <= 16; rt *= 2) {
         if (R % rt) break;
@@ -234,6 +290,35 @@ size_t matvec_smem_bytes(int R, int Nmax, bool fp64) {
     return 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * (fp64 ? 16 : 8);
 }
 
+namespace {
+template <typename V, int RT, int RB>
+int occupancy(int Nmax) {
+    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
+    const int I = (n + kB - 1) / kB;
+    const int threads = 32 * I * (RT / RB);
+    const size_t smem = 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * sizeof(V);
+    cudaFuncSetAttribute(k_bt_matvec<V, RT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb < 1 ? 1 : nb;
+}
+}  // namespace
+
+// Resident CTAs per SM of the product kernel chosen for (R, Nmax, precision).
+int matvec_blocks_per_sm(int R, int Nmax, bool fp64) {
+    if (fp64) return occupancy<double2, 1, 1>(Nmax);
+    switch (matvec_col_tile(R, Nmax, fp64)) {
+        case 1: return occupancy<float2, 1, 1>(Nmax);
+        case 2: return occupancy<float2, 2, 2>(Nmax);
+        case 4: return occupancy<float2, 4, 4>(Nmax);
+        case 8: return occupancy<float2, 8, 4>(Nmax);
+        default: return occupancy<float2, 16, 4>(Nmax);
+    }
+}
+
 void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const double2* G, const double* rf, const double2* lf, long long Ntot, int R,
                        const double2* x, double2* xs, double2* part, int nsplit, double2* y, cudaStream_t s,
@@ -243,13 +328,7 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<double2, double><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
-    switch (matvec_col_tile(R, Nmax, true)) {
-        case 1: launch_bt<double2, 1, 1>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        case 2: launch_bt<double2, 2, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        case 4: launch_bt<double2, 4, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        case 8: launch_bt<double2, 8, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        default: launch_bt<double2, 16, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-    }
+    launch_bt<double2, 1, 1>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize<double2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;

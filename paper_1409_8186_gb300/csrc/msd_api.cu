@@ -18,6 +18,7 @@
 
 int matvec_col_tile(int R, int Nmax, bool fp64);
 size_t matvec_smem_bytes(int R, int Nmax, bool fp64);
+int matvec_blocks_per_sm(int R, int Nmax, bool fp64);
 
 // ---------------------------------------------------------------- errors
 
@@ -200,11 +201,29 @@ MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
     const int rtiles = R / RT;
     long long tiles = 0;
     for (auto& c : pb->cfg) tiles += c.Mp / MSD_TILE_P;
-    long long want = (kTargetCtas + tiles * rtiles - 1) / (tiles * rtiles);
-    int ns = (int)std::max<long long>(1, std::min<long long>(want, std::max(1, pb->Mmax / 4)));
-    // keep the partial-sum buffer within 2 GB
+    // Split the source range so that the CTAs fill whole waves of the
+    // resident slots: efficiency(ns) = (work items / slots) / ceil(...) times
+    // the balance of the largest source range against the mean.
+    int sms = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long slots = (long long)sms * matvec_blocks_per_sm(R, pb->Nmax, fp64);
+    const long long units = tiles * rtiles;
     const size_t elem = fp64 ? 16 : 8;
-    while (ns > 1 && (size_t)ns * pb->Ntot * R * elem > (2ull << 30)) --ns;
+    int ns = 1;
+    double best = -1;
+    for (int t = 1; t <= std::min(64, std::max(1, pb->Mmax / 2)); ++t) {
+        if (t > 1 && (size_t)t * pb->Ntot * R * elem > (2ull << 30)) break;  // partial sums <= 2 GB
+        const double waves = (double)(units * t) / slots;
+        const double fill = waves / std::ceil(waves);
+        const double per = (double)pb->Mmax / t;
+        const double bal = per / std::ceil(per);
+        const double eff = fill * bal;
+        if (eff > best + 1e-9) {
+            best = eff;
+            ns = t;
+        }
+    }
     plan.nsplit = ns;
     for (int ci = 0; ci < pb->C; ++ci) {
         const MsdConfig& c = pb->cfg[ci];
@@ -369,7 +388,20 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     memset(&o, 0, sizeof(o));
     if (opts_in) o = *opts_in;
     if (o.tol <= 0) o.tol = 1e-10;
-    if (o.restart <= 0) o.restart = 100;
+    if (o.restart <= 0) {
+        // Automatic restart length: GMRES converges fastest unrestarted, and
+        // HBM is large, so take the longest Krylov basis that fits in half of
+        // the free device memory and keeps the per-system Hessenberg
+        // matrices within 2 GB, capped by maxit and by 4000.
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const double vec = (double)pb->Ntot * R * ((o.precision == MSD_MIXED) ? 8 : 16);
+        const double S_ = (double)pb->C * R;
+        const long long m_mem = (long long)(0.5 * (double)free_b / vec) - 2;
+        const long long m_hess = (long long)std::sqrt(2e9 / (16.0 * S_));
+        long long m = std::min<long long>({m_mem, m_hess, (long long)o.maxit, 4000LL});
+        o.restart = (int)std::max<long long>(m, 10);
+    }
     if (o.maxit <= 0) o.maxit = 3000;
     if (o.max_refine <= 0) o.max_refine = 60;
     if (o.inner_tol <= 0) o.inner_tol = 2e-6;

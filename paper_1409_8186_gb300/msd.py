@@ -271,7 +271,7 @@ class Problem:
         msd_matvec(self.handle, R, precision, x, y)
         return y
 
-    def solve(self, betas, tol=1e-10, restart=100, maxit=3000, precision=MSD_FP64, max_refine=0,
+    def solve(self, betas, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64, max_refine=0,
               inner_tol=0.0, out=None) -> SolveResult:
         import torch
         b = self._betas(betas)
