@@ -2,135 +2,172 @@
 // Krylov solve; the restarted GMRES call of section 6.2).
 //
 // A "system" is one (configuration, column) pair s = cfg*R + r; all systems
-// advance in lock step (one block matvec per Arnoldi step serves all of
+// advance in lock step (one block product per Arnoldi step serves all of
 // them) and each carries its own Hessenberg matrix, Givens rotations and
-// convergence state.  Orthogonalisation is classical Gram-Schmidt applied
-// twice (CGS2); dot products accumulate in FP64 whatever the storage type of
-// the basis.  Vectors are [rows][R] with R innermost; reductions run over
-// row chunks that never straddle two configurations.
+// convergence state.
+//
+// Orthogonalisation is classical Gram-Schmidt with one selective
+// re-orthogonalisation pass (Daniel-Gragg-Kaufman-Stewart criterion: repeat
+// the projection when it removed more than half of ||w||^2).  Dot products
+// accumulate in FP64 whatever the storage type of the basis.  Vectors are
+// [rows][R] with R innermost; reductions run over row chunks that never
+// straddle two configurations; projections V^H w and updates w -= V h are
+// tiled over (row chunk, group of basis vectors) so that long Krylov bases
+// are read with the whole GPU.
+//
+// The Givens rotations of a new Hessenberg column form the first-order
+// linear recurrence z_{i+1} = -conj(s_i) z_i + c_i h_{i+1} (z_0 = h_0,
+// rotated entry i = c_i z_i + s_i h_{i+1}); it is evaluated with a
+// parallel scan of affine maps over one CTA per system, so a step costs
+// O(j / threads + log threads) instead of a j-long dependency chain.
 #include "msd_internal.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kIChunk = 8;  // basis vectors handled per pass of a reduction
+constexpr int kI = 8;    // basis vectors per dot-product block
+constexpr int kU = 32;   // basis vectors per update block
 
 template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return make_double2(v.x, v.y); }
 
-// Column lanes: RC = min(R, 32) (power of two not required), rows lanes RY.
+// Column lanes RC = min(R, 32); row lanes RY = largest power of two with RY * RC <= threads.
 __host__ __device__ inline int col_lanes(int R) { return R < 32 ? R : 32; }
+__device__ inline int row_lanes(int RC) {
+    int RY = 1;
+    while (RY * 2 * RC <= (int)blockDim.x) RY *= 2;
+    return RY;
+}
 
-// Partial sums of conj(V_i) * w over one chunk of rows (blockIdx.x), for the
-// kIChunk basis vectors i in [blockIdx.z * kIChunk, ...), columns of group
-// blockIdx.y.  Each block reads its w chunk once per vector group.
+__device__ __forceinline__ void atomic_add_v(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ void atomic_add_v(float2* p, double2 v) {
+    atomicAdd(&p->x, (float)v.x);
+    atomicAdd(&p->y, (float)v.y);
+}
+
+// Partial sums over one chunk of rows (blockIdx.x), columns of group
+// blockIdx.y, and the kI "vectors" i in [blockIdx.z * kI, ...) of the
+// list V_0..V_{nv-1} followed, when self != 0, by w itself:
+//   part[chunk][i][r] = sum_rows conj(u_i[row][r]) * w[row][r].
+// Systems with skip[s] != 0 contribute zeros.
 template <typename V>
-__global__ void k_multidot_part(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb,
-                                long long vstride, int nv, const V* __restrict__ w,
-                                double2* __restrict__ part) {
+__global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb,
+                            long long vstride, int nv, int self, const V* __restrict__ w,
+                            const int* __restrict__ skip, double2* __restrict__ part) {
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
-    int RY = 1;  // row lanes: a power of two so that the tree below is exact
-    while (RY * 2 * RC <= (int)blockDim.x) RY *= 2;
+    const int RY = row_lanes(RC);
     const int tx = threadIdx.x % RC, ty = threadIdx.x / RC;
     const int r = blockIdx.y * RC + tx;
-    const int i0 = blockIdx.z * kIChunk;
+    const int i0 = blockIdx.z * kI;
+    const int nvv = nv + self;
     __shared__ double2 red[kThreads];
-    double2 acc[kIChunk];
+    double2 acc[kI];
 #pragma unroll
-    for (int ii = 0; ii < kIChunk; ++ii) acc[ii] = make_double2(0.0, 0.0);
-    if (ty < RY && r < R) {
+    for (int ii = 0; ii < kI; ++ii) acc[ii] = make_double2(0.0, 0.0);
+    const bool live = ty < RY && r < R && !(skip && skip[ch.cfg * R + r]);
+    if (live) {
         for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
             const double2 wv = to_d2(w[row * R + r]);
 #pragma unroll
-            for (int ii = 0; ii < kIChunk; ++ii) {
-                if (i0 + ii < nv) {
-                    const double2 vv = to_d2(Vb[(long long)(i0 + ii) * vstride + row * R + r]);
+            for (int ii = 0; ii < kI; ++ii) {
+                const int i = i0 + ii;
+                if (i < nvv) {
+                    const double2 vv = i < nv ? to_d2(Vb[(long long)i * vstride + row * R + r]) : wv;
                     acc[ii].x += vv.x * wv.x + vv.y * wv.y;  // conj(v) * w
                     acc[ii].y += vv.x * wv.y - vv.y * wv.x;
                 }
             }
         }
     }
-    for (int ii = 0; ii < kIChunk && i0 + ii < nv; ++ii) {
+    for (int ii = 0; ii < kI && i0 + ii < nvv; ++ii) {
         red[threadIdx.x] = acc[ii];
         __syncthreads();
         for (int st = RY / 2; st > 0; st /= 2) {
             if (ty < st) {
-                double2 o = red[threadIdx.x + st * RC];
+                const double2 o = red[threadIdx.x + st * RC];
                 red[threadIdx.x].x += o.x;
                 red[threadIdx.x].y += o.y;
             }
             __syncthreads();
         }
-        if (ty == 0 && r < R) part[((long long)blockIdx.x * nv + (i0 + ii)) * R + r] = red[tx];
+        if (ty == 0 && r < R) part[((long long)blockIdx.x * nvv + (i0 + ii)) * R + r] = red[tx];
         __syncthreads();
     }
 }
 
-// h[s][i] = sum over the chunks of cfg(s) of part[chunk][i][r] (+= if accumulate)
-__global__ void k_multidot_fin(int C, int R, int nv, const int* __restrict__ cfg_chunk_off,
-                               const double2* __restrict__ part, double2* __restrict__ h, int hstride,
-                               int accumulate) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= C * R * nv) return;
-    const int i = idx % nv;
-    const int s = idx / nv;
+// out[s * ostride + i] = sum over the chunks of cfg(s) of part[chunk][i][r]
+__global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_chunk_off,
+                           const double2* __restrict__ part, double2* __restrict__ out, int ostride) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)C * R * nvv) return;
+    const int i = (int)(idx % nvv);
+    const int s = (int)(idx / nvv);
     const int c = s / R, r = s % R;
     double2 acc = make_double2(0.0, 0.0);
     for (int k = cfg_chunk_off[c]; k < cfg_chunk_off[c + 1]; ++k) {
-        const double2 v = part[((long long)k * nv + i) * R + r];
+        const double2 v = part[((long long)k * nvv + i) * R + r];
         acc.x += v.x;
         acc.y += v.y;
     }
-    double2* dst = h + (long long)s * hstride + i;
-    if (accumulate) {
-        dst->x += acc.x;
-        dst->y += acc.y;
-    } else {
-        *dst = acc;
-    }
+    out[(long long)s * ostride + i] = acc;
 }
 
-// w[row][r] -= sum_i V_i[row][r] h[s][i]   (s = cfg(row)*R + r)
-template <typename V>
-__global__ void k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb,
-                         long long vstride, int nv, const double2* __restrict__ h, int hstride,
-                         V* __restrict__ w) {
+// w[row][r] += sign * sum_{i in block's group, i < nv} V_i[row][r] h[s][i].
+// With more than one vector group the groups meet in atomics; with one
+// group the result is stored directly.
+template <typename V, typename W>
+__global__ void k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
+                         int nv, const double2* __restrict__ h, int hstride, const int* __restrict__ skip,
+                         double sign, W* __restrict__ w) {
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
     const int RY = blockDim.x / RC;
     const int tx = threadIdx.x % RC, ty = threadIdx.x / RC;
     const int r = blockIdx.y * RC + tx;
     if (ty >= RY || r >= R) return;
-    const double2* hs = h + (long long)(ch.cfg * R + r) * hstride;
+    const int s = ch.cfg * R + r;
+    if (skip && skip[s]) return;
+    const int i0 = blockIdx.z * kU;
+    const int i1 = min(nv, i0 + kU);
+    if (i0 >= i1) return;
+    const double2* hs = h + (long long)s * hstride;
+    const bool atomic = gridDim.z > 1;
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-        // four independent partial sums keep several loads of V in flight
-        double2 a[4] = {to_d2(w[row * R + r]), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+        double2 a[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
                         make_double2(0.0, 0.0)};
         const V* vp = Vb + row * R + r;
-        int i = 0;
-        for (; i + 4 <= nv; i += 4) {
+        int i = i0;
+        for (; i + 4 <= i1; i += 4) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const double2 vv = to_d2(vp[(long long)(i + u) * vstride]);
                 const double2 hh = hs[i + u];
-                a[u].x -= vv.x * hh.x - vv.y * hh.y;
-                a[u].y -= vv.x * hh.y + vv.y * hh.x;
+                a[u].x += vv.x * hh.x - vv.y * hh.y;
+                a[u].y += vv.x * hh.y + vv.y * hh.x;
             }
         }
-        for (; i < nv; ++i) {
+        for (; i < i1; ++i) {
             const double2 vv = to_d2(vp[(long long)i * vstride]);
             const double2 hh = hs[i];
-            a[0].x -= vv.x * hh.x - vv.y * hh.y;
-            a[0].y -= vv.x * hh.y + vv.y * hh.x;
+            a[0].x += vv.x * hh.x - vv.y * hh.y;
+            a[0].y += vv.x * hh.y + vv.y * hh.x;
         }
-        const double ax = (a[0].x + a[1].x) + (a[2].x + a[3].x);
-        const double ay = (a[0].y + a[1].y) + (a[2].y + a[3].y);
-        w[row * R + r] = V{(decltype(V{}.x))ax, (decltype(V{}.x))ay};
+        const double2 d = make_double2(sign * ((a[0].x + a[1].x) + (a[2].x + a[3].x)),
+                                       sign * ((a[0].y + a[1].y) + (a[2].y + a[3].y)));
+        W* p = w + row * R + r;
+        if (atomic) {
+            atomic_add_v(p, d);
+        } else {
+            const double2 o = to_d2(*p);
+            *p = W{(decltype(W{}.x))(o.x + d.x), (decltype(W{}.x))(o.y + d.y)};
+        }
     }
 }
 
-// v = w * scale[s] for active systems, 0 otherwise.  Input FP64 or T, output T.
+// v = w * scale[s] for active systems, 0 otherwise.
 template <typename Vin, typename Vout>
 __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* __restrict__ w,
                         const double* __restrict__ scale, const int* __restrict__ active,
@@ -149,30 +186,16 @@ __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* _
     }
 }
 
-// x[row][r] += sum_{i < kconv[s]} V_i[row][r] y[s][i]
-template <typename V>
-__global__ void k_xupdate(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb,
-                          long long vstride, const double2* __restrict__ y, int ystride,
-                          const int* __restrict__ kconv, double2* __restrict__ x) {
-    const RowChunk ch = chunks[blockIdx.x];
-    const int RC = col_lanes(R);
-    const int RY = blockDim.x / RC;
-    const int tx = threadIdx.x % RC, ty = threadIdx.x / RC;
-    const int r = blockIdx.y * RC + tx;
-    if (ty >= RY || r >= R) return;
-    const int s = ch.cfg * R + r;
-    const int k = kconv[s];
-    if (k == 0) return;
-    const double2* ys = y + (long long)s * ystride;
-    for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-        double2 acc = x[row * R + r];
-        for (int i = 0; i < k; ++i) {
-            const double2 vv = to_d2(Vb[(long long)i * vstride + row * R + r]);
-            acc.x += vv.x * ys[i].x - vv.y * ys[i].y;
-            acc.y += vv.x * ys[i].y + vv.y * ys[i].x;
-        }
-        x[row * R + r] = acc;
-    }
+// Selective re-orthogonalisation flags: need[s] = 1 for an active system
+// whose first projection left ||w'||^2 < ||w||^2 / 2.
+__global__ void k_reorth_flags(int S, const double2* __restrict__ h1, int hstride, int j,
+                               const double2* __restrict__ wn2, const int* __restrict__ active,
+                               int* __restrict__ skip2) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double before = h1[(long long)s * hstride + j + 1].x;  // ||w||^2 before the projection
+    const double after = wn2[(long long)s * hstride].x;
+    skip2[s] = !(active[s] && after < 0.5 * before);
 }
 
 // Start of a cycle: beta = ||r||; systems whose residual already meets
@@ -183,7 +206,7 @@ __global__ void k_start(int S, int m, const double2* __restrict__ rr, int hstrid
                         int* __restrict__ kconv, int* __restrict__ any_active) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
-    const double beta = sqrt(rr[(long long)s * hstride].x);
+    const double beta = sqrt(fmax(rr[(long long)s * hstride].x, 0.0));
     beta_out[s] = beta;
     kconv[s] = 0;
     const int act = (beta > tol_abs[s]) && isfinite(beta);
@@ -195,32 +218,82 @@ __global__ void k_start(int S, int m, const double2* __restrict__ rr, int hstrid
     if (act) atomicOr(any_active, 1);
 }
 
-// Arnoldi step j: column h = h1 + h2 (CGS2), h[j+1] = ||w||; apply the previous
-// rotations, make a new one, update g and the convergence state.
-__global__ void k_givens(int S, int m, int j, const double2* __restrict__ h1, const double2* __restrict__ h2,
-                         int hstride, const double2* __restrict__ wn2, const double* __restrict__ tol_cycle,
-                         double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
-                         double2* __restrict__ g, double* __restrict__ vscale, int* __restrict__ active,
-                         int* __restrict__ kconv, int* __restrict__ iters, int* __restrict__ any_active,
-                         int* __restrict__ nonfinite) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+// affine map z -> A z + B (complex); compose(second, first) = second o first
+struct Aff {
+    double2 A, B;
+};
+__device__ __forceinline__ Aff compose(const Aff& second, const Aff& first) {
+    return Aff{cmul(second.A, first.A), cadd(cmul(second.A, first.B), second.B)};
+}
+
+// Arnoldi step j for one system per CTA: column h = h1 + h2 (h2 only where
+// the second projection ran), h[j+1] = ||w||, previous rotations by scan,
+// new rotation, g, convergence state.
+__global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2* __restrict__ h1,
+                                                     const double2* __restrict__ h2, int hstride,
+                                                     const double2* __restrict__ wn2a,
+                                                     const double2* __restrict__ wn2b,
+                                                     const int* __restrict__ skip2,
+                                                     const double* __restrict__ tol_cycle,
+                                                     double2* __restrict__ H, double2* __restrict__ cs,
+                                                     double2* __restrict__ sn, double2* __restrict__ g,
+                                                     double* __restrict__ vscale, int* __restrict__ active,
+                                                     int* __restrict__ kconv, int* __restrict__ iters,
+                                                     int* __restrict__ any_active, int* __restrict__ nonfinite) {
+    const int s = blockIdx.x;
     if (!active[s]) return;
-    double2* Hc = H + ((long long)s * m + j) * (m + 1);  // column j, rows 0..j+1
+    __shared__ Aff pre[kThreads];
+    __shared__ double2 zj_sh;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const bool second = !skip2[s];
     const double2* a = h1 + (long long)s * hstride;
     const double2* b = h2 + (long long)s * hstride;
-    for (int i = 0; i <= j; ++i) Hc[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
-    const double hn = sqrt(fmax(wn2[(long long)s * hstride].x, 0.0));
-    double2* csj = cs + (long long)s * m;
-    double2* snj = sn + (long long)s * m;
-    for (int i = 0; i < j; ++i) {
-        const double2 c = csj[i], sn_ = snj[i];
-        const double2 hi = Hc[i], hi1 = Hc[i + 1];
-        // [c s; -conj(s) c] with c real
-        Hc[i] = cadd(cscale(hi, c.x), cmul(sn_, hi1));
-        Hc[i + 1] = csub(cscale(hi1, c.x), cmul(cconj(sn_), hi));
+    const double2* csj = cs + (long long)s * m;
+    const double2* snj = sn + (long long)s * m;
+    double2* Hc = H + ((long long)s * m + j) * (m + 1);  // column j, rows 0..j+1
+    auto hval = [&](int i) {
+        double2 v = a[i];
+        if (second) v = cadd(v, b[i]);
+        return v;
+    };
+    // segment of rotations [lo, hi) owned by this thread
+    const int per = (j + T - 1) / T;
+    const int lo = min(j, tid * per), hi = min(j, lo + per);
+    Aff seg{make_double2(1.0, 0.0), make_double2(0.0, 0.0)};
+    for (int i = lo; i < hi; ++i) {
+        const Aff st{cscale(cconj(snj[i]), -1.0), cscale(hval(i + 1), csj[i].x)};
+        seg = compose(st, seg);
     }
-    const double2 hjj = Hc[j];
+    pre[tid] = seg;
+    __syncthreads();
+    // inclusive Hillis-Steele scan of the segment maps in thread order
+    for (int off = 1; off < T; off *= 2) {
+        Aff v = pre[tid];
+        if (tid >= off) v = compose(v, pre[tid - off]);
+        __syncthreads();
+        pre[tid] = v;
+        __syncthreads();
+    }
+    const double2 z0 = hval(0);
+    double2 z = z0;
+    if (tid > 0) {
+        const Aff p = pre[tid - 1];
+        z = cadd(cmul(p.A, z0), p.B);
+    }
+    for (int i = lo; i < hi; ++i) {
+        const double2 c = csj[i], sv = snj[i], hn1 = hval(i + 1);
+        Hc[i] = cadd(cscale(z, c.x), cmul(sv, hn1));
+        z = csub(cscale(hn1, c.x), cmul(cconj(sv), z));
+    }
+    if (hi == j && lo <= j && (lo < hi || tid == 0)) {
+        // the thread owning the last rotation (or thread 0 when j == 0)
+        if (lo < hi || j == 0) zj_sh = z;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    const double2 hjj = zj_sh;
+    const double wn = second ? wn2b[(long long)s * hstride].x : wn2a[(long long)s * hstride].x;
+    const double hn = sqrt(fmax(wn, 0.0));
     const double ajj = sqrt(cabs2(hjj));
     const double den = hypot(ajj, hn);
     double2 c, sv;
@@ -235,9 +308,10 @@ __global__ void k_givens(int S, int m, int j, const double2* __restrict__ h1, co
         c = make_double2(ajj / den, 0.0);
         sv = cscale(ph, hn / den);  // ph * conj(hn) / den, hn real
     }
-    csj[j] = c;
-    snj[j] = sv;
-    Hc[j] = cadd(cscale(hjj, c.x), cscale(sv, hn));
+    cs[(long long)s * m + j] = c;
+    sn[(long long)s * m + j] = sv;
+    const double2 rjj = cadd(cscale(hjj, c.x), cscale(sv, hn));
+    Hc[j] = rjj;
     Hc[j + 1] = make_double2(0.0, 0.0);
     double2* gs = g + (long long)s * (m + 1);
     const double2 gj = gs[j];
@@ -245,7 +319,7 @@ __global__ void k_givens(int S, int m, int j, const double2* __restrict__ h1, co
     gs[j] = cscale(gj, c.x);
     iters[s] += 1;
     const double res = sqrt(cabs2(gs[j + 1]));
-    const bool bad = !isfinite(res) || !isfinite(Hc[j].x) || !isfinite(Hc[j].y);
+    const bool bad = !isfinite(res) || !isfinite(rjj.x) || !isfinite(rjj.y);
     if (bad) atomicOr(nonfinite, 1);
     if (bad || res <= tol_cycle[s] || hn == 0.0 || j + 1 == m) {
         active[s] = 0;
@@ -257,20 +331,35 @@ __global__ void k_givens(int S, int m, int j, const double2* __restrict__ h1, co
     }
 }
 
-// Back substitution H y = g on the leading kconv x kconv triangle.
-__global__ void k_lsq(int S, int m, const double2* __restrict__ H, const double2* __restrict__ g,
-                      const int* __restrict__ kconv, double2* __restrict__ y) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+// Back substitution H y = g on the leading kconv x kconv triangle, one CTA
+// per system: column-oriented, the CTA updates the remaining right-hand
+// side in parallel after each pivot.
+__global__ void __launch_bounds__(kThreads) k_lsq(int m, const double2* __restrict__ H,
+                                                  const double2* __restrict__ g, const int* __restrict__ kconv,
+                                                  double2* __restrict__ y, double2* __restrict__ work) {
+    const int s = blockIdx.x;
     const int k = kconv[s];
-    const double2* Hs = H + (long long)s * m * (m + 1);
-    const double2* gs = g + (long long)s * (m + 1);
     double2* ys = y + (long long)s * m;
+    // the x update sweeps every column of the cycle: zero what this system did not use
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) ys[i] = make_double2(0.0, 0.0);
+    if (k == 0) return;
+    const double2* Hs = H + (long long)s * m * (m + 1);
+    double2* rhs = work + (long long)s * (m + 1);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = g[(long long)s * (m + 1) + i];
+    __shared__ double2 yi_sh;
+    __syncthreads();
     for (int i = k - 1; i >= 0; --i) {
-        double2 acc = gs[i];
-        for (int jj = i + 1; jj < k; ++jj) acc = csub(acc, cmul(Hs[(long long)jj * (m + 1) + i], ys[jj]));
-        const double2 d = Hs[(long long)i * (m + 1) + i];
-        ys[i] = (d.x == 0.0 && d.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(acc, d);
+        if (threadIdx.x == 0) {
+            const double2 d = Hs[(long long)i * (m + 1) + i];
+            const double2 v = (d.x == 0.0 && d.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(rhs[i], d);
+            ys[i] = v;
+            yi_sh = v;
+        }
+        __syncthreads();
+        const double2 v = yi_sh;
+        const double2* col = Hs + (long long)i * (m + 1);
+        for (int t = threadIdx.x; t < i; t += blockDim.x) rhs[t] = csub(rhs[t], cmul(col[t], v));
+        __syncthreads();
     }
 }
 
@@ -285,71 +374,66 @@ __global__ void k_zero(long long n, double2* __restrict__ x) {
     if (i < n) x[i] = make_double2(0.0, 0.0);
 }
 
-__global__ void k_cast_f32(long long n, const double2* __restrict__ a, float2* __restrict__ b) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
-}
-
-inline dim3 grid_for(const GmresDims& d) { return dim3(d.nchunk, (d.R + col_lanes(d.R) - 1) / col_lanes(d.R)); }
 inline unsigned blocks_for(long long n, int th) { return (unsigned)((n + th - 1) / th); }
+inline unsigned rgroups(int R) { return (unsigned)((R + col_lanes(R) - 1) / col_lanes(R)); }
 
 }  // namespace
 
 // ---------------------------------------------------------------- host wrappers
 
 template <typename V>
-void gm_multidot(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb,
-                 long long vstride, int nv, const V* w, double2* part, double2* h, int hstride,
-                 int accumulate, cudaStream_t s) {
-    dim3 g = grid_for(d);
-    g.z = (nv + kIChunk - 1) / kIChunk;
-    k_multidot_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, w, part);
-    const int tot = d.S * nv;
-    k_multidot_fin<<<blocks_for(tot, 128), 128, 0, s>>>(d.C, d.R, nv, cfg_chunk_off, part, h, hstride,
-                                                        accumulate);
+void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
+             int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
+             cudaStream_t s) {
+    const int nvv = nv + self;
+    dim3 g(d.nchunk, rgroups(d.R), (nvv + kI - 1) / kI);
+    k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, part);
+    const long long tot = (long long)d.S * nvv;
+    k_dots_fin<<<blocks_for(tot, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
     g_msd_launches += 2;
 }
 
-template <typename V>
-void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv,
-               const double2* h, int hstride, V* w, cudaStream_t s) {
-    k_update<V><<<grid_for(d), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, h, hstride, w);
+template <typename V, typename W>
+void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv, const double2* h,
+               int hstride, const int* skip, double sign, W* w, cudaStream_t s) {
+    if (nv <= 0) return;
+    dim3 g(d.nchunk, rgroups(d.R), (nv + kU - 1) / kU);
+    k_update<V, W><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, h, hstride, skip, sign, w);
     g_msd_launches += 1;
 }
 
 template <typename Vin, typename Vout>
-void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale,
-              const int* active, Vout* v, cudaStream_t s) {
-    k_scale<Vin, Vout><<<grid_for(d), kThreads, 0, s>>>(chunks, d.R, w, scale, active, v);
+void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale, const int* active,
+              Vout* v, cudaStream_t s) {
+    k_scale<Vin, Vout><<<dim3(d.nchunk, rgroups(d.R)), kThreads, 0, s>>>(chunks, d.R, w, scale, active, v);
     g_msd_launches += 1;
 }
 
-template <typename V>
-void gm_xupdate(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride,
-                const double2* y, const int* kconv, double2* x, cudaStream_t s) {
-    k_xupdate<V><<<grid_for(d), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, y, d.m, kconv, x);
+void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, const double2* wn2,
+                     const int* active, int* skip2, cudaStream_t s) {
+    k_reorth_flags<<<blocks_for(d.S, 128), 128, 0, s>>>(d.S, h1, hstride, j, wn2, active, skip2);
     g_msd_launches += 1;
 }
 
 void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* tol_abs, double* beta,
               double* vscale, double2* g, int* active, int* kconv, int* any_active, cudaStream_t s) {
-    k_start<<<blocks_for(d.S, 128), 128, 0, s>>>(d.S, d.m, rr, hstride, tol_abs, beta, vscale, g, active,
-                                                 kconv, any_active);
+    k_start<<<blocks_for(d.S, 128), 128, 0, s>>>(d.S, d.m, rr, hstride, tol_abs, beta, vscale, g, active, kconv,
+                                                 any_active);
     g_msd_launches += 1;
 }
 
-void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride,
-               const double2* wn2, const double* tol_cycle, double2* H, double2* cs, double2* sn,
-               double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
+void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride, const double2* wn2a,
+               const double2* wn2b, const int* skip2, const double* tol_cycle, double2* H, double2* cs,
+               double2* sn, double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
                int* nonfinite, cudaStream_t s) {
-    k_givens<<<blocks_for(d.S, 128), 128, 0, s>>>(d.S, d.m, j, h1, h2, hstride, wn2, tol_cycle, H, cs, sn,
-                                                  g, vscale, active, kconv, iters, any_active, nonfinite);
+    k_givens<<<d.S, kThreads, 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H, cs, sn, g, vscale,
+                                      active, kconv, iters, any_active, nonfinite);
     g_msd_launches += 1;
 }
 
-void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y,
+void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y, double2* work,
             cudaStream_t s) {
-    k_lsq<<<blocks_for(d.S, 128), 128, 0, s>>>(d.S, d.m, H, g, kconv, y);
+    k_lsq<<<d.S, kThreads, 0, s>>>(d.m, H, g, kconv, y, work);
     g_msd_launches += 1;
 }
 
@@ -357,30 +441,25 @@ void gm_residual(long long n, const double2* b, const double2* Ax, double2* r, c
     k_residual<<<blocks_for(n, 256), 256, 0, s>>>(n, b, Ax, r);
     g_msd_launches += 1;
 }
+
 void gm_zero(long long n, double2* x, cudaStream_t s) {
     k_zero<<<blocks_for(n, 256), 256, 0, s>>>(n, x);
     g_msd_launches += 1;
 }
-void gm_cast_f32(long long n, const double2* a, float2* b, cudaStream_t s) {
-    k_cast_f32<<<blocks_for(n, 256), 256, 0, s>>>(n, a, b);
-    g_msd_launches += 1;
-}
 
-template void gm_multidot<double2>(const GmresDims&, const RowChunk*, const int*, const double2*, long long,
-                                   int, const double2*, double2*, double2*, int, int, cudaStream_t);
-template void gm_multidot<float2>(const GmresDims&, const RowChunk*, const int*, const float2*, long long,
-                                  int, const float2*, double2*, double2*, int, int, cudaStream_t);
-template void gm_update<double2>(const GmresDims&, const RowChunk*, const double2*, long long, int,
-                                 const double2*, int, double2*, cudaStream_t);
-template void gm_update<float2>(const GmresDims&, const RowChunk*, const float2*, long long, int,
-                                const double2*, int, float2*, cudaStream_t);
+template void gm_dots<double2>(const GmresDims&, const RowChunk*, const int*, const double2*, long long, int, int,
+                               const double2*, const int*, double2*, double2*, int, cudaStream_t);
+template void gm_dots<float2>(const GmresDims&, const RowChunk*, const int*, const float2*, long long, int, int,
+                              const float2*, const int*, double2*, double2*, int, cudaStream_t);
+template void gm_update<double2, double2>(const GmresDims&, const RowChunk*, const double2*, long long, int,
+                                          const double2*, int, const int*, double, double2*, cudaStream_t);
+template void gm_update<float2, float2>(const GmresDims&, const RowChunk*, const float2*, long long, int,
+                                        const double2*, int, const int*, double, float2*, cudaStream_t);
+template void gm_update<float2, double2>(const GmresDims&, const RowChunk*, const float2*, long long, int,
+                                         const double2*, int, const int*, double, double2*, cudaStream_t);
 template void gm_scale<double2, double2>(const GmresDims&, const RowChunk*, const double2*, const double*,
                                          const int*, double2*, cudaStream_t);
 template void gm_scale<double2, float2>(const GmresDims&, const RowChunk*, const double2*, const double*,
                                         const int*, float2*, cudaStream_t);
-template void gm_scale<float2, float2>(const GmresDims&, const RowChunk*, const float2*, const double*,
-                                       const int*, float2*, cudaStream_t);
-template void gm_xupdate<double2>(const GmresDims&, const RowChunk*, const double2*, long long,
-                                  const double2*, const int*, double2*, cudaStream_t);
-template void gm_xupdate<float2>(const GmresDims&, const RowChunk*, const float2*, long long,
-                                 const double2*, const int*, double2*, cudaStream_t);
+template void gm_scale<float2, float2>(const GmresDims&, const RowChunk*, const float2*, const double*, const int*,
+                                       float2*, cudaStream_t);

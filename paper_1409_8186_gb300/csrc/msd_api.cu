@@ -110,8 +110,6 @@ T* dalloc(size_t n) {
     return d;
 }
 
-const int kTargetCtas = 4 * 152;  // a few CTAs per SM of the GB300
-
 }  // namespace
 
 // ---------------------------------------------------------------- problem
@@ -318,45 +316,54 @@ struct SolveCtx {
     int m;
     // FP64 vectors [Ntot][R]
     double2 *b, *x, *r, *Ax;
-    // per-system arrays
-    double2 *h1, *h2, *wn2, *H, *cs, *sn, *g, *y;
+    // per-system arrays ([S][hstride] for projections and norms)
+    double2 *h1, *h2, *wn2, *wn2b, *H, *cs, *sn, *g, *y, *lsq_work;
     double *beta, *vscale, *tol_abs, *tol_cycle;
-    int *active, *kconv, *iters, *flags;  // flags[0] any_active, flags[1] nonfinite
+    int *active, *kconv, *iters, *skip2, *flags;  // flags[0] any_active, flags[1] nonfinite
     int hstride;
+    double2* part;  // [nchunk][m + 2][R] reduction partials
 };
 
+// ||u||^2 per system into out[s * hstride] (FP64 vectors)
+void norm2_f64(SolveCtx& cx, const double2* u, double2* out) {
+    gm_dots<double2>(cx.d, cx.pb->d_chunks, cx.pb->d_cfg_chunk_off, nullptr, 0, 0, 1, u, nullptr, cx.part, out,
+                     cx.hstride, cx.pb->stream);
+}
+
+// One restart cycle of GMRES on P^-1 A d = r (x += d), basis type V.
 template <typename V>
 void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* steps_taken) {
     msd_problem* pb = cx.pb;
     cudaStream_t s = pb->stream;
     const GmresDims& d = cx.d;
     const long long vstride = pb->Ntot * d.R;
-    double2* part = (double2*)pb->sbuf[0].get((size_t)d.nchunk * (cx.m + 1) * d.R * sizeof(double2));
-    // r . r -> rr (reuse wn2)
-    gm_multidot<double2>(d, pb->d_chunks, pb->d_cfg_chunk_off, cx.r, vstride, 1, cx.r, part, cx.wn2,
-                         cx.hstride, 0, s);
+    const RowChunk* ch = pb->d_chunks;
+    const int* co = pb->d_cfg_chunk_off;
+    norm2_f64(cx, cx.r, cx.wn2);
     CK(cudaMemsetAsync(cx.flags, 0, 2 * sizeof(int), s));
     gm_start(d, cx.wn2, cx.hstride, cx.tol_abs, cx.beta, cx.vscale, cx.g, cx.active, cx.kconv, cx.flags, s);
-    gm_scale<double2, V>(d, pb->d_chunks, cx.r, cx.vscale, cx.active, Vb, s);
+    gm_scale<double2, V>(d, ch, cx.r, cx.vscale, cx.active, Vb, s);
     CK_LAUNCH();
-    int any = 0;
     CK(cudaMemcpyAsync(pb->h_pinned, cx.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    any = pb->h_pinned[0];
+    int any = pb->h_pinned[0];
     int j = 0;
     for (; any && j < cx.m && j < maxit_left; ++j) {
         V* vj = Vb + (long long)j * vstride;
         matvec_dev(pb, d.R, fp64, vj, w);
-        gm_multidot<V>(d, pb->d_chunks, pb->d_cfg_chunk_off, Vb, vstride, j + 1, w, part, cx.h1, cx.hstride, 0, s);
-        gm_update<V>(d, pb->d_chunks, Vb, vstride, j + 1, cx.h1, cx.hstride, w, s);
-        gm_multidot<V>(d, pb->d_chunks, pb->d_cfg_chunk_off, Vb, vstride, j + 1, w, part, cx.h2, cx.hstride, 0, s);
-        gm_update<V>(d, pb->d_chunks, Vb, vstride, j + 1, cx.h2, cx.hstride, w, s);
-        gm_multidot<V>(d, pb->d_chunks, pb->d_cfg_chunk_off, w, vstride, 1, w, part, cx.wn2, cx.hstride, 0, s);
+        // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1
+        gm_dots<V>(d, ch, co, Vb, vstride, j + 1, 1, w, nullptr, cx.part, cx.h1, cx.hstride, s);
+        gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, nullptr, -1.0, w, s);
+        gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, nullptr, cx.part, cx.wn2, cx.hstride, s);
+        // second projection only where the first removed more than half of ||w||^2
+        gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
+        gm_dots<V>(d, ch, co, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s);
+        gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h2, cx.hstride, cx.skip2, -1.0, w, s);
+        gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s);
         CK(cudaMemsetAsync(cx.flags, 0, sizeof(int), s));
-        // a step that would exceed the iteration budget ends the cycle for everyone
-        gm_givens(d, j, cx.h1, cx.h2, cx.hstride, cx.wn2, cx.tol_cycle, cx.H, cx.cs, cx.sn, cx.g, cx.vscale,
-                  cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, s);
-        gm_scale<V, V>(d, pb->d_chunks, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
+        gm_givens(d, j, cx.h1, cx.h2, cx.hstride, cx.wn2, cx.wn2b, cx.skip2, cx.tol_cycle, cx.H, cx.cs, cx.sn,
+                  cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, s);
+        gm_scale<V, V>(d, ch, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(pb->h_pinned, cx.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -365,7 +372,6 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
     }
     if (any) {
         // budget exhausted mid-cycle: close the still-active systems at j columns
-        // (their kconv is set here; converged ones keep theirs)
         std::vector<int> act(d.S), kc(d.S);
         CK(cudaMemcpyAsync(act.data(), cx.active, d.S * sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(kc.data(), cx.kconv, d.S * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -376,8 +382,9 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         CK(cudaStreamSynchronize(s));
     }
     *steps_taken = j;
-    gm_lsq(d, cx.H, cx.g, cx.kconv, cx.y, s);
-    gm_xupdate<V>(d, pb->d_chunks, Vb, vstride, cx.y, cx.kconv, cx.x, s);
+    gm_lsq(d, cx.H, cx.g, cx.kconv, cx.y, cx.lsq_work, s);
+    // x += V y, each system over its own kconv columns (y is zero beyond it)
+    gm_update<V, double2>(d, ch, Vb, vstride, j, cx.y, cx.m, nullptr, 1.0, cx.x, s);
     CK_LAUNCH();
 }
 
@@ -431,6 +438,8 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     cx.h1 = (double2*)sb((size_t)S * cx.hstride * 16);
     cx.h2 = (double2*)sb((size_t)S * cx.hstride * 16);
     cx.wn2 = (double2*)sb((size_t)S * cx.hstride * 16);
+    cx.wn2b = (double2*)sb((size_t)S * cx.hstride * 16);
+    cx.lsq_work = (double2*)sb((size_t)S * (m + 1) * 16);
     cx.H = (double2*)sb((size_t)S * m * (m + 1) * 16);
     cx.cs = (double2*)sb((size_t)S * m * 16);
     cx.sn = (double2*)sb((size_t)S * m * 16);
@@ -441,16 +450,17 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     cx.vscale = dsys + S;
     cx.tol_abs = dsys + 2 * S;
     cx.tol_cycle = dsys + 3 * S;
-    int* isys = (int*)sb((size_t)(S * 3 + 2) * 4);
+    int* isys = (int*)sb((size_t)(S * 4 + 2) * 4);
     cx.active = isys;
     cx.kconv = isys + S;
     cx.iters = isys + 2 * S;
-    cx.flags = isys + 3 * S;
+    cx.skip2 = isys + 3 * S;
+    cx.flags = isys + 4 * S;
     const size_t velem = mixed ? 8 : 16;
     void* Vb = sb((size_t)(m + 1) * nv * velem);
     void* w = sb(nv * velem);
     double* d_betas = (double*)sb((size_t)pb->C * R * 8);
-    double2* part = (double2*)pb->sbuf[0].get((size_t)cx.d.nchunk * (m + 1) * R * sizeof(double2));
+    cx.part = (double2*)pb->sbuf[0].get((size_t)cx.d.nchunk * (m + 2) * R * sizeof(double2));
 
     CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
     launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
@@ -461,7 +471,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     gm_zero(nv, cx.x, s);
     CK(cudaMemsetAsync(cx.iters, 0, S * sizeof(int), s));
     // ||b|| per system
-    gm_multidot<double2>(cx.d, pb->d_chunks, pb->d_cfg_chunk_off, cx.b, nv, 1, cx.b, part, cx.wn2, cx.hstride, 0, s);
+    norm2_f64(cx, cx.b, cx.wn2);
     std::vector<double2> hb((size_t)S * cx.hstride);
     CK(cudaMemcpyAsync(hb.data(), cx.wn2, hb.size() * 16, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -484,8 +494,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
             matvec_dev(pb, R, true, cx.x, cx.Ax);
             gm_residual(nv, cx.b, cx.Ax, cx.r, s);
         }
-        gm_multidot<double2>(cx.d, pb->d_chunks, pb->d_cfg_chunk_off, cx.r, nv, 1, cx.r, part, cx.wn2,
-                             cx.hstride, 0, s);
+        norm2_f64(cx, cx.r, cx.wn2);
         CK(cudaMemcpyAsync(hb.data(), cx.wn2, hb.size() * 16, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         bool all = true, improved = false;
@@ -645,8 +654,10 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             pb->d_flags = dalloc<int>(4);
             CK(cudaMemsetAsync(pb->d_flags, 0, 4 * sizeof(int), pb->stream));
             CK(cudaMallocHost((void**)&pb->h_pinned, 64));
-            // reduction chunks: ~kTargetCtas chunks overall, never across configurations
-            const long long target_rows = std::max<long long>(256, row / kTargetCtas);
+            // reduction chunks: at least 2048 rows each (so a block amortises
+            // its tree reductions) and about 128 overall, never across
+            // configurations
+            const long long target_rows = std::max<long long>(2048, row / 128);
             std::vector<int> coff(C + 1, 0);
             for (int c = 0; c < C; ++c) {
                 const MsdConfig& m = pb->cfg[c];

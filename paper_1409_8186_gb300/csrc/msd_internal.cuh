@@ -135,31 +135,29 @@ struct GmresDims {
     int nchunk;       // reduction chunks
 };
 
-// h[s][i] = sum over the rows of cfg(s) of conj(V_i[row][r]) w[row][r], i < nv (FP64 sums).
+// out[s][i] = sum over the rows of cfg(s) of conj(u_i) w for u = V_0..V_{nv-1}
+// (and w itself when self = 1); systems with skip[s] != 0 get zeros.
 template <typename V>
-void gm_multidot(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb,
-                 long long vstride, int nv, const V* w, double2* part, double2* h, int hstride,
-                 int accumulate, cudaStream_t s);
-// w[row][r] -= sum_i V_i[row][r] h[s][i]
-template <typename V>
-void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv,
-               const double2* h, int hstride, V* w, cudaStream_t s);
+void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
+             int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
+             cudaStream_t s);
+// w += sign * sum_i V_i h[s][i]  (skip[s] != 0: unchanged)
+template <typename V, typename W>
+void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv, const double2* h,
+               int hstride, const int* skip, double sign, W* w, cudaStream_t s);
 // v = w * scale[s] for active systems, 0 otherwise
 template <typename Vin, typename Vout>
-void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale,
-              const int* active, Vout* v, cudaStream_t s);
-// x[row][r] += sum_{i < kconv[s]} V_i[row][r] y[s][i]
-template <typename V>
-void gm_xupdate(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride,
-                const double2* y, const int* kconv, double2* x, cudaStream_t s);
+void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale, const int* active,
+              Vout* v, cudaStream_t s);
+void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, const double2* wn2,
+                     const int* active, int* skip2, cudaStream_t s);
 void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* tol_abs, double* beta,
               double* vscale, double2* g, int* active, int* kconv, int* any_active, cudaStream_t s);
-void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride,
-               const double2* wn2, const double* tol_cycle, double2* H, double2* cs, double2* sn,
-               double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
+void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride, const double2* wn2a,
+               const double2* wn2b, const int* skip2, const double* tol_cycle, double2* H, double2* cs,
+               double2* sn, double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
                int* nonfinite, cudaStream_t s);
-void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y,
+void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y, double2* work,
             cudaStream_t s);
 void gm_residual(long long n, const double2* b, const double2* Ax, double2* r, cudaStream_t s);
 void gm_zero(long long n, double2* x, cudaStream_t s);
-void gm_cast_f32(long long n, const double2* a, float2* b, cudaStream_t s);
