@@ -10,21 +10,21 @@
 //
 // Work decomposition: a CTA owns a tile of 32 target disks (one per lane),
 // a contiguous range of source disks q, and RT columns.  Warps split the
-// target modes into blocks of B consecutive m (and the columns into groups
+// target modes into blocks of KB consecutive m (and the columns into groups
 // of RB).  Per source q the CTA stages, with cp.async and double buffering,
 // the 32 generator rows g^{p q}_{.} (contiguous in the [q][p][l] layout) and
 // the RT-column slab of xs^q into shared memory.  Each thread then sweeps n
-// with a register window of B generator values (one new value per n, since
-// neighbouring m need neighbouring l = n - m) and accumulates B x RB complex
-// sums.  Generator rows are padded in shared memory to an odd length so the
-// 32 lanes (32 different rows) hit 32 different banks; the xs slab is a
-// broadcast.  Raw sums go to a per-split partial buffer; a finalize kernel
-// adds the splits, applies l^p_m and adds x.
+// with a register window of KB generator values (one new value per n, since
+// neighbouring m need neighbouring l = n - m) and accumulates KB x RB
+// complex sums.  Generator rows are padded in shared memory to an odd
+// length so the 32 lanes (32 different rows) hit 32 different banks; the
+// xs slab is a broadcast.  KB is chosen per truncation order so that
+// ceil(n / KB) * KB wastes as few padded modes as possible.  Raw sums go to a
+// per-split partial buffer; a finalize kernel adds the splits, applies
+// l^p_m and adds x.
 #include "msd_internal.cuh"
 
 namespace {
-
-constexpr int kB = 8;  // target modes per thread (register window length)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -44,22 +44,19 @@ template <> __device__ __forceinline__ float2 vzero<float2>() { return make_floa
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 
 // Shared-memory footprint (elements) of one stage.
-__host__ __device__ inline int stage_g_elems(int L) { return MSD_TILE_P * (L + 2 * kB); }
-__host__ __device__ inline int stage_x_elems(int n, int RT) {
-    int I = (n + kB - 1) / kB;
-    return I * kB * RT;
-}
+__host__ __device__ inline int stage_g_elems(int L, int KB) { return MSD_TILE_P * (L + 2 * KB); }
+__host__ __device__ inline int stage_x_elems(int n, int RT, int KB) { return ((n + KB - 1) / KB) * KB * RT; }
 
-// Complex multiply-accumulate policies over a B x RB register tile.
+// Complex multiply-accumulate policies over a KB x RB register tile.
 // Mac4: the textbook product, 4 real FMAs per complex MAC (FP32 path).
-template <typename V, int RB>
+template <typename V, int KB, int RB>
 struct Mac4 {
     struct G { V g; };
     struct X { V x; };
-    V acc[kB][RB];
+    V acc[KB][RB];
     __device__ __forceinline__ void init() {
 #pragma unroll
-        for (int b = 0; b < kB; ++b)
+        for (int b = 0; b < KB; ++b)
 #pragma unroll
             for (int r = 0; r < RB; ++r) acc[b][r] = vzero<V>();
     }
@@ -75,14 +72,14 @@ struct Mac4 {
 // then Re = k1 - k3, Im = k1 + k2.  The sums c+d, d-c are formed once per
 // generator value entering the register window and a+b once per source
 // value, so a complex MAC costs 3 FMAs instead of 4.
-template <typename V, int RB>
+template <typename V, int KB, int RB>
 struct Mac3 {
     struct G { double c, u, v; };
     struct X { double a, b, s; };
-    double k1[kB][RB], k2[kB][RB], k3[kB][RB];
+    double k1[KB][RB], k2[KB][RB], k3[KB][RB];
     __device__ __forceinline__ void init() {
 #pragma unroll
-        for (int b = 0; b < kB; ++b)
+        for (int b = 0; b < KB; ++b)
 #pragma unroll
             for (int r = 0; r < RB; ++r) k1[b][r] = k2[b][r] = k3[b][r] = 0.0;
     }
@@ -98,16 +95,11 @@ struct Mac3 {
     }
 };
 
-template <typename V, int RB> struct MacFor { typedef Mac4<V, RB> type; };
-template <int RB> struct MacFor<double2, RB> { typedef Mac3<double2, RB> type; };
+template <typename V, int KB, int RB> struct MacFor { typedef Mac4<V, KB, RB> type; };
+template <int KB, int RB> struct MacFor<double2, KB, RB> { typedef Mac3<double2, KB, RB> type; };
 
-// Threads per CTA at most: 512 for FP32 (<= 128 registers), 256 for FP64 so
-// that the three-sum accumulators and the converted window stay in registers.
-template <typename V> struct MaxThreads { static constexpr int value = 512; };
-template <> struct MaxThreads<double2> { static constexpr int value = 256; };
-
-template <typename V, int RT, int RB>
-__global__ void __launch_bounds__(MaxThreads<V>::value) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
+template <typename V, int RT, int RB, int KB>
+__global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
                                                    const MatvecWork* __restrict__ works,
                                                    const V* __restrict__ G, const V* __restrict__ xs,
                                                    V* __restrict__ part, long long Ntot, int R, int rtiles) {
@@ -119,10 +111,10 @@ __global__ void __launch_bounds__(MaxThreads<V>::value) k_bt_matvec(const MsdCon
     const MatvecWork w = works[wi];
     const MsdConfig c = cfgs[w.cfg];
     const int N = c.N, n = c.n, L = c.L;
-    const int Ls = L + 2 * kB;
-    const int I = (n + kB - 1) / kB;
-    const int npad = I * kB;
-    const int gsz = stage_g_elems(L), xsz = stage_x_elems(n, RT);
+    const int Ls = L + 2 * KB;
+    const int I = (n + KB - 1) / KB;
+    const int npad = I * KB;
+    const int gsz = stage_g_elems(L, KB), xsz = stage_x_elems(n, RT, KB);
     V* gbuf[2] = {smem, smem + gsz + xsz};
     V* xbuf[2] = {smem + gsz, smem + 2 * gsz + xsz};
 
@@ -136,15 +128,15 @@ __global__ void __launch_bounds__(MaxThreads<V>::value) k_bt_matvec(const MsdCon
     const int mblk = warp % Imax;
     const int rgrp = warp / Imax;
     const bool mact = mblk < I;
-    const int m0 = mblk * kB;
-    const int c0 = rgrp * RB;         // first column of this thread within the tile
-    const int col0 = rt * RT;         // first column of the tile
+    const int m0 = mblk * KB;
+    const int c0 = rgrp * RB;  // first column of this thread within the tile
+    const int col0 = rt * RT;  // first column of the tile
 
     // zero the padding of both stages once (staging never writes it)
     for (int s = 0; s < 2; ++s) {
-        for (int t = tid; t < MSD_TILE_P * 2 * kB; t += nthreads) {
-            int row = t / (2 * kB), j = t % (2 * kB);
-            int pos = j < kB ? j : (L + j);
+        for (int t = tid; t < MSD_TILE_P * 2 * KB; t += nthreads) {
+            const int row = t / (2 * KB), j = t % (2 * KB);
+            const int pos = j < KB ? j : (L + j);
             gbuf[s][row * Ls + pos] = vzero<V>();
         }
         for (int t = n * RT + tid; t < npad * RT; t += nthreads) xbuf[s][t] = vzero<V>();
@@ -153,51 +145,59 @@ __global__ void __launch_bounds__(MaxThreads<V>::value) k_bt_matvec(const MsdCon
     const V* gsrc_cfg = G + c.gen_off + (long long)w.p0 * L;
     auto stage = [&](int q, int s) {
         const V* src = gsrc_cfg + (long long)q * c.Mp * L;
-        V* dst = gbuf[s];
+        V* dst = gbuf[s] + KB;
+        // row-major walk of the 32 x L tile: (row, j) advanced incrementally
+        int row = tid / L, j = tid - (tid / L) * L;
+        const int drow = nthreads / L, dj = nthreads - drow * L;
         for (int t = tid; t < MSD_TILE_P * L; t += nthreads) {
-            int row = t / L, j = t - row * L;
-            cp_async(dst + row * Ls + kB + j, src + t);
+            cp_async(dst + row * Ls + j, src + t);
+            row += drow;
+            j += dj;
+            if (j >= L) {
+                j -= L;
+                ++row;
+            }
         }
         const V* xsrc = xs + (c.row_off + (long long)q * n) * R + col0;
         V* xd = xbuf[s];
         for (int t = tid; t < n * RT; t += nthreads) {
-            int rr = t / RT, cc = t - rr * RT;
+            const int rr = t / RT, cc = t - rr * RT;
             cp_async(xd + t, xsrc + (long long)rr * R + cc);
         }
     };
 
-    typedef typename MacFor<V, RB>::type Mac;
+    typedef typename MacFor<V, KB, RB>::type Mac;
     Mac acc;
     acc.init();
 
     if (w.q0 < w.q1) stage(w.q0, 0);
     cp_commit();
-    const int base = kB + 2 * N - m0;  // smem position of l' = n - m0 + 2N at n = 0
+    const int base = KB + 2 * N - m0;  // smem position of l' = n - m0 + 2N at n = 0
     for (int it = 0, q = w.q0; q < w.q1; ++it, ++q) {
         if (q + 1 < w.q1) stage(q + 1, (it + 1) & 1);
         cp_commit();
         cp_wait<1>();
         __syncthreads();
         if (mact) {
-        const V* gs = gbuf[it & 1] + lane * Ls + base;
-        const V* xsl = xbuf[it & 1] + c0;
-        typename Mac::G win[kB];
+            const V* gs = gbuf[it & 1] + lane * Ls + base;
+            const V* xsl = xbuf[it & 1] + c0;
+            typename Mac::G win[KB];
 #pragma unroll
-        for (int j = 1; j < kB; ++j) win[kB - j] = Mac::gen(gs[-j]);
-        for (int nb = 0; nb < npad; nb += kB) {
+            for (int j = 1; j < KB; ++j) win[KB - j] = Mac::gen(gs[-j]);
+            for (int nb = 0; nb < npad; nb += KB) {
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                win[u] = Mac::gen(gs[nb + u]);
-                typename Mac::X xv[RB];
+                for (int u = 0; u < KB; ++u) {
+                    win[u] = Mac::gen(gs[nb + u]);
+                    typename Mac::X xv[RB];
 #pragma unroll
-                for (int r = 0; r < RB; ++r) xv[r] = Mac::src(xsl[(nb + u) * RT + r]);
+                    for (int r = 0; r < RB; ++r) xv[r] = Mac::src(xsl[(nb + u) * RT + r]);
 #pragma unroll
-                for (int b = 0; b < kB; ++b) {
+                    for (int b = 0; b < KB; ++b) {
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) acc.mac(b, r, win[(u - b + kB) % kB], xv[r]);
+                        for (int r = 0; r < RB; ++r) acc.mac(b, r, win[(u - b + KB) % KB], xv[r]);
+                    }
                 }
             }
-        }
         }
         __syncthreads();
     }
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(MaxThreads<V>::value) k_bt_matvec(const MsdCon
     if (mact && p < c.M) {
         V* out = part + (long long)w.split * Ntot * R;
 #pragma unroll
-        for (int b = 0; b < kB; ++b) {
+        for (int b = 0; b < KB; ++b) {
             const int mi = m0 + b;
             if (mi < n) {
                 const long long row = c.row_off + (long long)p * n + mi;
@@ -246,77 +246,142 @@ __global__ void k_finalize(long long Ntot, int R, int nsplit, const V* __restric
     y[i] = V{v.x + (l.x * s.x - l.y * s.y), v.y + (l.x * s.y + l.y * s.x)};
 }
 
-template <typename V, int RT, int RB>
-void launch_bt(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const V* G,
-               const V* xs, V* part, long long Ntot, int R, cudaStream_t s) {
-    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
-    const int I = (n + kB - 1) / kB;
-    const int rtiles = R / RT;
-    dim3 block(32, I * (RT / RB));
-    size_t smem = 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * sizeof(V);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_bt_matvec<V, RT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-        attr_set = true;
-    }
-    k_bt_matvec<V, RT, RB><<<(unsigned)(nwork * rtiles), block, smem, s>>>(d_cfg, d_work, G, xs, part,
-                                                                          Ntot, R, rtiles);
-}
+// ---------------------------------------------------------------- kernel selection
 
-}  // namespace
+// Candidate window lengths: FP64 keeps the three-sum accumulators and the
+// converted window in <= 128 registers up to KB = 7; FP32 up to KB = 9.
+constexpr int kKbMin = 4;
+constexpr int kKbMax64 = 7;
+constexpr int kKbMax32 = 9;
 
-// Column tile RT for R columns: the largest power of two dividing R such
-// that the CTA stays within 16 warps (I m-blocks x RT/RB column groups).
-int matvec_col_tile(int R, int Nmax, bool fp64) {
-    // FP64: one column per CTA (the FP64 pipe, not the generator traffic,
-    // bounds the product; more columns per thread would spill registers)
-    if (fp64) return 1;
+struct Choice {
+    int KB, RT, RB, I;
+};
+
+Choice choose(int R, int Nmax, bool fp64) {
     const int n = 2 * Nmax + 1;
-    const int I = (n + kB - 1) / kB;
-    const int rb_max = 4;
-    int best = 1;
-    for (int rt = 1; rt <= 16; rt *= 2) {
-        if (R % rt) break;
-        int rb = rt < rb_max ? rt : rb_max;
-        if (I * (rt / rb) <= 16) best = rt;
+    Choice best{8, 1, 1, 0};
+    double best_cost = 1e300;
+    for (int KB = kKbMin; KB <= (fp64 ? kKbMax64 : kKbMax32); ++KB) {
+        const int I = (n + KB - 1) / KB;
+        if (I > 16) continue;
+        const double pad = (double)I * KB;
+        // padded MACs times the per-MAC instruction overhead of the window
+        // (3 extra FP64 adds per KB x 3 FMAs, or ~3 extra instructions per
+        // KB x 4 FFMAs)
+        const double cost = pad * pad * (fp64 ? (1.0 + 1.0 / KB) : (1.0 + 0.75 / KB));
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = Choice{KB, 1, 1, I};
+        }
+    }
+    if (!fp64) {
+        const int rb_max = 4;
+        for (int rt = 2; rt <= 16; rt *= 2) {
+            if (R % rt) break;
+            const int rb = rt < rb_max ? rt : rb_max;
+            if (best.I * (rt / rb) <= 16) {
+                best.RT = rt;
+                best.RB = rb;
+            }
+        }
     }
     return best;
 }
 
-size_t matvec_smem_bytes(int R, int Nmax, bool fp64) {
-    const int RT = matvec_col_tile(R, Nmax, fp64);
-    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
-    return 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * (fp64 ? 16 : 8);
+template <typename V, int RT, int RB, int KB>
+struct Bt {
+    static void attr() {
+        static bool done = false;
+        if (!done) {
+            cudaFuncSetAttribute(k_bt_matvec<V, RT, RB, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024);
+            done = true;
+        }
+    }
+    static size_t smem(int Nmax) {
+        const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
+        return 2 * (size_t)(stage_g_elems(L, KB) + stage_x_elems(n, RT, KB)) * sizeof(V);
+    }
+    static dim3 block(int Nmax) {
+        const int n = 2 * Nmax + 1;
+        return dim3(32, ((n + KB - 1) / KB) * (RT / RB));
+    }
+    static void launch(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const V* G,
+                       const V* xs, V* part, long long Ntot, int R, cudaStream_t s) {
+        attr();
+        const int rtiles = R / RT;
+        k_bt_matvec<V, RT, RB, KB><<<(unsigned)(nwork * rtiles), block(Nmax), smem(Nmax), s>>>(
+            d_cfg, d_work, G, xs, part, Ntot, R, rtiles);
+    }
+    static int occupancy(int Nmax) {
+        attr();
+        const dim3 b = block(Nmax);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB, KB>, b.x * b.y,
+                                                          smem(Nmax)) != cudaSuccess) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        return nb < 1 ? 1 : nb;
+    }
+};
+
+// Dispatch on (RT, RB) for a fixed KB (FP32), or KB alone (FP64).
+template <int KB, typename F>
+void with_f32(const Choice& c, F&& f) {
+    switch (c.RT) {
+        case 1: f(Bt<float2, 1, 1, KB>()); break;
+        case 2: f(Bt<float2, 2, 2, KB>()); break;
+        case 4: f(Bt<float2, 4, 4, KB>()); break;
+        case 8: f(Bt<float2, 8, 4, KB>()); break;
+        default: f(Bt<float2, 16, 4, KB>()); break;
+    }
 }
 
-namespace {
-template <typename V, int RT, int RB>
-int occupancy(int Nmax) {
-    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
-    const int I = (n + kB - 1) / kB;
-    const int threads = 32 * I * (RT / RB);
-    const size_t smem = 2 * (size_t)(stage_g_elems(L) + stage_x_elems(n, RT)) * sizeof(V);
-    cudaFuncSetAttribute(k_bt_matvec<V, RT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB>, threads, smem) != cudaSuccess) {
-        cudaGetLastError();
-        nb = 1;
+template <typename F>
+void dispatch64(const Choice& c, F&& f) {
+    switch (c.KB) {
+        case 4: f(Bt<double2, 1, 1, 4>()); break;
+        case 5: f(Bt<double2, 1, 1, 5>()); break;
+        case 6: f(Bt<double2, 1, 1, 6>()); break;
+        default: f(Bt<double2, 1, 1, 7>()); break;
     }
-    return nb < 1 ? 1 : nb;
 }
+
+template <typename F>
+void dispatch32(const Choice& c, F&& f) {
+    switch (c.KB) {
+        case 4: with_f32<4>(c, f); break;
+        case 5: with_f32<5>(c, f); break;
+        case 6: with_f32<6>(c, f); break;
+        case 7: with_f32<7>(c, f); break;
+        case 8: with_f32<8>(c, f); break;
+        default: with_f32<9>(c, f); break;
+    }
+}
+
+template <typename F>
+void dispatch(const Choice& c, bool fp64, F&& f) {
+    if (fp64) dispatch64(c, f);
+    else dispatch32(c, f);
+}
+
 }  // namespace
+
+int matvec_col_tile(int R, int Nmax, bool fp64) { return choose(R, Nmax, fp64).RT; }
+
+size_t matvec_smem_bytes(int R, int Nmax, bool fp64) {
+    size_t b = 0;
+    dispatch(choose(R, Nmax, fp64), fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
+    return b;
+}
 
 // Resident CTAs per SM of the product kernel chosen for (R, Nmax, precision).
 int matvec_blocks_per_sm(int R, int Nmax, bool fp64) {
-    if (fp64) return occupancy<double2, 1, 1>(Nmax);
-    switch (matvec_col_tile(R, Nmax, fp64)) {
-        case 1: return occupancy<float2, 1, 1>(Nmax);
-        case 2: return occupancy<float2, 2, 2>(Nmax);
-        case 4: return occupancy<float2, 4, 4>(Nmax);
-        case 8: return occupancy<float2, 8, 4>(Nmax);
-        default: return occupancy<float2, 16, 4>(Nmax);
-    }
+    int nb = 1;
+    dispatch(choose(R, Nmax, fp64), fp64, [&](auto k) { nb = decltype(k)::occupancy(Nmax); });
+    return nb;
 }
 
 void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
@@ -328,7 +393,9 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<double2, double><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
-    launch_bt<double2, 1, 1>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
+    dispatch64(choose(R, Nmax, true), [&](auto k) {
+        decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
+    });
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize<double2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;
@@ -343,13 +410,9 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
-    switch (matvec_col_tile(R, Nmax, false)) {
-        case 1: launch_bt<float2, 1, 1>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        case 2: launch_bt<float2, 2, 2>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        case 4: launch_bt<float2, 4, 4>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        case 8: launch_bt<float2, 8, 4>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-        default: launch_bt<float2, 16, 4>(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); break;
-    }
+    dispatch32(choose(R, Nmax, false), [&](auto k) {
+        decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
+    });
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize<float2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;
