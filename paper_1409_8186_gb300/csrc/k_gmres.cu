@@ -26,12 +26,17 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kI = 8;    // basis vectors per dot-product block
-constexpr int kU = 32;   // basis vectors per update block
+constexpr int kU = 16;   // basis vectors per update block
 
 template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return make_double2(v.x, v.y); }
 
 // Column lanes RC = min(R, 32); row lanes RY = largest power of two with RY * RC <= threads.
-__host__ __device__ inline int col_lanes(int R) { return R < 32 ? R : 32; }
+// (a power of two, so that lanes of one column are xor-shuffle partners)
+__host__ __device__ inline int col_lanes(int R) {
+    int c = 1;
+    while (c < R && c < 32) c *= 2;
+    return c;
+}
 __device__ inline int row_lanes(int RC) {
     int RY = 1;
     while (RY * 2 * RC <= (int)blockDim.x) RY *= 2;
@@ -58,16 +63,17 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
                             const int* __restrict__ skip, double2* __restrict__ part) {
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
-    const int RY = row_lanes(RC);
+    const int RY = blockDim.x / RC;  // kThreads and RC are powers of two
     const int tx = threadIdx.x % RC, ty = threadIdx.x / RC;
     const int r = blockIdx.y * RC + tx;
     const int i0 = blockIdx.z * kI;
     const int nvv = nv + self;
-    __shared__ double2 red[kThreads];
+    constexpr int kWarps = kThreads / 32;
+    __shared__ double2 red[kWarps][32][kI];
     double2 acc[kI];
 #pragma unroll
     for (int ii = 0; ii < kI; ++ii) acc[ii] = make_double2(0.0, 0.0);
-    const bool live = ty < RY && r < R && !(skip && skip[ch.cfg * R + r]);
+    const bool live = r < R && !(skip && skip[ch.cfg * R + r]);
     if (live) {
         for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
             const double2 wv = to_d2(w[row * R + r]);
@@ -82,19 +88,28 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
             }
         }
     }
-    for (int ii = 0; ii < kI && i0 + ii < nvv; ++ii) {
-        red[threadIdx.x] = acc[ii];
-        __syncthreads();
-        for (int st = RY / 2; st > 0; st /= 2) {
-            if (ty < st) {
-                const double2 o = red[threadIdx.x + st * RC];
-                red[threadIdx.x].x += o.x;
-                red[threadIdx.x].y += o.y;
-            }
-            __syncthreads();
+    // lanes lane and lane ^ off (off >= RC) hold the same column: fold them
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int ii = 0; ii < kI; ++ii) {
+        for (int off = 16; off >= RC; off >>= 1) {
+            acc[ii].x += __shfl_xor_sync(0xffffffffu, acc[ii].x, off);
+            acc[ii].y += __shfl_xor_sync(0xffffffffu, acc[ii].y, off);
         }
-        if (ty == 0 && r < R) part[((long long)blockIdx.x * nvv + (i0 + ii)) * R + r] = red[tx];
-        __syncthreads();
+        if (lane < RC) red[warp][lane][ii] = acc[ii];
+    }
+    __syncthreads();
+    // one thread per (column lane, vector) adds the warps' partials
+    for (int t = threadIdx.x; t < RC * kI; t += blockDim.x) {
+        const int cl = t % RC, ii = t / RC;
+        const int rr = blockIdx.y * RC + cl;
+        if (rr >= R || i0 + ii >= nvv) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int wv = 0; wv < kWarps; ++wv) {  // every warp carries all RC columns
+            s.x += red[wv][cl][ii].x;
+            s.y += red[wv][cl][ii].y;
+        }
+        part[((long long)blockIdx.x * nvv + (i0 + ii)) * R + rr] = s;
     }
 }
 

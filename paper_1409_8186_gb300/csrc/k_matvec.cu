@@ -230,17 +230,29 @@ __global__ void k_scale_cols(long long Ntot, int R, const S* __restrict__ rf, co
 }
 
 // y = x + lf .* sum_s part[s]
+// (kFinLanes threads per element split the partial slots, then shuffle-add)
+constexpr int kFinLanes = 8;
 template <typename V>
 __global__ void k_finalize(long long Ntot, int R, int nsplit, const V* __restrict__ lf,
                            const V* __restrict__ x, const V* __restrict__ part, V* __restrict__ y) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Ntot * R) return;
-    V s = part[i];
-    for (int k = 1; k < nsplit; ++k) {
-        const V t = part[(long long)k * Ntot * R + i];
-        s.x += t.x;
-        s.y += t.y;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = t / kFinLanes;
+    const int sub = (int)(t % kFinLanes);
+    const long long tot = Ntot * R;
+    V s = vzero<V>();
+    if (i < tot) {
+        for (int k = sub; k < nsplit; k += kFinLanes) {
+            const V v = part[(long long)k * tot + i];
+            s.x += v.x;
+            s.y += v.y;
+        }
     }
+#pragma unroll
+    for (int off = kFinLanes / 2; off > 0; off >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+    }
+    if (i >= tot || sub != 0) return;
     const V l = lf[i / R];
     const V v = x[i];
     y[i] = V{v.x + (l.x * s.x - l.y * s.y), v.y + (l.x * s.y + l.y * s.x)};
@@ -397,7 +409,7 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
         decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
     });
     if (ev1) cudaEventRecord(ev1, s);
-    k_finalize<double2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
+    k_finalize<double2><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;
 }
 
@@ -414,6 +426,6 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
         decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
     });
     if (ev1) cudaEventRecord(ev1, s);
-    k_finalize<float2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
+    k_finalize<float2><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;
 }

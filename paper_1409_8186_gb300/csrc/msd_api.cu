@@ -143,7 +143,8 @@ struct msd_problem {
     std::vector<RowChunk> chunks;
     RowChunk* d_chunks = nullptr;
     int* d_cfg_chunk_off = nullptr;
-    int* h_pinned = nullptr;  // small pinned host flags
+    int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags
+    cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf xs, part, sbuf[24];
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
@@ -347,8 +348,19 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
     CK(cudaMemcpyAsync(pb->h_pinned, cx.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     int any = pb->h_pinned[0];
+    // The host reads the convergence flags of step j - kLag while step j is
+    // queued, so the GPU never waits for the host; the (at most kLag) steps
+    // queued after the last system converged run on zero vectors and change
+    // nothing.
+    constexpr int kLag = 2, kRing = 4;
     int j = 0;
     for (; any && j < cx.m && j < maxit_left; ++j) {
+        if (j >= kLag) {
+            const int slot = (j - kLag) % kRing;
+            CK(cudaEventSynchronize(pb->ring_ev[slot]));
+            if (pb->h_pinned[2 + 2 * slot + 1]) fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+            if (!pb->h_pinned[2 + 2 * slot]) break;
+        }
         V* vj = Vb + (long long)j * vstride;
         matvec_dev(pb, d.R, fp64, vj, w);
         // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1
@@ -365,10 +377,16 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
                   cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, s);
         gm_scale<V, V>(d, ch, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
         CK_LAUNCH();
-        CK(cudaMemcpyAsync(pb->h_pinned, cx.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        any = pb->h_pinned[0];
-        if (pb->h_pinned[1]) fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+        const int slot = j % kRing;
+        CK(cudaMemcpyAsync(pb->h_pinned + 2 + 2 * slot, cx.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(pb->ring_ev[slot], s));
+    }
+    // settle: the last queued steps decide whether any system is still active
+    CK(cudaStreamSynchronize(s));
+    if (j > 0) {
+        const int slot = (j - 1) % kRing;
+        if (pb->h_pinned[2 + 2 * slot + 1]) fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+        any = pb->h_pinned[2 + 2 * slot];
     }
     if (any) {
         // budget exhausted mid-cycle: close the still-active systems at j columns
@@ -654,10 +672,11 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             pb->d_flags = dalloc<int>(4);
             CK(cudaMemsetAsync(pb->d_flags, 0, 4 * sizeof(int), pb->stream));
             CK(cudaMallocHost((void**)&pb->h_pinned, 64));
-            // reduction chunks: at least 2048 rows each (so a block amortises
-            // its tree reductions) and about 128 overall, never across
-            // configurations
-            const long long target_rows = std::max<long long>(2048, row / 128);
+            for (auto& e : pb->ring_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            // reduction chunks: at least 512 rows each (two or more rows per
+            // thread of a reduction block) and about 256 overall, never
+            // across configurations
+            const long long target_rows = std::max<long long>(512, row / 256);
             std::vector<int> coff(C + 1, 0);
             for (int c = 0; c < C; ++c) {
                 const MsdConfig& m = pb->cfg[c];
@@ -700,6 +719,8 @@ void msd_destroy(msd_problem* pb) {
         if (kv.second.d_work) cudaFree(kv.second.d_work);
     if (pb->h_pinned) cudaFreeHost(pb->h_pinned);
     for (cudaEvent_t e : pb->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : pb->ring_ev)
+        if (e) cudaEventDestroy(e);
     pb->xs.release();
     pb->part.release();
     for (auto& b : pb->sbuf) b.release();
