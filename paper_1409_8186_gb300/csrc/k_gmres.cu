@@ -8,8 +8,10 @@
 //
 // Orthogonalisation is classical Gram-Schmidt with one selective
 // re-orthogonalisation pass (Daniel-Gragg-Kaufman-Stewart criterion: repeat
-// the projection when it removed more than half of ||w||^2).  Dot products
-// accumulate in FP64 whatever the storage type of the basis.  Vectors are
+// the projection when it removed more than half of ||w||^2).  Per-thread
+// sums of dot products and updates run in the storage precision of the
+// basis (FP32 for the inner sweeps of a mixed solve, whose FP64 pipe would
+// otherwise bound them) and cross-thread reductions in FP64.  Vectors are
 // [rows][R] with R innermost; reductions run over row chunks that never
 // straddle two configurations; projections V^H w and updates w -= V h are
 // tiled over (row chunk, group of basis vectors) so that long Krylov bases
@@ -70,20 +72,25 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
     const int nvv = nv + self;
     constexpr int kWarps = kThreads / 32;
     __shared__ double2 red[kWarps][32][kI];
-    double2 acc[kI];
+    // Per-thread sums run in the storage precision (a handful of rows per
+    // thread); they are widened to FP64 for the cross-lane and cross-warp
+    // reduction.  An FP32 basis therefore costs FP32 arithmetic: the FP64
+    // pipe of this GPU is a small fraction of the FP32 one.
+    typedef decltype(V{}.x) A;
+    A ax[kI], ay[kI];
 #pragma unroll
-    for (int ii = 0; ii < kI; ++ii) acc[ii] = make_double2(0.0, 0.0);
+    for (int ii = 0; ii < kI; ++ii) ax[ii] = ay[ii] = A(0);
     const bool live = r < R && !(skip && skip[ch.cfg * R + r]);
     if (live) {
         for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-            const double2 wv = to_d2(w[row * R + r]);
+            const V wv = w[row * R + r];
 #pragma unroll
             for (int ii = 0; ii < kI; ++ii) {
                 const int i = i0 + ii;
                 if (i < nvv) {
-                    const double2 vv = i < nv ? to_d2(Vb[(long long)i * vstride + row * R + r]) : wv;
-                    acc[ii].x += vv.x * wv.x + vv.y * wv.y;  // conj(v) * w
-                    acc[ii].y += vv.x * wv.y - vv.y * wv.x;
+                    const V vv = i < nv ? Vb[(long long)i * vstride + row * R + r] : wv;
+                    ax[ii] = fma(vv.x, wv.x, fma(vv.y, wv.y, ax[ii]));  // conj(v) * w
+                    ay[ii] = fma(vv.x, wv.y, fma(-vv.y, wv.x, ay[ii]));
                 }
             }
         }
@@ -92,11 +99,12 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int ii = 0; ii < kI; ++ii) {
+        double2 acc = make_double2((double)ax[ii], (double)ay[ii]);
         for (int off = 16; off >= RC; off >>= 1) {
-            acc[ii].x += __shfl_xor_sync(0xffffffffu, acc[ii].x, off);
-            acc[ii].y += __shfl_xor_sync(0xffffffffu, acc[ii].y, off);
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
         }
-        if (lane < RC) red[warp][lane][ii] = acc[ii];
+        if (lane < RC) red[warp][lane][ii] = acc;
     }
     __syncthreads();
     // one thread per (column lane, vector) adds the warps' partials
@@ -131,47 +139,57 @@ __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_ch
 }
 
 // w[row][r] += sign * sum_{i in block's group, i < nv} V_i[row][r] h[s][i].
-// With more than one vector group the groups meet in atomics; with one
-// group the result is stored directly.
+// The block's slice of h (times sign) is staged in shared memory in the
+// basis storage type and the sums run in that precision (FP32 for an FP32
+// basis: the correction it builds only needs the accuracy of the FP32
+// sweep).  With more than one vector group the groups meet in atomics;
+// with one group the result is stored directly.
 template <typename V, typename W>
 __global__ void k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
                          int nv, const double2* __restrict__ h, int hstride, const int* __restrict__ skip,
                          double sign, W* __restrict__ w) {
+    typedef decltype(V{}.x) A;
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
     const int RY = blockDim.x / RC;
     const int tx = threadIdx.x % RC, ty = threadIdx.x / RC;
     const int r = blockIdx.y * RC + tx;
-    if (ty >= RY || r >= R) return;
-    const int s = ch.cfg * R + r;
-    if (skip && skip[s]) return;
     const int i0 = blockIdx.z * kU;
     const int i1 = min(nv, i0 + kU);
-    if (i0 >= i1) return;
-    const double2* hs = h + (long long)s * hstride;
+    __shared__ V hsm[kU][32];
+    for (int t = threadIdx.x; t < kU * RC; t += blockDim.x) {
+        const int ii = t / RC, cl = t % RC;
+        const int rr = blockIdx.y * RC + cl;
+        double2 v = make_double2(0.0, 0.0);
+        if (rr < R && i0 + ii < i1) v = h[(long long)(ch.cfg * R + rr) * hstride + i0 + ii];
+        hsm[ii][cl] = V{(A)(sign * v.x), (A)(sign * v.y)};
+    }
+    __syncthreads();
+    if (r >= R || i0 >= i1) return;
+    if (skip && skip[ch.cfg * R + r]) return;
     const bool atomic = gridDim.z > 1;
+    const int cnt = i1 - i0;
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-        double2 a[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
-                        make_double2(0.0, 0.0)};
-        const V* vp = Vb + row * R + r;
-        int i = i0;
-        for (; i + 4 <= i1; i += 4) {
+        A ax[4] = {A(0), A(0), A(0), A(0)}, ay[4] = {A(0), A(0), A(0), A(0)};
+        const V* vp = Vb + (long long)i0 * vstride + row * R + r;
+        int i = 0;
+        for (; i + 4 <= cnt; i += 4) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const double2 vv = to_d2(vp[(long long)(i + u) * vstride]);
-                const double2 hh = hs[i + u];
-                a[u].x += vv.x * hh.x - vv.y * hh.y;
-                a[u].y += vv.x * hh.y + vv.y * hh.x;
+                const V vv = vp[(long long)(i + u) * vstride];
+                const V hh = hsm[i + u][tx];
+                ax[u] = fma(vv.x, hh.x, fma(-vv.y, hh.y, ax[u]));
+                ay[u] = fma(vv.x, hh.y, fma(vv.y, hh.x, ay[u]));
             }
         }
-        for (; i < i1; ++i) {
-            const double2 vv = to_d2(vp[(long long)i * vstride]);
-            const double2 hh = hs[i];
-            a[0].x += vv.x * hh.x - vv.y * hh.y;
-            a[0].y += vv.x * hh.y + vv.y * hh.x;
+        for (; i < cnt; ++i) {
+            const V vv = vp[(long long)i * vstride];
+            const V hh = hsm[i][tx];
+            ax[0] = fma(vv.x, hh.x, fma(-vv.y, hh.y, ax[0]));
+            ay[0] = fma(vv.x, hh.y, fma(vv.y, hh.x, ay[0]));
         }
-        const double2 d = make_double2(sign * ((a[0].x + a[1].x) + (a[2].x + a[3].x)),
-                                       sign * ((a[0].y + a[1].y) + (a[2].y + a[3].y)));
+        const double2 d = make_double2((double)((ax[0] + ax[1]) + (ax[2] + ax[3])),
+                                       (double)((ay[0] + ay[1]) + (ay[2] + ay[3])));
         W* p = w + row * R + r;
         if (atomic) {
             atomic_add_v(p, d);
@@ -194,10 +212,12 @@ __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* _
     const int r = blockIdx.y * RC + tx;
     if (ty >= RY || r >= R) return;
     const int s = ch.cfg * R + r;
-    const double f = active[s] ? scale[s] : 0.0;
+    // arithmetic in the wider of the two storage types (FP32 for an FP32 basis)
+    typedef decltype(Vin{}.x + Vout{}.x) A;
+    const A f = (A)(active[s] ? scale[s] : 0.0);
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
-        const double2 a = to_d2(w[row * R + r]);
-        v[row * R + r] = Vout{(decltype(Vout{}.x))(a.x * f), (decltype(Vout{}.x))(a.y * f)};
+        const Vin a = w[row * R + r];
+        v[row * R + r] = Vout{(decltype(Vout{}.x))((A)a.x * f), (decltype(Vout{}.x))((A)a.y * f)};
     }
 }
 
