@@ -99,12 +99,13 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int ii = 0; ii < kI; ++ii) {
-        double2 acc = make_double2((double)ax[ii], (double)ay[ii]);
+        // within a warp in the storage precision (at most 32 terms), across
+        // warps and chunks in FP64
         for (int off = 16; off >= RC; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            ax[ii] += __shfl_xor_sync(0xffffffffu, ax[ii], off);
+            ay[ii] += __shfl_xor_sync(0xffffffffu, ay[ii], off);
         }
-        if (lane < RC) red[warp][lane][ii] = acc;
+        if (lane < RC) red[warp][lane][ii] = make_double2((double)ax[ii], (double)ay[ii]);
     }
     __syncthreads();
     // one thread per (column lane, vector) adds the warps' partials
@@ -122,20 +123,26 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
 }
 
 // out[s * ostride + i] = sum over the chunks of cfg(s) of part[chunk][i][r]
+// (one warp per output: the lanes stride over the chunks, then shuffle-add)
 __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_chunk_off,
                            const double2* __restrict__ part, double2* __restrict__ out, int ostride) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)C * R * nvv) return;
+    const long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (idx >= (long long)C * R * nvv) return;  // uniform across the warp
     const int i = (int)(idx % nvv);
     const int s = (int)(idx / nvv);
     const int c = s / R, r = s % R;
     double2 acc = make_double2(0.0, 0.0);
-    for (int k = cfg_chunk_off[c]; k < cfg_chunk_off[c + 1]; ++k) {
+    for (int k = cfg_chunk_off[c] + lane; k < cfg_chunk_off[c + 1]; k += 32) {
         const double2 v = part[((long long)k * nvv + i) * R + r];
         acc.x += v.x;
         acc.y += v.y;
     }
-    out[(long long)s * ostride + i] = acc;
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) out[(long long)s * ostride + i] = acc;
 }
 
 // w[row][r] += sign * sum_{i in block's group, i < nv} V_i[row][r] h[s][i].
@@ -424,7 +431,7 @@ void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
     dim3 g(d.nchunk, rgroups(d.R), (nvv + kI - 1) / kI);
     k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, part);
     const long long tot = (long long)d.S * nvv;
-    k_dots_fin<<<blocks_for(tot, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
+    k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
     g_msd_launches += 2;
 }
 
