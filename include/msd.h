@@ -137,6 +137,29 @@ msd_status msd_rhs_planewave(msd_problem* pb, int R, const double* betas_host, v
  * Asynchronous on the problem's stream. */
 msd_status msd_matvec(msd_problem* pb, int R, int precision, const void* x_dev, void* y_dev);
 
+/* The same product as msd_matvec, for callers that must not allocate device
+ * memory at the time of the call: a serving process that reserves its whole
+ * device-memory budget at start-up, or a latency-critical caller for which
+ * the implicit device-wide synchronisation of cudaMalloc/cudaFree is not
+ * acceptable.  The paper has no counterpart; it is a property of this
+ * library's memory management only.
+ *   pb         a problem whose generators of this precision already exist
+ *              (after one msd_matvec or msd_solve_planewaves call with that
+ *              precision; otherwise MSD_ERR_ARG)
+ *   x, y       device, [N_tot][R], as for msd_matvec
+ * The call allocates nothing: its work list, scaled input and per-split
+ * partial sums live in one 32 MiB device array that the library declares
+ * at file scope (every GPU that loads the library holds it until the
+ * process exits).  A problem whose 2 * N_tot * R values (complex128 or
+ * complex64) plus work list exceed 32 MiB is rejected with MSD_ERR_ARG.
+ * The first call on a device looks up the device address of that array
+ * (cudaGetSymbolAddress), so that first call should come before any stream
+ * capture.  Every call shares the array and overwrites what it reads before
+ * reading it; calls whose execution overlaps on the GPU (other streams,
+ * other problems) race on it and must be serialised by the caller.
+ * Asynchronous on the problem's stream. */
+msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, const void* x_dev, void* y_dev);
+
 /* Section 5 / section 6.2: solve A rho = -U for R plane waves per
  * configuration with left-preconditioned restarted GMRES on the device
  * (x0 = 0), FP64 throughout (MSD_FP64) or FP32 inner sweeps with FP64

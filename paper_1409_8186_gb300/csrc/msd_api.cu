@@ -857,3 +857,114 @@ msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T, const do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free product
+//
+// msd_matvec_noalloc: the block-Toeplitz product of msd_matvec for callers
+// that may not allocate device memory when they call it.  Its work list,
+// scaled-input buffer and per-split partial sums live in one file-scope
+// device array instead of library buffers obtained from cudaMalloc.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32ull << 20;  // 32 MiB held by every GPU that loads the library
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch, per device (host code may not take
+// the address of a __device__ variable directly).
+void* g_static_scratch_dev[kMaxDevices] = {};
+
+// Work list of the product (configuration-major, then target tile, then
+// source split), written on the device so that no host buffer is needed.
+__global__ void k_fill_static_work(const MsdConfig* __restrict__ cfg, int C, int ns, int nwork,
+                                   MatvecWork* __restrict__ out) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwork) return;
+    const int w0 = w;
+    for (int c = 0; c < C; ++c) {
+        const int cnt = (cfg[c].Mp / MSD_TILE_P) * ns;
+        if (w < cnt) {
+            const int tile = w / ns, split = w % ns, M = cfg[c].M;
+            MatvecWork x;
+            x.cfg = c;
+            x.p0 = tile * MSD_TILE_P;
+            x.q0 = (int)((long long)M * split / ns);
+            x.q1 = (int)((long long)M * (split + 1) / ns);
+            x.split = split;
+            x.pad = 0;
+            out[w0] = x;
+            return;
+        }
+        w -= cnt;
+    }
+}
+
+void* static_scratch_address() {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(MSD_ERR_ARG, "msd_matvec_noalloc: device index out of range");
+    if (!g_static_scratch_dev[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_scratch_dev[dev] = p;
+    }
+    return g_static_scratch_dev[dev];
+}
+
+}  // namespace
+
+extern "C" msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, const void* x_dev, void* y_dev) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || !x_dev || !y_dev) fail(MSD_ERR_ARG, "msd_matvec_noalloc: bad argument");
+        if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_matvec_noalloc: precision");
+        if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev))
+            fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must be device memory");
+        if (x_dev == y_dev) fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must not overlap");
+        const bool fp64 = precision == MSD_FP64;
+        if ((fp64 && !pb->d_G64) || (!fp64 && !pb->d_G32))
+            fail(MSD_ERR_ARG, "msd_matvec_noalloc: the generators of this precision are not built yet "
+                              "(call msd_matvec or msd_solve_planewaves once first)");
+        if (matvec_smem_bytes(R, pb->Nmax, fp64) > 227 * 1024)
+            fail(MSD_ERR_ARG, "msd_matvec_noalloc: truncation order too large for the shared-memory tile");
+        unsigned char* base = (unsigned char*)static_scratch_address();
+        // layout: [work list][xs][partials], each 256-byte aligned
+        const size_t elem = fp64 ? 16 : 8;
+        const size_t vec = (size_t)pb->Ntot * R * elem;
+        long long tiles = 0;
+        for (auto& c : pb->cfg) tiles += c.Mp / MSD_TILE_P;
+        auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        auto need = [&](int ns) { return up((size_t)tiles * ns * sizeof(MatvecWork)) + up(vec) + (size_t)ns * vec; };
+        if (need(1) > kStaticScratchBytes)
+            fail(MSD_ERR_ARG, "msd_matvec_noalloc: N_tot * R too large for the 32 MiB static work area");
+        // source splits: as many as fill one wave of resident CTAs and fit
+        int sms = 0, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long slots = (long long)sms * matvec_blocks_per_sm(R, pb->Nmax, fp64);
+        const long long units = tiles * (R / matvec_col_tile(R, pb->Nmax, fp64));
+        int ns = (int)std::max<long long>(1, std::min<long long>(slots / std::max<long long>(1, units),
+                                                                 std::max(1, pb->Mmax / 2)));
+        while (ns > 1 && need(ns) > kStaticScratchBytes) --ns;
+        const int nwork = (int)(tiles * ns);
+        MatvecWork* work = (MatvecWork*)base;
+        unsigned char* xs = base + up((size_t)nwork * sizeof(MatvecWork));
+        unsigned char* part = xs + up(vec);
+        k_fill_static_work<<<(nwork + 127) / 128, 128, 0, pb->stream>>>(pb->d_cfg, pb->C, ns, nwork, work);
+        g_msd_launches += 1;
+        CK_LAUNCH();
+        // every (split, row, column) of the partials and every element of xs
+        // is written by this call before it is read, so no clearing is needed
+        if (fp64)
+            launch_matvec_f64(pb->d_cfg, work, nwork, pb->Nmax, pb->d_G64, pb->d_rf64, pb->d_lf64, pb->Ntot, R,
+                              (const double2*)x_dev, (double2*)xs, (double2*)part, ns, (double2*)y_dev, pb->stream,
+                              nullptr, nullptr);
+        else
+            launch_matvec_f32(pb->d_cfg, work, nwork, pb->Nmax, pb->d_G32, pb->d_rf32, pb->d_lf32, pb->Ntot, R,
+                              (const float2*)x_dev, (float2*)xs, (float2*)part, ns, (float2*)y_dev, pb->stream,
+                              nullptr, nullptr);
+        CK_LAUNCH();
+        return MSD_OK;
+    });
+}

@@ -61,6 +61,7 @@ def _load():
         "msd_pair_generators": (I, [P, I, P]),
         "msd_rhs_planewave": (I, [P, I, P, P]),
         "msd_matvec": (I, [P, I, I, P, P]),
+        "msd_matvec_noalloc": (I, [P, I, I, P, P]),
         "msd_solve_planewaves": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P]),
         "msd_farfield": (I, [P, P, I, I, P, P]),
         "msd_update_geometry": (I, [P, P, P, P]),
@@ -79,7 +80,7 @@ _lib = _load()
 EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "msd_disk_diagonals",
             "msd_pair_generators", "msd_rhs_planewave", "msd_matvec", "msd_solve_planewaves",
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
-            "msd_last_error")
+            "msd_matvec_noalloc", "msd_last_error")
 
 
 def library_path() -> str:
@@ -152,6 +153,12 @@ def msd_rhs_planewave(h, R: int, betas, out) -> None:
 
 def msd_matvec(h, R: int, precision: int, x, y) -> None:
     _check(_lib.msd_matvec(h, R, precision, _ptr(x), _ptr(y)))
+
+
+def msd_matvec_noalloc(h, R: int, precision: int, x, y) -> None:
+    """msd_matvec without any device allocation in the call (work area in a
+    fixed 32 MiB device array; see include/msd.h)."""
+    _check(_lib.msd_matvec_noalloc(h, R, precision, _ptr(x), _ptr(y)))
 
 
 def msd_solve_planewaves(h, R: int, betas, opts: msd_opts | None, rho_out, stats_out=None) -> int:
