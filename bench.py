@@ -130,6 +130,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(local_ms: float, local_bytes: float, dist, device="cpu"):
+    """Whole-job throughput across ranks: the slowest rank's time and the
+    algorithmic bytes of every rank's block products (replicas: each rank
+    runs its own copy of the workload).  Returns (max_ms, GB/s)."""
+    import torch
+    t = torch.tensor([local_ms, local_bytes], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized():
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        max_ms, all_bytes = float(mx.item()), float(tot.item())
+    else:
+        max_ms, all_bytes = local_ms, local_bytes
+    return max_ms, all_bytes / (max_ms * 1e-3) / 1e9
+
+
+def profile_only(what: str):
+    """Minimal runs for ncu captures: 'matvec' = three FP64 then three FP32
+    products of the 400-disk operator; 'fp64' / 'mixed' = one solve."""
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cl = W.random_cluster_400()
+    pb = msd.Problem(cl)
+    if what == "matvec":
+        g = torch.Generator(device="cpu").manual_seed(0)
+        x64 = torch.randn(cl.ntot, 1, dtype=torch.complex128, generator=g).cuda()
+        x32 = x64.to(torch.complex64)
+        for x, p in ((x64, msd.MSD_FP64), (x32, msd.MSD_FP32)):
+            for _ in range(3):
+                pb.matvec(x, p)
+    else:
+        prec = msd.MSD_FP64 if what == "fp64" else msd.MSD_MIXED
+        res = pb.solve([cl.meta["beta"]], tol=1e-10, precision=prec)
+        print("status", res.status, "iters", int(res.iters[0]), "relres", float(res.relres[0]))
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -137,9 +175,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed"], default=None,
+                    help="run a minimal workload for a profiler capture and print no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_only:
+        return profile_only(args.profile_only)
 
     import numpy as np
     import torch
@@ -206,14 +248,7 @@ def main():
     r64 = timed(msd.MSD_FP64, args.steps, args.warmup)
     rmx = timed(msd.MSD_MIXED, args.steps, args.warmup)
 
-    total_ms = sum(r64["ms"])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    # whole-job throughput: algorithmic bytes of every block product in the
-    # timed steps (all ranks) over the slowest rank's time
-    value = r64["kernel_bytes"] * world / (total_ms * 1e-3) / 1e9
+    total_ms, value = aggregate(sum(r64["ms"]), r64["kernel_bytes"], dist, device="cuda")
 
     # end to end through the C ABI with host buffers (host->device inputs,
     # device->host densities and far field inside the timed region)

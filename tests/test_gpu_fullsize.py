@@ -1,0 +1,128 @@
+"""Parity at the workloads' full sizes, in the launch configurations the
+benchmark uses, on outputs the oracle can compute one block row at a time.
+
+* products: sampled target disks of P^-1 A x against the oracle's block rows
+  (FP64 1e-11, FP32 1e-5 relative to the sampled rows);
+* solves: the oracle's residual of the GPU densities on sampled rows -- any
+  subset of rows of r = P^-1(b - A rho) has norm <= ||r|| <= tol ||P^-1 b||,
+  so the sampled rows must satisfy that bound with the oracle's operator;
+* far field: the oracle's section 4.4 sum evaluated on the GPU densities.
+"""
+import numpy as np
+import pytest
+
+import oracle.msd_oracle as O_
+from paper_1409_8186_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def msd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_8186_gb300 import msd as m
+    return m
+
+
+def sample_targets(M, count, seed=0):
+    rng = np.random.default_rng(seed)
+    s = set([0, M - 1, M // 2]) | set(rng.choice(M, size=min(count, M), replace=False).tolist())
+    return sorted(s)[:count + 3]
+
+
+def oracle_rows(cl, x, targets):
+    return O_.preconditioned_rows(cl.centres, cl.radii, cl.bc, cl.k, cl.N, x, targets)
+
+
+def check_product(msd, pb, cl, R, targets, row0=0, seed=0):
+    n = cl.n
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    x64 = torch.randn(pb.ntot, R, dtype=torch.complex128, generator=g)
+    y64 = pb.matvec(x64.cuda(), msd.MSD_FP64).cpu().numpy()
+    x32 = x64.to(torch.complex64)
+    y32 = pb.matvec(x32.cuda(), msd.MSD_FP32).cpu().numpy()
+    xs = x64.numpy()[row0:row0 + cl.ntot]
+    ref = oracle_rows(cl, xs, targets)
+    ref32 = oracle_rows(cl, x32.numpy().astype(np.complex128)[row0:row0 + cl.ntot], targets)
+    for i, p in enumerate(targets):
+        rows = slice(row0 + p * n, row0 + (p + 1) * n)
+        e64 = np.abs(y64[rows] - ref[i]).max() / np.abs(ref[i]).max()
+        e32 = np.abs(y32[rows] - ref32[i]).max() / np.abs(ref32[i]).max()
+        assert e64 < 1e-11, (p, e64)
+        assert e32 < 1e-5, (p, e32)
+
+
+def check_residual(cl, rho, betas, targets, tol, row0=0):
+    n = cl.n
+    b = O_.preconditioned_rhs(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas)
+    bn = np.linalg.norm(b, axis=0)
+    r_rows = oracle_rows(cl, rho[row0:row0 + cl.ntot], targets)
+    for i, p in enumerate(targets):
+        res = r_rows[i] - b[p * n:(p + 1) * n]
+        worst = (np.linalg.norm(res, axis=0) / bn).max()
+        assert worst <= 1.05 * tol, (p, worst)
+
+
+def test_random400_product_solve_farfield(msd):
+    """M = 400, k = 2 pi, N = 20, one plane wave: the benchmark workload."""
+    cl = W.random_cluster_400()
+    pb = msd.Problem(cl)
+    targets = sample_targets(cl.M, 8)
+    check_product(msd, pb, cl, 1, targets)
+    beta = [cl.meta["beta"]]
+    for prec in (msd.MSD_FP64, msd.MSD_MIXED):
+        res = pb.solve(beta, tol=1e-10, precision=prec)
+        assert res.status == msd.MSD_OK, (prec, res.flags, res.relres)
+        rho = res.rho.cpu().numpy()
+        check_residual(cl, rho, beta, targets, 1e-10)
+    th = W.angles(360)
+    F = pb.farfield(res.rho, th).cpu().numpy()[0]
+    Fref = O_.farfield(cl.centres, cl.radii, cl.k, cl.N, rho, th)
+    assert np.abs(F - Fref).max() <= 1e-12 * np.abs(Fref).max()
+
+
+def test_cluster200_sixteen_incidences(msd):
+    """M = 200, k = 10, N = 22, 16 plane waves (mixed precision)."""
+    cl = W.cluster_200()
+    pb = msd.Problem(cl)
+    targets = sample_targets(cl.M, 6, seed=1)
+    check_product(msd, pb, cl, 16, targets, seed=1)
+    betas = W.angles(16)
+    res = pb.solve(betas, tol=1e-10, precision=msd.MSD_MIXED)
+    assert res.status == msd.MSD_OK, (res.flags, res.relres)
+    check_residual(cl, res.rho.cpu().numpy(), betas, targets, 1e-10)
+
+
+def test_lattice4000_products(msd):
+    """M = 4000 on a jittered lattice, k = 5, N = 15, 64 columns."""
+    cl = W.lattice_4000()
+    pb = msd.Problem(cl)
+    check_product(msd, pb, cl, 64, sample_targets(cl.M, 4, seed=2), seed=2)
+
+
+def test_batched_clusters_subset(msd):
+    """Six of the 256 batched clusters (M ~ U{50..800}, mixed Dirichlet /
+    Neumann, k ~ U[1, 8], N = ceil(k) + 8), 32 incidences each, one batch."""
+    cls = W.batched_clusters(count=6)
+    pb = msd.Problem(cls)
+    R = 32
+    betas = np.stack([W.angles(R)] * len(cls))
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = torch.randn(pb.ntot, R, dtype=torch.complex128, generator=g)
+    y64 = pb.matvec(x.cuda(), msd.MSD_FP64).cpu().numpy()
+    y32 = pb.matvec(x.to(torch.complex64).cuda(), msd.MSD_FP32).cpu().numpy()
+    res = pb.solve(betas, tol=1e-10, precision=msd.MSD_MIXED)
+    assert res.status == msd.MSD_OK, (res.flags, res.relres)
+    rho = res.rho.cpu().numpy()
+    for c, cl in enumerate(cls):
+        o0 = pb.row_offset(c)
+        targets = sample_targets(cl.M, 3, seed=c)
+        ref = oracle_rows(cl, x.numpy()[o0:o0 + cl.ntot], targets)
+        ref32 = oracle_rows(cl, x.to(torch.complex64).numpy().astype(np.complex128)[o0:o0 + cl.ntot], targets)
+        for i, p in enumerate(targets):
+            rows = slice(o0 + p * cl.n, o0 + (p + 1) * cl.n)
+            assert np.abs(y64[rows] - ref[i]).max() < 1e-11 * np.abs(ref[i]).max()
+            assert np.abs(y32[rows] - ref32[i]).max() < 1e-5 * np.abs(ref32[i]).max()
+        check_residual(cl, rho, betas[c], targets, 1e-10, row0=o0)
