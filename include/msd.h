@@ -182,6 +182,29 @@ msd_status msd_solve_planewaves(msd_problem* pb, int R, const double* betas_host
 msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T,
                         const double* thetas_host, void* F_out);
 
+/* Far-field misfit and its gradient (adjoint method).  The misfit is
+ *   J_c = sum_{t, r} |F_c(theta_t; beta_r) - Ftarget_c[t][r]|^2
+ * per configuration c, with F the far field a_L of section 4.4 for the plane
+ * waves of Prop. 4.1 (densities from the section 5 system).  The gradient is
+ * taken with respect to every disk centre, every radius and each k, through
+ * one forward solve, one adjoint solve with (P^-1 A)^H, the raw Toeplitz sums
+ * of both, a per-pair correlation contracted with the derivatives of the
+ * separation generators, and per-row terms (kernel K7).  The paper itself
+ * computes fields only; the misfit is this library's differentiation target.
+ *   betas_host   [C][R] incidence angles
+ *   thetas_host  [T] far-field sample angles
+ *   F_target     host or device, complex128 [C][T][R]
+ *   opts         solver options for both solves (default tol 1e-12; NULL ok)
+ *   J_out        host or device [C] (may be NULL)
+ *   dO           host or device [disk_off[C]][2] dJ/dO_p (may be NULL)
+ *   da           host or device [disk_off[C]] dJ/da_p (may be NULL)
+ *   dk           host or device [C] dJ/dk_c (may be NULL)
+ * Returns MSD_NOT_CONVERGED / MSD_STAGNATED (no gradient written) when a
+ * solve misses its tolerance.  Synchronises the stream. */
+msd_status msd_grad_farfield_misfit(msd_problem* pb, int R, const double* betas_host, int T,
+                                    const double* thetas_host, const void* F_target, const msd_opts* opts,
+                                    double* J_out, double* dO, double* da, double* dk);
+
 /* Replace the geometry of every configuration (same disk counts, N and
  * boundary flags) and recompute the Bessel diagonals (K1) and any stored
  * Toeplitz generators (K2).  Any argument may be NULL to keep it.

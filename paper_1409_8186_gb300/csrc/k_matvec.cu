@@ -429,3 +429,95 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
     k_finalize<float2><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;
 }
+
+// ---------------------------------------------------------------- general scalings
+// The same Toeplitz sums with other diagonal scalings, for the adjoint
+// operator (P^-1 A)^H z = z + r .* T^H (conj(l) .* z) and for the raw sums
+// the gradient needs.  Column scaling: real (r) or complex (conj l); row
+// scaling: none (raw sums), real or complex; optional + x.
+
+namespace {
+
+template <typename V>
+__global__ void k_scale_cols_c(long long Ntot, int R, const V* __restrict__ cf, const V* __restrict__ x,
+                               V* __restrict__ xs) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ntot * R) return;
+    const V f = cf[i / R];
+    const V v = x[i];
+    xs[i] = V{f.x * v.x - f.y * v.y, f.x * v.y + f.y * v.x};
+}
+
+// y = (add_x ? x : 0) + row .* sum_s part[s];  row: rr (real), rc (complex) or none
+template <typename V, typename S>
+__global__ void k_finalize_gen(long long Ntot, int R, int nsplit, const S* __restrict__ rr,
+                               const V* __restrict__ rc, int add_x, const V* __restrict__ x,
+                               const V* __restrict__ part, V* __restrict__ y) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = t / kFinLanes;
+    const int sub = (int)(t % kFinLanes);
+    const long long tot = Ntot * R;
+    V s = vzero<V>();
+    if (i < tot) {
+        for (int k = sub; k < nsplit; k += kFinLanes) {
+            const V v = part[(long long)k * tot + i];
+            s.x += v.x;
+            s.y += v.y;
+        }
+    }
+#pragma unroll
+    for (int off = kFinLanes / 2; off > 0; off >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+    }
+    if (i >= tot || sub != 0) return;
+    V o = s;
+    if (rr) {
+        const S f = rr[i / R];
+        o = V{f * s.x, f * s.y};
+    } else if (rc) {
+        const V l = rc[i / R];
+        o = V{l.x * s.x - l.y * s.y, l.x * s.y + l.y * s.x};
+    }
+    if (add_x) {
+        const V v = x[i];
+        o.x += v.x;
+        o.y += v.y;
+    }
+    y[i] = o;
+}
+
+template <typename V, typename S, typename D>
+void product_general(D&& dispatch_fn, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
+                     const V* G, const S* col_r, const V* col_c, const S* row_r, const V* row_c, int add_x,
+                     long long Ntot, int R, const V* x, V* xs, V* part, int nsplit, V* y, cudaStream_t s) {
+    const long long tot = Ntot * R;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((tot + th - 1) / th);
+    if (col_c) k_scale_cols_c<V><<<blocks, th, 0, s>>>(Ntot, R, col_c, x, xs);
+    else k_scale_cols<V, S><<<blocks, th, 0, s>>>(Ntot, R, col_r, x, xs);
+    dispatch_fn([&](auto k) { decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); });
+    k_finalize_gen<V, S><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, row_r, row_c,
+                                                                                   add_x, x, part, y);
+    g_msd_launches += 3;
+}
+
+}  // namespace
+
+void launch_product_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const double2* G,
+                        const double* col_r, const double2* col_c, const double* row_r, const double2* row_c,
+                        int add_x, long long Ntot, int R, const double2* x, double2* xs, double2* part, int nsplit,
+                        double2* y, cudaStream_t s) {
+    const Choice c = choose(R, Nmax, true);
+    product_general<double2, double>([&](auto f) { dispatch64(c, f); }, d_cfg, d_work, nwork, Nmax, G, col_r,
+                                     col_c, row_r, row_c, add_x, Ntot, R, x, xs, part, nsplit, y, s);
+}
+
+void launch_product_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float2* G,
+                        const float* col_r, const float2* col_c, const float* row_r, const float2* row_c,
+                        int add_x, long long Ntot, int R, const float2* x, float2* xs, float2* part, int nsplit,
+                        float2* y, cudaStream_t s) {
+    const Choice c = choose(R, Nmax, false);
+    product_general<float2, float>([&](auto f) { dispatch32(c, f); }, d_cfg, d_work, nwork, Nmax, G, col_r, col_c,
+                                   row_r, row_c, add_x, Ntot, R, x, xs, part, nsplit, y, s);
+}

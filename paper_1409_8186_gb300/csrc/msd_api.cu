@@ -139,6 +139,13 @@ struct msd_problem {
     long long gen_elems = 0;
     double2* d_G64 = nullptr;
     float2* d_G32 = nullptr;
+    // adjoint operator data: GA[p][q][l] = conj(g^pq_{-l}), conj(l); rebuilt
+    // when the geometry version moves on
+    double2* d_GA64 = nullptr;
+    float2* d_GA32 = nullptr;
+    double2* d_clf64 = nullptr;
+    float2* d_clf32 = nullptr;
+    long long geom_version = 0, adj64_version = -1, adj32_version = -1, adj_rows_version = -1;
     std::map<long long, MatvecPlan> plans;  // key: R*4 + precision
     std::vector<RowChunk> chunks;
     RowChunk* d_chunks = nullptr;
@@ -146,6 +153,7 @@ struct msd_problem {
     int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags
     cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf xs, part, sbuf[24];
+    DBuf gbuf[9];  // gradient work buffers
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
     double offdiag_L = 0, offdiag_n2 = 0;
@@ -278,6 +286,71 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
     CK_LAUNCH();
 }
 
+// Adjoint generators GA[p][q][l] = conj(g^pq_{-l}) and conj(l) of the current
+// geometry (rebuilt after msd_update_geometry).
+void ensure_adjoint(msd_problem* pb, bool fp64) {
+    ensure_generators(pb, fp64);
+    if (!pb->d_clf64 || pb->adj_rows_version != pb->geom_version) {
+        if (!pb->d_clf64) {
+            pb->d_clf64 = dalloc<double2>(pb->Ntot);
+            pb->d_clf32 = dalloc<float2>(pb->Ntot);
+        }
+        launch_conj_rows(pb->Ntot, pb->d_lf64, pb->d_clf64, pb->d_clf32, pb->stream);
+        CK_LAUNCH();
+        pb->adj_rows_version = pb->geom_version;
+    }
+    if (fp64) {
+        if (!pb->d_GA64 || pb->adj64_version != pb->geom_version) {
+            if (!pb->d_GA64) pb->d_GA64 = dalloc<double2>(pb->gen_elems);
+            launch_adjoint_generators_f64(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_G64, pb->d_GA64, pb->stream);
+            CK_LAUNCH();
+            pb->adj64_version = pb->geom_version;
+        }
+    } else {
+        if (!pb->d_GA32 || pb->adj32_version != pb->geom_version) {
+            if (!pb->d_GA32) pb->d_GA32 = dalloc<float2>(pb->gen_elems);
+            launch_adjoint_generators_f32(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_G32, pb->d_GA32, pb->stream);
+            CK_LAUNCH();
+            pb->adj32_version = pb->geom_version;
+        }
+    }
+}
+
+// Products with other scalings on the problem's stream (device pointers):
+//   adjoint: y = x + r .* T^H(conj(l) .* x)       ((P^-1 A)^H x)
+//   raw forward: y = T(r .* x)    raw adjoint: y = T^H(conj(l) .* x)
+void product_dev(msd_problem* pb, int R, bool fp64, bool adjoint, bool raw, const void* x, void* y) {
+    if (matvec_smem_bytes(R, pb->Nmax, fp64) > 227 * 1024)
+        fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
+    if (adjoint) ensure_adjoint(pb, fp64);
+    else ensure_generators(pb, fp64);
+    MatvecPlan& plan = get_plan(pb, R, fp64);
+    const size_t elem = fp64 ? 16 : 8;
+    void* xs = pb->xs.get((size_t)pb->Ntot * R * elem);
+    void* part = pb->part.get((size_t)plan.nsplit * pb->Ntot * R * elem);
+    const int nwork = (int)plan.work.size();
+    if (fp64) {
+        const double2* G = adjoint ? pb->d_GA64 : pb->d_G64;
+        launch_product_f64(pb->d_cfg, plan.d_work, nwork, pb->Nmax, G, adjoint ? nullptr : pb->d_rf64,
+                           adjoint ? pb->d_clf64 : nullptr, (adjoint && !raw) ? pb->d_rf64 : nullptr,
+                           (!adjoint && !raw) ? pb->d_lf64 : nullptr, raw ? 0 : 1, pb->Ntot, R,
+                           (const double2*)x, (double2*)xs, (double2*)part, plan.nsplit, (double2*)y, pb->stream);
+    } else {
+        const float2* G = adjoint ? pb->d_GA32 : pb->d_G32;
+        launch_product_f32(pb->d_cfg, plan.d_work, nwork, pb->Nmax, G, adjoint ? nullptr : pb->d_rf32,
+                           adjoint ? pb->d_clf32 : nullptr, (adjoint && !raw) ? pb->d_rf32 : nullptr,
+                           (!adjoint && !raw) ? pb->d_lf32 : nullptr, raw ? 0 : 1, pb->Ntot, R,
+                           (const float2*)x, (float2*)xs, (float2*)part, plan.nsplit, (float2*)y, pb->stream);
+    }
+    CK_LAUNCH();
+}
+
+// The operator of a solve: P^-1 A, or its adjoint.
+void operator_dev(msd_problem* pb, int R, bool fp64, bool adjoint, const void* x, void* y) {
+    if (adjoint) product_dev(pb, R, fp64, true, false, x, y);
+    else matvec_dev(pb, R, fp64, x, y);
+}
+
 // Stage a caller buffer that may live on the host: returns a device pointer
 // (the caller's if it is device memory, else a library buffer filled from it).
 const void* stage_in(msd_problem* pb, DBuf& buf, const void* p, size_t bytes) {
@@ -323,6 +396,7 @@ struct SolveCtx {
     int *active, *kconv, *iters, *skip2, *flags;  // flags[0] any_active, flags[1] nonfinite
     int hstride;
     double2* part;  // [nchunk][m + 2][R] reduction partials
+    bool adjoint = false;  // solve with (P^-1 A)^H
 };
 
 // ||u||^2 per system into out[s * hstride] (FP64 vectors)
@@ -362,7 +436,7 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
             if (!pb->h_pinned[2 + 2 * slot]) break;
         }
         V* vj = Vb + (long long)j * vstride;
-        matvec_dev(pb, d.R, fp64, vj, w);
+        operator_dev(pb, d.R, fp64, cx.adjoint, vj, w);
         // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1
         gm_dots<V>(d, ch, co, Vb, vstride, j + 1, 1, w, nullptr, cx.part, cx.h1, cx.hstride, s);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, nullptr, -1.0, w, s);
@@ -406,9 +480,12 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
     CK_LAUNCH();
 }
 
+// Solve (P^-1 A) x = b, or its adjoint, for R columns per configuration.
+// The right-hand side is the plane-wave one of betas_host, or b_dev (FP64,
+// preconditioned, device) when given.
 msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts_in,
-                      void* rho_out, msd_stats* stats_host) {
-    if (!pb || R <= 0 || !betas_host || !rho_out) fail(MSD_ERR_ARG, "msd_solve_planewaves: bad argument");
+                      void* rho_out, msd_stats* stats_host, const double2* b_dev = nullptr, bool adjoint = false) {
+    if (!pb || R <= 0 || (!betas_host && !b_dev) || !rho_out) fail(MSD_ERR_ARG, "msd_solve_planewaves: bad argument");
     msd_opts o;
     memset(&o, 0, sizeof(o));
     if (opts_in) o = *opts_in;
@@ -480,12 +557,22 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     double* d_betas = (double*)sb((size_t)pb->C * R * 8);
     cx.part = (double2*)pb->sbuf[0].get((size_t)cx.d.nchunk * (m + 2) * R * sizeof(double2));
 
-    CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
-    launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
-                         pb->Nmax, R, d_betas, cx.b, s);
-    CK_LAUNCH();
-    ensure_generators(pb, true);
-    if (mixed) ensure_generators(pb, false);
+    cx.adjoint = adjoint;
+    if (b_dev) {
+        CK(cudaMemcpyAsync(cx.b, b_dev, nv * 16, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
+                             pb->Nmax, R, d_betas, cx.b, s);
+        CK_LAUNCH();
+    }
+    if (adjoint) {
+        ensure_adjoint(pb, true);
+        if (mixed) ensure_adjoint(pb, false);
+    } else {
+        ensure_generators(pb, true);
+        if (mixed) ensure_generators(pb, false);
+    }
     gm_zero(nv, cx.x, s);
     CK(cudaMemsetAsync(cx.iters, 0, S * sizeof(int), s));
     // ||b|| per system
@@ -509,7 +596,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
         if (sweeps == 0) {
             CK(cudaMemcpyAsync(cx.r, cx.b, nv * 16, cudaMemcpyDeviceToDevice, s));
         } else {
-            matvec_dev(pb, R, true, cx.x, cx.Ax);
+            operator_dev(pb, R, true, cx.adjoint, cx.x, cx.Ax);
             gm_residual(nv, cx.b, cx.Ax, cx.r, s);
         }
         norm2_f64(cx, cx.r, cx.wn2);
@@ -712,7 +799,8 @@ void msd_destroy(msd_problem* pb) {
     if (pb->stream) cudaStreamSynchronize(pb->stream);
     void* ptrs[] = {pb->d_cfg, pb->d_centre, pb->d_radius, pb->d_bc, pb->d_disk_cfg, pb->d_J, pb->d_dJ,
                     pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rhs_scale, pb->d_rf64, pb->d_lf32, pb->d_rf32,
-                    pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off};
+                    pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off,
+                    pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : pb->plans)
@@ -724,6 +812,7 @@ void msd_destroy(msd_problem* pb) {
     pb->xs.release();
     pb->part.release();
     for (auto& b : pb->sbuf) b.release();
+    for (auto& b : pb->gbuf) b.release();
     delete pb;
 }
 
@@ -817,6 +906,7 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
                                    pb->d_flags, pb->stream);
         CK_LAUNCH();
         check_flags(pb, "msd_update_geometry");
+        pb->geom_version += 1;  // adjoint operator data is rebuilt on next use
         return MSD_OK;
     });
 }
@@ -840,6 +930,85 @@ msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int
 }
 
 int64_t msd_kernel_launches(void) { return g_msd_launches.load(); }
+
+msd_status msd_grad_farfield_misfit(msd_problem* pb, int R, const double* betas_host, int T,
+                                    const double* thetas_host, const void* F_target, const msd_opts* opts,
+                                    double* J_out, double* dO, double* da, double* dk) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || T <= 0 || !betas_host || !thetas_host || !F_target)
+            fail(MSD_ERR_ARG, "msd_grad_farfield_misfit: bad argument");
+        cudaStream_t s = pb->stream;
+        const long long nv = pb->Ntot * R;
+        const size_t nF = (size_t)pb->C * T * R;
+        msd_opts o;
+        memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        if (o.tol <= 0) o.tol = 1e-12;
+        // work buffers (library-owned, separate from the solver's)
+        double2* rho = (double2*)pb->gbuf[0].get(nv * 16);
+        double2* mu = (double2*)pb->gbuf[1].get(nv * 16);
+        double2* F = (double2*)pb->gbuf[2].get(nF * 16 * 3);
+        double2* w = F + nF;
+        double2* Ft = w + nF;
+        double2* u = (double2*)pb->gbuf[3].get(nv * 16);
+        double2* sv = (double2*)pb->gbuf[4].get(nv * 16);
+        double2* tv = (double2*)pb->gbuf[5].get(nv * 16);
+        const int nmax = 2 * pb->Nmax + 1;
+        double2* E = (double2*)pb->gbuf[6].get((size_t)pb->C * nmax * T * 16);
+        // thetas, betas, J, gO, ga, gk
+        double* d_par = (double*)pb->gbuf[7].get((size_t)(T + pb->C * R + pb->C + 3 * pb->Mtot + pb->C) * 8);
+        double* d_th = d_par;
+        double* d_beta = d_th + T;
+        double* d_J = d_beta + (size_t)pb->C * R;
+        double* d_gO = d_J + pb->C;
+        double* d_ga = d_gO + 2 * pb->Mtot;
+        double* d_gk = d_ga + pb->Mtot;
+        CK(cudaMemcpyAsync(d_th, thetas_host, (size_t)T * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_beta, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(d_J, 0, (size_t)(pb->C + 3 * pb->Mtot + pb->C) * 8, s));
+        CK(cudaMemcpyAsync(Ft, F_target, nF * 16, is_device_ptr(F_target) ? cudaMemcpyDeviceToDevice
+                                                                            : cudaMemcpyHostToDevice, s));
+        // 1. forward solve and far field (Prop. 4.1, section 5, section 4.4)
+        msd_stats* st_fwd = nullptr;
+        msd_status st = solve_impl(pb, R, betas_host, &o, rho, st_fwd);
+        if (st != MSD_OK) fail(st, "msd_grad_farfield_misfit: forward solve did not converge");
+        launch_farfield(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_radius, pb->d_J, R, T, d_th, rho,
+                        nullptr, F, s);
+        launch_misfit(pb->C, T, R, F, Ft, w, d_J, s);
+        // 2. adjoint right-hand side C^H w and adjoint solve (P^-1 A)^H mu = C^H w
+        launch_ff_table(pb->d_cfg, pb->C, nmax, T, d_th, E, s);
+        launch_farfield_adj(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_J, nmax, T, R,
+                            d_th, E, w, u, s);
+        CK_LAUNCH();
+        st = solve_impl(pb, R, nullptr, &o, mu, nullptr, u, true);
+        if (st != MSD_OK) fail(st, "msd_grad_farfield_misfit: adjoint solve did not converge");
+        // 3. raw Toeplitz sums s = T(r .* rho), t = T^H(conj(l) .* mu)
+        product_dev(pb, R, true, false, true, rho, sv);
+        product_dev(pb, R, true, true, true, mu, tv);
+        // 4. pair correlations, far-field term, per-row terms
+        double2* muh = u;  // u is no longer needed
+        double2* rhoh = (double2*)pb->gbuf[8].get(nv * 16);
+        launch_scale_pair_inputs(pb->Ntot, R, pb->d_lf64, pb->d_rf64, mu, rho, muh, rhoh, s);
+        launch_pair_grad(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_G64, R, muh, rhoh, d_gO, d_gk, s);
+        launch_farfield_grad(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_J, pb->d_dJ, nmax,
+                             T, R, d_th, E, w, rho, d_gO, d_ga, d_gk, s);
+        launch_grad_rows(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_bc, pb->d_J,
+                         pb->d_dJ, pb->d_H, pb->d_dH, R, d_beta, mu, rho, sv, tv, d_gO, d_ga, d_gk, s);
+        CK_LAUNCH();
+        // 5. results
+        auto out = [&](void* dst, const double* src, size_t n) {
+            if (!dst) return;
+            CK(cudaMemcpyAsync(dst, src, n * 8, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               s));
+        };
+        out(J_out, d_J, pb->C);
+        out(dO, d_gO, 2 * (size_t)pb->Mtot);
+        out(da, d_ga, pb->Mtot);
+        out(dk, d_gk, pb->C);
+        CK(cudaStreamSynchronize(s));
+        return MSD_OK;
+    });
+}
 
 msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T, const double* thetas_host, void* F_out) {
     return guarded([&]() -> msd_status {

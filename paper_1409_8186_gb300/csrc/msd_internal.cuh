@@ -161,3 +161,35 @@ void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* k
             cudaStream_t s);
 void gm_residual(long long n, const double2* b, const double2* Ax, double2* r, cudaStream_t s);
 void gm_zero(long long n, double2* x, cudaStream_t s);
+
+// ---------------------------------------------------------------- K3 with other scalings, K7
+void launch_product_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const double2* G,
+                        const double* col_r, const double2* col_c, const double* row_r, const double2* row_c,
+                        int add_x, long long Ntot, int R, const double2* x, double2* xs, double2* part, int nsplit,
+                        double2* y, cudaStream_t s);
+void launch_product_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float2* G,
+                        const float* col_r, const float2* col_c, const float* row_r, const float2* row_c,
+                        int add_x, long long Ntot, int R, const float2* x, float2* xs, float2* part, int nsplit,
+                        float2* y, cudaStream_t s);
+void launch_adjoint_generators_f64(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg, const double2* G,
+                                   double2* GA, cudaStream_t s);
+void launch_adjoint_generators_f32(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg, const float2* G,
+                                   float2* GA, cudaStream_t s);
+void launch_conj_rows(long long n, const double2* a, double2* ca, float2* ca32, cudaStream_t s);
+void launch_ff_table(const MsdConfig* d_cfg, int C, int nmax, int T, const double* th, double2* E, cudaStream_t s);
+void launch_misfit(int C, int T, int R, const double2* F, const double2* Ft, double2* w, double* J, cudaStream_t s);
+void launch_farfield_adj(const MsdConfig* d_cfg, int Mtot, const int* disk_cfg, const double2* centre,
+                         const double* radius, const double2* J, int nmax, int T, int R, const double* th,
+                         const double2* E, const double2* w, double2* u, cudaStream_t s);
+void launch_farfield_grad(const MsdConfig* d_cfg, int Mtot, const int* disk_cfg, const double2* centre,
+                          const double* radius, const double2* J, const double2* dJ, int nmax, int T, int R,
+                          const double* th, const double2* E, const double2* w, const double2* rho, double* gO,
+                          double* ga, double* gk, cudaStream_t s);
+void launch_pair_grad(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg, const double2* centre, const double2* G,
+                      int R, const double2* muh, const double2* rhoh, double* gO, double* gk, cudaStream_t s);
+void launch_grad_rows(const MsdConfig* d_cfg, int Mtot, const int* disk_cfg, const double2* centre,
+                      const double* radius, const int8_t* bc, const double2* J, const double2* dJ, const double2* H,
+                      const double2* dH, int R, const double* betas, const double2* mu, const double2* rho,
+                      const double2* sv, const double2* tv, double* gO, double* ga, double* gk, cudaStream_t s);
+void launch_scale_pair_inputs(long long Ntot, int R, const double2* lf, const double* rf, const double2* mu,
+                              const double2* rho, double2* muh, double2* rhoh, cudaStream_t s);

@@ -65,6 +65,7 @@ def _load():
         "msd_solve_planewaves": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P]),
         "msd_farfield": (I, [P, P, I, I, P, P]),
         "msd_update_geometry": (I, [P, P, P, P]),
+        "msd_grad_farfield_misfit": (I, [P, I, P, I, P, P, ctypes.POINTER(msd_opts), P, P, P, P]),
         "msd_matvec_timing": (I, [P, I, P, P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
@@ -80,7 +81,7 @@ _lib = _load()
 EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "msd_disk_diagonals",
             "msd_pair_generators", "msd_rhs_planewave", "msd_matvec", "msd_solve_planewaves",
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
-            "msd_matvec_noalloc", "msd_last_error")
+            "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_last_error")
 
 
 def library_path() -> str:
@@ -182,6 +183,18 @@ def msd_update_geometry(h, centres=None, radii=None, k=None) -> None:
     _check(_lib.msd_update_geometry(h, _ptr(c) if c is not None else None,
                                     _ptr(r) if r is not None else None,
                                     _ptr(kk) if kk is not None else None))
+
+
+def msd_grad_farfield_misfit(h, R: int, betas, thetas, F_target, opts: msd_opts | None, J_out=None, dO=None,
+                             da=None, dk=None) -> int:
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    thetas = np.ascontiguousarray(thetas, dtype=np.float64)
+    if not hasattr(F_target, "data_ptr"):
+        F_target = np.ascontiguousarray(F_target, dtype=np.complex128)
+    p = lambda a: _ptr(a) if a is not None else None  # noqa: E731
+    return _check(_lib.msd_grad_farfield_misfit(h, R, _ptr(betas), len(thetas), _ptr(thetas), _ptr(F_target),
+                                                ctypes.byref(opts) if opts else None, p(J_out), p(dO), p(da),
+                                                p(dk)), allow_positive=True)
 
 
 def msd_matvec_timing(h, enable: int):
@@ -297,3 +310,56 @@ class Problem:
         F = torch.empty((self.C, len(th), R), dtype=torch.complex128, device="cuda") if out is None else out
         msd_farfield(self.handle, rho, R, th, F)
         return F
+
+    def update_geometry(self, centres=None, radii=None, k=None):
+        msd_update_geometry(self.handle, centres, radii, k)
+
+    def grad_farfield_misfit(self, betas, thetas, F_target, tol=1e-12, precision=MSD_FP64, restart=0,
+                             maxit=3000):
+        """J [C], dJ/dO [sum M, 2], dJ/da [sum M], dJ/dk [C] (NumPy arrays)."""
+        b = self._betas(betas)
+        Mtot = int(self.disk_off[-1])
+        J = np.zeros(self.C)
+        dO = np.zeros((Mtot, 2))
+        da = np.zeros(Mtot)
+        dk = np.zeros(self.C)
+        o = msd_opts(tol, restart, maxit, 0, 0.0, precision, MSD_GEN_AUTO)
+        st = msd_grad_farfield_misfit(self.handle, b.shape[1], b, np.asarray(thetas, np.float64), F_target, o, J,
+                                      dO, da, dk)
+        if st != MSD_OK:
+            raise MsdError(st, "a solve of the gradient did not converge")
+        return J, dO, da, dk
+
+
+def _autograd_function():
+    import torch
+
+    class FarFieldMisfit(torch.autograd.Function):
+        """J = sum_c sum_{t,r} |F - F*|^2 as a differentiable function of the
+        centres [sum M, 2], radii [sum M] and wavenumbers [C] (float64
+        tensors), evaluated by the CUDA library: the forward pass runs the
+        solve and the adjoint solve, the backward pass scales the stored
+        gradients."""
+
+        @staticmethod
+        def forward(ctx, centres, radii, k, problem, betas, thetas, F_target, tol, precision):
+            problem.update_geometry(centres.detach().contiguous().cpu().numpy(),
+                                    radii.detach().contiguous().cpu().numpy(),
+                                    k.detach().contiguous().cpu().numpy())
+            J, dO, da, dk = problem.grad_farfield_misfit(betas, thetas, F_target, tol=tol, precision=precision)
+            dev = centres.device
+            ctx.save_for_backward(torch.from_numpy(dO).to(dev), torch.from_numpy(da).to(dev),
+                                  torch.from_numpy(dk).to(dev))
+            return torch.tensor(float(J.sum()), dtype=torch.float64, device=dev)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dO, da, dk = ctx.saved_tensors
+            return gJ * dO, gJ * da, gJ * dk, None, None, None, None, None, None
+
+    return FarFieldMisfit
+
+
+def farfield_misfit(problem, centres, radii, k, betas, thetas, F_target, tol=1e-12, precision=MSD_FP64):
+    """Differentiable far-field misfit (torch.autograd), see FarFieldMisfit."""
+    return _autograd_function().apply(centres, radii, k, problem, betas, thetas, F_target, tol, precision)
