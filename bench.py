@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "block-matvec GB/s (% HBM peak) & solve time at relres 1e-10, FP64 vs mixed"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
+# product kernel (window length 7) on this workload, from an ncu capture
+# (216.42 MB read + 5.75 MB written); the algorithmic stream is 207.7 MB
+K3_FP64_DRAM_BYTES_PER_LAUNCH = 222170624
 WORKLOAD = ("random400_k2pi: M=400 sound-soft disks, a~U[0.5,1.5], centres U[-50,50]^2 gap 0.2, "
             "k=2pi, N=20 (16400 unknowns), 1 plane wave, GMRES (restart length sized to HBM) to relres 1e-10, "
             "far field T=360")
@@ -317,7 +321,7 @@ def main():
                         "GB_s": rmx["kernel_bytes"] / 2 / mix_kern_s / 1e9 if mix_kern_s > 0 else None,
                         "TFLOP_s": rmx["kernel_flops"] / mix_kern_s / 1e12 if mix_kern_s > 0 else None},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": K3_FP64_DRAM_BYTES_PER_LAUNCH,
                      "kernel": "k_bt_matvec<double2,1,1> (FP64 block-Toeplitz product)",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
         "cpu_baseline": cpu,
