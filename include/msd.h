@@ -227,6 +227,45 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
 msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int64_t* launches,
                              double* flops, double* bytes);
 
+/* Generators of the forward products (the Toeplitz storage of section 5).
+ *   MSD_GEN_STREAMED (default): the 4N+1 values of every ordered pair are
+ *     stored in HBM (complex128, plus complex64 for FP32 products) and read
+ *     by every product.
+ *   MSD_GEN_RECOMPUTE: no stored array; every product evaluates the
+ *     generators again (kernel K2), chunk by chunk, into a work buffer of
+ *     about chunk_bytes (0: 64 MiB, sized to stay in L2) that the product
+ *     kernel reads at once.  The stored arrays are freed.
+ *   MSD_GEN_AUTO: streamed if both stored copies fit in half the free
+ *     device memory, else recompute (decided now).
+ * Applies to msd_matvec and to msd_solve_planewaves (whose opts.gen_mode,
+ * when not MSD_GEN_AUTO, overrides it for that solve).  The gradient and
+ * msd_pair_generators always use (and build) the stored arrays.  A complex64
+ * range overflow of a generator (MSD_ERR_RANGE) is checked once per
+ * geometry on the first recomputed FP32 product.  Synchronises the stream. */
+msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes);
+
+/* Tile shape of the block-Toeplitz product kernel (an implementation
+ * choice; the paper fixes none).  The kernel gives each thread a register
+ * window of KB consecutive modes and each CTA a tile of 32 target disks by
+ * RT columns; the sources of a tile are split into nsplit ranges.  On the
+ * first product of a given (R, precision) the library times every shape
+ * that fits (autotuner; the first product therefore synchronises the
+ * stream, so make it before any stream capture) unless the environment sets
+ * MSD_AUTOTUNE=0 (cost-model choice) or msd_set_tile fixed one.
+ *
+ * msd_plan_info: the shape used for (R, precision), precision MSD_FP64 or
+ *   MSD_FP32, creating the plan (and tuning) if needed.  out[4] receives
+ *   {KB, RT, nsplit, number of shapes timed (0: not tuned)}; tuned_ms (may
+ *   be NULL) the kernel time of the chosen shape in the tuning run (0 if
+ *   not tuned).  Needs the generators of that precision (builds them).
+ * msd_set_tile: fix the shape (KB, RT) for later products of (R, precision)
+ *   of this problem, replacing any plan made before.  MSD_ERR_ARG if
+ *   (KB, RT) is not one of the instantiated shapes that fit (FP64: KB 4..7,
+ *   RT 1; FP32: KB 4..9, RT in {1,2,4,8,16} dividing R, at most 16 warps
+ *   per CTA, shared memory <= 227 KB). */
+msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double* tuned_ms);
+msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT);
+
 /* Total number of CUDA kernels launched by this library in this process. */
 int64_t msd_kernel_launches(void);
 

@@ -212,7 +212,16 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
             if (mi < n) {
                 const long long row = c.row_off + (long long)p * n + mi;
 #pragma unroll
-                for (int r = 0; r < RB; ++r) out[row * R + col0 + c0 + r] = acc.result(b, r);
+                for (int r = 0; r < RB; ++r) {
+                    const long long o = row * R + col0 + c0 + r;
+                    const V v = acc.result(b, r);
+                    if (w.pad) {  // a later source block of a recomputed product: accumulate
+                        const V u = out[o];
+                        out[o] = V{u.x + v.x, u.y + v.y};
+                    } else {
+                        out[o] = v;
+                    }
+                }
             }
         }
     }
@@ -266,9 +275,7 @@ constexpr int kKbMin = 4;
 constexpr int kKbMax64 = 7;
 constexpr int kKbMax32 = 9;
 
-struct Choice {
-    int KB, RT, RB, I;
-};
+using Choice = MatvecChoice;
 
 Choice choose(int R, int Nmax, bool fp64) {
     const int n = 2 * Nmax + 1;
@@ -381,31 +388,92 @@ void dispatch(const Choice& c, bool fp64, F&& f) {
 
 }  // namespace
 
-int matvec_col_tile(int R, int Nmax, bool fp64) { return choose(R, Nmax, fp64).RT; }
+MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64) { return choose(R, Nmax, fp64); }
 
-size_t matvec_smem_bytes(int R, int Nmax, bool fp64) {
+// Every instantiated tile shape that fits this (R, N): FP64 KB = 4..7 with
+// RT = 1; FP32 KB = 4..9 with each column tile RT in {1, 2, 4, 8, 16} that
+// divides R and keeps I * RT / RB <= 16 warps per CTA.
+int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap) {
+    const int n = 2 * Nmax + 1;
+    int cnt = 0;
+    for (int KB = kKbMin; KB <= (fp64 ? kKbMax64 : kKbMax32); ++KB) {
+        const int I = (n + KB - 1) / KB;
+        if (I > 16) continue;
+        for (int rt = 1; rt <= (fp64 ? 1 : 16); rt *= 2) {
+            if (R % rt) break;
+            const int rb = rt < 4 ? rt : 4;
+            if (I * (rt / rb) > 16) continue;
+            Choice c{KB, rt, rb, I};
+            size_t b = 0;
+            dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
+            if (b > 227 * 1024) continue;
+            if (cnt < cap) out[cnt] = c;
+            ++cnt;
+        }
+    }
+    return cnt < cap ? cnt : cap;
+}
+
+size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64) {
     size_t b = 0;
-    dispatch(choose(R, Nmax, fp64), fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
+    dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
     return b;
 }
 
-// Resident CTAs per SM of the product kernel chosen for (R, Nmax, precision).
-int matvec_blocks_per_sm(int R, int Nmax, bool fp64) {
+// Resident CTAs per SM of one product kernel instance.
+int matvec_blocks_per_sm(const MatvecChoice& c, int Nmax, bool fp64) {
     int nb = 1;
-    dispatch(choose(R, Nmax, fp64), fp64, [&](auto k) { nb = decltype(k)::occupancy(Nmax); });
+    dispatch(c, fp64, [&](auto k) { nb = decltype(k)::occupancy(Nmax); });
     return nb;
+}
+
+void launch_scale_cols(bool fp64, long long Ntot, int R, const void* rf, const void* x, void* xs, cudaStream_t s) {
+    const long long tot = Ntot * R;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((tot + th - 1) / th);
+    if (fp64) k_scale_cols<double2, double><<<blocks, th, 0, s>>>(Ntot, R, (const double*)rf, (const double2*)x,
+                                                                   (double2*)xs);
+    else k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, (const float*)rf, (const float2*)x, (float2*)xs);
+    g_msd_launches += 1;
+}
+
+void launch_finalize(bool fp64, long long Ntot, int R, int nsplit, const void* lf, const void* x, const void* part,
+                     void* y, cudaStream_t s) {
+    const long long tot = Ntot * R;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((tot * kFinLanes + th - 1) / th);
+    if (fp64) k_finalize<double2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, (const double2*)lf, (const double2*)x,
+                                                         (const double2*)part, (double2*)y);
+    else k_finalize<float2><<<blocks, th, 0, s>>>(Ntot, R, nsplit, (const float2*)lf, (const float2*)x,
+                                                  (const float2*)part, (float2*)y);
+    g_msd_launches += 1;
+}
+
+void launch_bt_only(const MatvecChoice& c, bool fp64, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork,
+                    int Nmax, const void* G, const void* xs, void* part, long long Ntot, int R, cudaStream_t s) {
+    if (fp64)
+        dispatch64(c, [&](auto k) {
+            decltype(k)::launch(d_cfg, d_work, nwork, Nmax, (const double2*)G, (const double2*)xs, (double2*)part,
+                                Ntot, R, s);
+        });
+    else
+        dispatch32(c, [&](auto k) {
+            decltype(k)::launch(d_cfg, d_work, nwork, Nmax, (const float2*)G, (const float2*)xs, (float2*)part,
+                                Ntot, R, s);
+        });
+    g_msd_launches += 1;
 }
 
 void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const double2* G, const double* rf, const double2* lf, long long Ntot, int R,
                        const double2* x, double2* xs, double2* part, int nsplit, double2* y, cudaStream_t s,
-                       cudaEvent_t ev0, cudaEvent_t ev1) {
+                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch) {
     const long long tot = Ntot * R;
     const int th = 256;
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<double2, double><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
-    dispatch64(choose(R, Nmax, true), [&](auto k) {
+    dispatch64(ch ? *ch : choose(R, Nmax, true), [&](auto k) {
         decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
     });
     if (ev1) cudaEventRecord(ev1, s);
@@ -416,13 +484,13 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
 void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const float2* G, const float* rf, const float2* lf, long long Ntot, int R,
                        const float2* x, float2* xs, float2* part, int nsplit, float2* y, cudaStream_t s,
-                       cudaEvent_t ev0, cudaEvent_t ev1) {
+                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch) {
     const long long tot = Ntot * R;
     const int th = 256;
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
-    dispatch32(choose(R, Nmax, false), [&](auto k) {
+    dispatch32(ch ? *ch : choose(R, Nmax, false), [&](auto k) {
         decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
     });
     if (ev1) cudaEventRecord(ev1, s);
@@ -507,8 +575,8 @@ void product_general(D&& dispatch_fn, const MsdConfig* d_cfg, const MatvecWork* 
 void launch_product_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const double2* G,
                         const double* col_r, const double2* col_c, const double* row_r, const double2* row_c,
                         int add_x, long long Ntot, int R, const double2* x, double2* xs, double2* part, int nsplit,
-                        double2* y, cudaStream_t s) {
-    const Choice c = choose(R, Nmax, true);
+                        double2* y, cudaStream_t s, const MatvecChoice* ch) {
+    const Choice c = ch ? *ch : choose(R, Nmax, true);
     product_general<double2, double>([&](auto f) { dispatch64(c, f); }, d_cfg, d_work, nwork, Nmax, G, col_r,
                                      col_c, row_r, row_c, add_x, Ntot, R, x, xs, part, nsplit, y, s);
 }
@@ -516,8 +584,8 @@ void launch_product_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nw
 void launch_product_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float2* G,
                         const float* col_r, const float2* col_c, const float* row_r, const float2* row_c,
                         int add_x, long long Ntot, int R, const float2* x, float2* xs, float2* part, int nsplit,
-                        float2* y, cudaStream_t s) {
-    const Choice c = choose(R, Nmax, false);
+                        float2* y, cudaStream_t s, const MatvecChoice* ch) {
+    const Choice c = ch ? *ch : choose(R, Nmax, false);
     product_general<float2, float>([&](auto f) { dispatch32(c, f); }, d_cfg, d_work, nwork, Nmax, G, col_r, col_c,
                                    row_r, row_c, add_x, Ntot, R, x, xs, part, nsplit, y, s);
 }

@@ -98,20 +98,33 @@ void launch_disk_diagonals(const MsdConfig* d_cfg, int Mtot, const int* d_disk_c
 
 // ---------------------------------------------------------------- K2
 
-// One thread per ordered pair (q, p) of configuration `ci`, p in [0, Mp).
+// One thread per ordered pair (q, p) of a generator block: configuration
+// g.cfg, sources q in [Q0, Q0+Qb), targets p in [P0, P0+Pc) (P0, Pc
+// multiples of 32, p may reach into the padding p >= M).  Output
+// out[g.out_off + ((q-Q0) Pc + (p-P0)) L + l + 2N].  The whole-problem
+// array is one block per configuration (P0 = Q0 = 0, Pc = Mp, Qb = M,
+// out_off = gen_off); recomputed products use blocks of a chunk.
 // b_pq = O_p - O_q, e^{i alpha_pq} = b_pq/|b_pq|; for l >= 0:
 // g_l = H_l(k b) e^{i l alpha}, g_{-l} = (-1)^l H_l(k b) e^{-i l alpha}.
 // Padded targets (p >= M) and the diagonal p == q get zeros.
-__global__ void k_pair_generators(const MsdConfig* __restrict__ cfg, int ci,
-                                  const double2* __restrict__ centre, double2* G64, float2* G32,
-                                  int* flags) {
-    const MsdConfig c = cfg[ci];
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)c.M * c.Mp) return;
-    const int q = (int)(idx / c.Mp);
-    const int p = (int)(idx % c.Mp);
+__global__ void k_pair_generators(const MsdConfig* __restrict__ cfg, const GenBlock* __restrict__ blocks,
+                                  int nblocks, long long nitems, const double2* __restrict__ centre,
+                                  double2* G64, float2* G32, int* flags) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nitems) return;
+    int lo = 0, hi = nblocks - 1;  // last block with item_off <= idx
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blocks[mid].item_off <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    const GenBlock g = blocks[lo];
+    const MsdConfig c = cfg[g.cfg];
+    const long long li = idx - g.item_off;
+    const int q = g.Q0 + (int)(li / g.Pc);
+    const int p = g.P0 + (int)(li % g.Pc);
     const int N = c.N, L = c.L, lmax = 2 * N;
-    const long long base = c.gen_off + ((long long)q * c.Mp + p) * L;
+    const long long base = g.out_off + li * L;
     if (p >= c.M || p == q) {
         for (int l = 0; l < L; ++l) {
             if (G64) G64[base + l] = make_double2(0.0, 0.0);
@@ -123,12 +136,11 @@ __global__ void k_pair_generators(const MsdConfig* __restrict__ cfg, int ci,
     const double dx = Op.x - Oq.x, dy = Op.y - Oq.y;
     const double b = hypot(dx, dy);
     const double2 e1 = make_double2(dx / b, dy / b);
-    double J[MAXL], Y[MAXL];
-    bessel_jy(c.k * b, lmax, J, Y);
+    const double x = c.k * b;
     double2 e = make_double2(1.0, 0.0);  // e^{i l alpha}
     int bad = 0;
-    for (int l = 0; l <= lmax; ++l) {
-        const double2 H = make_double2(J[l], Y[l]);
+    auto put = [&](int l, double Jl, double Yl) {
+        const double2 H = make_double2(Jl, Yl);
         const double2 gp = cmul(H, e);                  // g_l
         double2 gm = cmul(H, cconj(e));                 // H_l e^{-i l alpha}
         if (l & 1) gm = make_double2(-gm.x, -gm.y);    // g_{-l} = (-1)^l H_l e^{-i l alpha}
@@ -142,20 +154,40 @@ __global__ void k_pair_generators(const MsdConfig* __restrict__ cfg, int ci,
             G32[base + lmax - l] = make_float2((float)gm.x, (float)gm.y);
         }
         e = cmul(e, e1);
+    };
+    if (x > 20.0 && (double)(lmax < 1 ? 1 : lmax) <= x) {
+        // far pair: J and Y both by forward recurrence from Hankel's
+        // expansion of orders 0 and 1 (the same steps as bessel_jy), on the fly
+        double sx, cx, J0, J1, Y0, Y1;
+        sincos(x, &sx, &cx);
+        bessel_asymptotic(x, 0, sx, cx, &J0, &Y0);
+        bessel_asymptotic(x, 1, sx, cx, &J1, &Y1);
+        put(0, J0, Y0);
+        for (int l = 1; l <= lmax; ++l) {
+            put(l, J1, Y1);
+            const double f = 2.0 * l / x;
+            const double J2 = f * J1 - J0, Y2 = f * Y1 - Y0;
+            J0 = J1;
+            J1 = J2;
+            Y0 = Y1;
+            Y1 = Y2;
+        }
+    } else {
+        double J[MAXL], Y[MAXL];
+        bessel_jy(x, lmax, J, Y);
+        for (int l = 0; l <= lmax; ++l) put(l, J[l], Y[l]);
     }
     if (bad) atomicOr(flags, FLAG_RANGE32);
 }
 
-void launch_pair_generators(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
-                            const double2* d_centre, double2* G64, float2* G32, int* d_flags,
-                            cudaStream_t s) {
-    for (int ci = 0; ci < C; ++ci) {
-        long long n = (long long)h_cfg[ci].M * h_cfg[ci].Mp;
-        int threads = 128;
-        long long blocks = (n + threads - 1) / threads;
-        k_pair_generators<<<(unsigned)blocks, threads, 0, s>>>(d_cfg, ci, d_centre, G64, G32, d_flags);
-    }
-    g_msd_launches += C;
+void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, int nblocks, long long nitems,
+                             const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s) {
+    if (nitems <= 0) return;
+    const int threads = 128;
+    const long long blocks = (nitems + threads - 1) / threads;
+    k_pair_generators<<<(unsigned)blocks, threads, 0, s>>>(d_cfg, d_blocks, nblocks, nitems, d_centre, G64, G32,
+                                                            d_flags);
+    g_msd_launches += 1;
 }
 
 // ---------------------------------------------------------------- K5

@@ -8,17 +8,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "msd_internal.cuh"
-
-// ---------------------------------------------------------------- launchers from other units
-
-int matvec_col_tile(int R, int Nmax, bool fp64);
-size_t matvec_smem_bytes(int R, int Nmax, bool fp64);
-int matvec_blocks_per_sm(int R, int Nmax, bool fp64);
 
 // ---------------------------------------------------------------- errors
 
@@ -118,6 +115,30 @@ struct MatvecPlan {
     std::vector<MatvecWork> work;
     MatvecWork* d_work = nullptr;
     int nsplit = 1;
+    MatvecChoice ch{0, 1, 1, 0};  // tile shape of the product kernel
+    int candidates = 0;           // shapes the autotuner timed (0: model choice)
+    double tuned_ms = 0;          // kernel time of the chosen shape in the tuning run
+};
+
+// Product plan with recomputed generators: chunks of generator blocks
+// (configuration x target range x source range) small enough to stay in L2;
+// per chunk the generator kernel fills the chunk buffer and the product
+// kernel reads it through a configuration array whose generator offset and
+// target stride address that buffer.
+struct RecomputeChunk {
+    MsdConfig* d_cfg = nullptr;  // [C] copies with gen_off/Mp of this chunk
+    GenBlock* d_blocks = nullptr;
+    int nblocks = 0;
+    long long nitems = 0;
+    MatvecWork* d_work = nullptr;
+    int nwork = 0;
+};
+
+struct RecomputePlan {
+    std::vector<RecomputeChunk> chunks;
+    size_t buf_elems = 0;  // largest chunk buffer (complex elements)
+    int nsplit = 1;
+    MatvecChoice ch{0, 1, 1, 0};
 };
 
 struct msd_problem {
@@ -147,6 +168,15 @@ struct msd_problem {
     float2* d_clf32 = nullptr;
     long long geom_version = 0, adj64_version = -1, adj32_version = -1, adj_rows_version = -1;
     std::map<long long, MatvecPlan> plans;  // key: R*4 + precision
+    std::map<long long, MatvecChoice> pinned;  // shapes fixed by msd_set_tile
+    // generator mode of the forward products (msd_set_generator_mode)
+    int gen_mode = MSD_GEN_STREAMED;
+    size_t gen_chunk_bytes = 64ull << 20;
+    std::vector<GenBlock> gen_full;  // one block per configuration: the stored array
+    GenBlock* d_gen_full = nullptr;
+    std::map<long long, RecomputePlan> rplans;  // key: R*4 + precision
+    DBuf genbuf;
+    long long rc_checked = -1;  // geometry version whose complex64 range was checked
     std::vector<RowChunk> chunks;
     RowChunk* d_chunks = nullptr;
     int* d_cfg_chunk_off = nullptr;
@@ -188,33 +218,46 @@ void check_flags(msd_problem* pb, const char* where) {
     if (f & 2) fail(MSD_ERR_RANGE, std::string(where) + ": a Hankel generator exceeds the complex64 range; use MSD_FP64");
 }
 
+// K2 over the whole problem: the stored generator array(s).
+void launch_full_generators(msd_problem* pb, double2* G64, float2* G32) {
+    if (!pb->d_gen_full) {
+        pb->gen_full.clear();
+        long long items = 0;
+        for (int ci = 0; ci < pb->C; ++ci) {
+            const MsdConfig& c = pb->cfg[ci];
+            GenBlock g{ci, 0, c.Mp, 0, c.M, 0, items, c.gen_off};
+            pb->gen_full.push_back(g);
+            items += (long long)c.M * c.Mp;
+        }
+        pb->d_gen_full = dalloc_copy(pb->gen_full.data(), pb->gen_full.size());
+    }
+    const GenBlock& last = pb->gen_full.back();
+    launch_generator_blocks(pb->d_cfg, pb->d_gen_full, pb->C, last.item_off + (long long)last.Qb * last.Pc,
+                            pb->d_centre, G64, G32, pb->d_flags, pb->stream);
+}
+
 void ensure_generators(msd_problem* pb, bool fp64) {
     if (fp64 && pb->d_G64) return;
     if (!fp64 && pb->d_G32) return;
     if (fp64) pb->d_G64 = dalloc<double2>(pb->gen_elems);
     else pb->d_G32 = dalloc<float2>(pb->gen_elems);
-    launch_pair_generators(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, fp64 ? pb->d_G64 : nullptr,
-                           fp64 ? nullptr : pb->d_G32, pb->d_flags, pb->stream);
+    launch_full_generators(pb, fp64 ? pb->d_G64 : nullptr, fp64 ? nullptr : pb->d_G32);
     CK_LAUNCH();
     check_flags(pb, "pair generators");
 }
 
-MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
-    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
-    auto it = pb->plans.find(key);
-    if (it != pb->plans.end()) return it->second;
-    MatvecPlan plan;
-    const int RT = matvec_col_tile(R, pb->Nmax, fp64);
-    const int rtiles = R / RT;
+// Work list of a plan: every 32-target tile of every configuration, its
+// sources split into ns ranges.  ns is chosen so that the CTAs fill whole
+// waves of the resident slots: efficiency(ns) = (work items / slots) /
+// ceil(...) times the balance of the largest source range against the mean.
+void build_work(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
+    const int rtiles = R / plan.ch.RT;
     long long tiles = 0;
     for (auto& c : pb->cfg) tiles += c.Mp / MSD_TILE_P;
-    // Split the source range so that the CTAs fill whole waves of the
-    // resident slots: efficiency(ns) = (work items / slots) / ceil(...) times
-    // the balance of the largest source range against the mean.
     int sms = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const long long slots = (long long)sms * matvec_blocks_per_sm(R, pb->Nmax, fp64);
+    const long long slots = (long long)sms * matvec_blocks_per_sm(plan.ch, pb->Nmax, fp64);
     const long long units = tiles * rtiles;
     const size_t elem = fp64 ? 16 : 8;
     int ns = 1;
@@ -232,6 +275,7 @@ MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
         }
     }
     plan.nsplit = ns;
+    plan.work.clear();
     for (int ci = 0; ci < pb->C; ++ci) {
         const MsdConfig& c = pb->cfg[ci];
         for (int p0 = 0; p0 < c.Mp; p0 += MSD_TILE_P)
@@ -246,14 +290,266 @@ MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
                 plan.work.push_back(w);
             }
     }
+}
+
+// Autotuner: time the product kernel of every candidate tile shape (with its
+// own split count) on the problem's generators and keep the fastest.  Large
+// products are timed on a prefix of the work list of about 20 ms, scaled to
+// the whole list.  Results are cached per process by problem shape.  The
+// tuning run synchronises the stream; MSD_AUTOTUNE=0 keeps the model choice.
+bool autotune_enabled() {
+    const char* e = std::getenv("MSD_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+typedef std::tuple<int, int, int, int, long long, int, int> TuneKey;  // Nmax R fp64 C Ntot Mmax device
+
+void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
+    static std::mutex mu;
+    static std::map<TuneKey, std::pair<MatvecChoice, double>> cache;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const TuneKey key{pb->Nmax, R, fp64 ? 1 : 0, pb->C, pb->Ntot, pb->Mmax, dev};
+    MatvecChoice cand[64];
+    const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 64);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            plan.ch = it->second.first;
+            plan.tuned_ms = it->second.second;
+            plan.candidates = nc;
+            return;
+        }
+    }
+    if (nc <= 1) return;
+    const size_t elem = fp64 ? 16 : 8;
+    const size_t vec = (size_t)pb->Ntot * R * elem;
+    void* xs = pb->xs.get(vec);
+    CK(cudaMemsetAsync(xs, 0, vec, pb->stream));
+    const void* G = fp64 ? (const void*)pb->d_G64 : (const void*)pb->d_G32;
+    // estimated full time (FP64 ~1.2 TFLOP/s, FP32 ~40 TFLOP/s) -> prefix fraction
+    const double est_ms = 8.0 * R * pb->offdiag_n2 / (fp64 ? 1.2e9 : 4.0e10);
+    const double frac = est_ms > 20.0 ? 20.0 / est_ms : 1.0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    DBuf dwork;
+    double best_ms = 1e300;
+    MatvecChoice best = plan.ch;
+    for (int i = 0; i < nc; ++i) {
+        MatvecPlan trial;
+        trial.ch = cand[i];
+        build_work(pb, trial, R, fp64);
+        const int nfull = (int)trial.work.size();
+        const int nw = std::max(1, std::min(nfull, (int)std::ceil(frac * nfull)));
+        MatvecWork* dw = (MatvecWork*)dwork.get(nfull * sizeof(MatvecWork));
+        CK(cudaMemcpyAsync(dw, trial.work.data(), nw * sizeof(MatvecWork), cudaMemcpyHostToDevice, pb->stream));
+        void* part = pb->part.get((size_t)trial.nsplit * vec);
+        double t = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {  // first run warms caches and the module
+            CK(cudaEventRecord(e0, pb->stream));
+            launch_bt_only(cand[i], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
+            CK_LAUNCH();
+            CK(cudaEventRecord(e1, pb->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) t = std::min(t, (double)ms * nfull / nw);
+        }
+        if (t < best_ms) {
+            best_ms = t;
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dwork.release();
+    plan.ch = best;
+    plan.tuned_ms = best_ms;
+    plan.candidates = nc;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {best, best_ms};
+}
+
+MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
+    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
+    auto it = pb->plans.find(key);
+    if (it != pb->plans.end()) return it->second;
+    MatvecPlan plan;
+    auto pin = pb->pinned.find(key);
+    if (pin != pb->pinned.end()) {
+        plan.ch = pin->second;
+    } else {
+        plan.ch = matvec_default_choice(R, pb->Nmax, fp64);
+        if (autotune_enabled()) autotune(pb, plan, R, fp64);
+    }
+    build_work(pb, plan, R, fp64);
     plan.d_work = dalloc_copy(plan.work.data(), plan.work.size());
     return pb->plans.emplace(key, std::move(plan)).first->second;
 }
 
+// Chunks of a recomputed product.  A configuration whose M x Mp pairs fit
+// the budget is one block (several such share a chunk); a larger one is cut
+// into blocks of Qb >= 32 sources by Pc targets (multiples of 32), one
+// chunk each.  Work items split each block's sources into ns ranges; the
+// items of blocks with Q0 > 0 add to the partial sums (pad = 1).
+RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
+    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
+    auto it = pb->rplans.find(key);
+    if (it != pb->rplans.end()) return it->second;
+    RecomputePlan rp;
+    auto pin = pb->pinned.find(key);
+    rp.ch = pin != pb->pinned.end() ? pin->second : matvec_default_choice(R, pb->Nmax, fp64);
+    const size_t elem = fp64 ? 16 : 8;
+    const long long budget = std::max<long long>(1, (long long)(pb->gen_chunk_bytes / (elem * (4 * pb->Nmax + 1))));
+    // blocks grouped into chunks
+    std::vector<std::vector<GenBlock>> groups;
+    std::vector<GenBlock> cur;
+    long long cur_rows = 0;
+    auto flush = [&]() {
+        if (!cur.empty()) groups.push_back(cur);
+        cur.clear();
+        cur_rows = 0;
+    };
+    for (int ci = 0; ci < pb->C; ++ci) {
+        const MsdConfig& c = pb->cfg[ci];
+        const long long rows = (long long)c.M * c.Mp;
+        if (rows <= budget) {
+            if (cur_rows + rows > budget) flush();
+            cur.push_back(GenBlock{ci, 0, c.Mp, 0, c.M, 0, 0, 0});
+            cur_rows += rows;
+            continue;
+        }
+        flush();
+        const int Qb = std::min<long long>(c.M, std::max<long long>(32, budget / c.Mp));
+        const int Pc = (int)std::min<long long>(c.Mp, MSD_TILE_P * std::max<long long>(1, budget / (MSD_TILE_P * (long long)Qb)));
+        for (int P0 = 0; P0 < c.Mp; P0 += Pc)
+            for (int Q0 = 0; Q0 < c.M; Q0 += Qb) {
+                groups.push_back({GenBlock{ci, P0, std::min(Pc, c.Mp - P0), Q0, std::min(Qb, c.M - Q0), 0, 0, 0}});
+            }
+    }
+    flush();
+    // splits: enough CTAs in the largest chunk to fill the resident slots
+    int sms = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long slots = (long long)sms * matvec_blocks_per_sm(rp.ch, pb->Nmax, fp64);
+    long long max_units = 1;
+    int min_q = 1 << 30;
+    for (auto& g : groups) {
+        long long u = 0;
+        for (auto& b : g) {
+            u += (long long)(b.Pc / MSD_TILE_P) * (R / rp.ch.RT);
+            min_q = std::min(min_q, b.Qb);
+        }
+        max_units = std::max(max_units, u);
+    }
+    int ns = (int)std::min<long long>(64, std::max<long long>(1, (slots + max_units - 1) / max_units));
+    ns = std::max(1, std::min(ns, std::max(1, min_q / 2)));
+    while (ns > 1 && (size_t)ns * pb->Ntot * R * elem > (2ull << 30)) --ns;
+    rp.nsplit = ns;
+    for (auto& g : groups) {
+        RecomputeChunk ch;
+        std::vector<MsdConfig> ccfg = pb->cfg;
+        std::vector<MatvecWork> work;
+        long long items = 0, out = 0;
+        for (auto& b : g) {
+            const MsdConfig& c = pb->cfg[b.cfg];
+            b.item_off = items;
+            b.out_off = out;
+            ccfg[b.cfg].Mp = b.Pc;
+            ccfg[b.cfg].gen_off = out - ((long long)b.Q0 * b.Pc + b.P0) * c.L;
+            items += (long long)b.Qb * b.Pc;
+            out += (long long)b.Qb * b.Pc * c.L;
+            for (int p0 = b.P0; p0 < b.P0 + b.Pc; p0 += MSD_TILE_P)
+                for (int sp = 0; sp < ns; ++sp) {
+                    MatvecWork w;
+                    w.cfg = b.cfg;
+                    w.p0 = p0;
+                    w.q0 = b.Q0 + (int)((long long)b.Qb * sp / ns);
+                    w.q1 = b.Q0 + (int)((long long)b.Qb * (sp + 1) / ns);
+                    w.split = sp;
+                    w.pad = b.Q0 > 0 ? 1 : 0;
+                    work.push_back(w);
+                }
+        }
+        ch.d_cfg = dalloc_copy(ccfg.data(), ccfg.size());
+        ch.d_blocks = dalloc_copy(g.data(), g.size());
+        ch.nblocks = (int)g.size();
+        ch.nitems = items;
+        ch.d_work = dalloc_copy(work.data(), work.size());
+        ch.nwork = (int)work.size();
+        rp.buf_elems = std::max(rp.buf_elems, (size_t)out);
+        rp.chunks.push_back(ch);
+    }
+    return pb->rplans.emplace(key, std::move(rp)).first->second;
+}
+
+void free_recompute_plans(msd_problem* pb) {
+    for (auto& kv : pb->rplans)
+        for (auto& ch : kv.second.chunks) {
+            cudaFree(ch.d_cfg);
+            cudaFree(ch.d_blocks);
+            cudaFree(ch.d_work);
+        }
+    pb->rplans.clear();
+}
+
+// y = P^-1 A x with the generators recomputed chunk by chunk (no stored array).
+void matvec_recompute_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
+    RecomputePlan& rp = get_recompute_plan(pb, R, fp64);
+    const size_t elem = fp64 ? 16 : 8;
+    void* gbuf = pb->genbuf.get(rp.buf_elems * elem);
+    if (!fp64 && pb->rc_checked != pb->geom_version) {
+        // complex64 range of every generator, once per geometry
+        CK(cudaMemsetAsync(pb->d_flags, 0, sizeof(int), pb->stream));
+        for (auto& ch : rp.chunks)
+            launch_generator_blocks(pb->d_cfg, ch.d_blocks, ch.nblocks, ch.nitems, pb->d_centre, nullptr,
+                                    (float2*)gbuf, pb->d_flags, pb->stream);
+        CK_LAUNCH();
+        check_flags(pb, "recomputed generators");
+        pb->rc_checked = pb->geom_version;
+    }
+    void* xs = pb->xs.get((size_t)pb->Ntot * R * elem);
+    void* part = pb->part.get((size_t)rp.nsplit * pb->Ntot * R * elem);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (pb->timing) {
+        while (pb->events.size() < 256) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            pb->events.push_back(e);
+        }
+        if (pb->ev_used + 2 > pb->events.size()) flush_timing(pb);
+        e0 = pb->events[pb->ev_used++];
+        e1 = pb->events[pb->ev_used++];
+        pb->timed_flops += 8.0 * (double)R * pb->offdiag_n2;
+        pb->timed_bytes += (double)elem * 2.0 * (double)pb->Ntot * R;  // no stored generators
+    }
+    launch_scale_cols(fp64, pb->Ntot, R, fp64 ? (const void*)pb->d_rf64 : (const void*)pb->d_rf32, x, xs,
+                      pb->stream);
+    if (e0) CK(cudaEventRecord(e0, pb->stream));
+    for (auto& ch : rp.chunks) {
+        launch_generator_blocks(pb->d_cfg, ch.d_blocks, ch.nblocks, ch.nitems, pb->d_centre,
+                                fp64 ? (double2*)gbuf : nullptr, fp64 ? nullptr : (float2*)gbuf, pb->d_flags,
+                                pb->stream);
+        launch_bt_only(rp.ch, fp64, ch.d_cfg, ch.d_work, ch.nwork, pb->Nmax, gbuf, xs, part, pb->Ntot, R,
+                       pb->stream);
+    }
+    if (e1) CK(cudaEventRecord(e1, pb->stream));
+    launch_finalize(fp64, pb->Ntot, R, rp.nsplit, fp64 ? (const void*)pb->d_lf64 : (const void*)pb->d_lf32, x, part,
+                    y, pb->stream);
+    CK_LAUNCH();
+}
+
 // y = P^-1 A x on the problem's stream (device pointers).
 void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
-    if (matvec_smem_bytes(R, pb->Nmax, fp64) > 227 * 1024)
+    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
+    if (pb->gen_mode == MSD_GEN_RECOMPUTE) {
+        matvec_recompute_dev(pb, R, fp64, x, y);
+        return;
+    }
     ensure_generators(pb, fp64);
     MatvecPlan& plan = get_plan(pb, R, fp64);
     const size_t elem = fp64 ? 16 : 8;
@@ -278,11 +574,11 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
     if (fp64)
         launch_matvec_f64(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G64, pb->d_rf64,
                           pb->d_lf64, pb->Ntot, R, (const double2*)x, (double2*)xs, (double2*)part,
-                          plan.nsplit, (double2*)y, pb->stream, e0, e1);
+                          plan.nsplit, (double2*)y, pb->stream, e0, e1, &plan.ch);
     else
         launch_matvec_f32(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G32, pb->d_rf32,
                           pb->d_lf32, pb->Ntot, R, (const float2*)x, (float2*)xs, (float2*)part,
-                          plan.nsplit, (float2*)y, pb->stream, e0, e1);
+                          plan.nsplit, (float2*)y, pb->stream, e0, e1, &plan.ch);
     CK_LAUNCH();
 }
 
@@ -320,7 +616,7 @@ void ensure_adjoint(msd_problem* pb, bool fp64) {
 //   adjoint: y = x + r .* T^H(conj(l) .* x)       ((P^-1 A)^H x)
 //   raw forward: y = T(r .* x)    raw adjoint: y = T^H(conj(l) .* x)
 void product_dev(msd_problem* pb, int R, bool fp64, bool adjoint, bool raw, const void* x, void* y) {
-    if (matvec_smem_bytes(R, pb->Nmax, fp64) > 227 * 1024)
+    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     if (adjoint) ensure_adjoint(pb, fp64);
     else ensure_generators(pb, fp64);
@@ -334,13 +630,15 @@ void product_dev(msd_problem* pb, int R, bool fp64, bool adjoint, bool raw, cons
         launch_product_f64(pb->d_cfg, plan.d_work, nwork, pb->Nmax, G, adjoint ? nullptr : pb->d_rf64,
                            adjoint ? pb->d_clf64 : nullptr, (adjoint && !raw) ? pb->d_rf64 : nullptr,
                            (!adjoint && !raw) ? pb->d_lf64 : nullptr, raw ? 0 : 1, pb->Ntot, R,
-                           (const double2*)x, (double2*)xs, (double2*)part, plan.nsplit, (double2*)y, pb->stream);
+                           (const double2*)x, (double2*)xs, (double2*)part, plan.nsplit, (double2*)y, pb->stream,
+                           &plan.ch);
     } else {
         const float2* G = adjoint ? pb->d_GA32 : pb->d_G32;
         launch_product_f32(pb->d_cfg, plan.d_work, nwork, pb->Nmax, G, adjoint ? nullptr : pb->d_rf32,
                            adjoint ? pb->d_clf32 : nullptr, (adjoint && !raw) ? pb->d_rf32 : nullptr,
                            (!adjoint && !raw) ? pb->d_lf32 : nullptr, raw ? 0 : 1, pb->Ntot, R,
-                           (const float2*)x, (float2*)xs, (float2*)part, plan.nsplit, (float2*)y, pb->stream);
+                           (const float2*)x, (float2*)xs, (float2*)part, plan.nsplit, (float2*)y, pb->stream,
+                           &plan.ch);
     }
     CK_LAUNCH();
 }
@@ -489,6 +787,15 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     msd_opts o;
     memset(&o, 0, sizeof(o));
     if (opts_in) o = *opts_in;
+    if (o.gen_mode != MSD_GEN_AUTO && o.gen_mode != MSD_GEN_STREAMED && o.gen_mode != MSD_GEN_RECOMPUTE)
+        fail(MSD_ERR_ARG, "msd_solve_planewaves: gen_mode");
+    // a solve-level generator mode applies to this solve's forward products only
+    struct ModeGuard {
+        msd_problem* pb;
+        int old;
+        ~ModeGuard() { pb->gen_mode = old; }
+    } mode_guard{pb, pb->gen_mode};
+    if (o.gen_mode != MSD_GEN_AUTO && !adjoint) pb->gen_mode = o.gen_mode;
     if (o.tol <= 0) o.tol = 1e-10;
     if (o.restart <= 0) {
         // Automatic restart length: GMRES converges fastest unrestarted, and
@@ -569,7 +876,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     if (adjoint) {
         ensure_adjoint(pb, true);
         if (mixed) ensure_adjoint(pb, false);
-    } else {
+    } else if (pb->gen_mode != MSD_GEN_RECOMPUTE) {
         ensure_generators(pb, true);
         if (mixed) ensure_generators(pb, false);
     }
@@ -805,6 +1112,9 @@ void msd_destroy(msd_problem* pb) {
         if (p) cudaFree(p);
     for (auto& kv : pb->plans)
         if (kv.second.d_work) cudaFree(kv.second.d_work);
+    free_recompute_plans(pb);
+    if (pb->d_gen_full) cudaFree(pb->d_gen_full);
+    pb->genbuf.release();
     if (pb->h_pinned) cudaFreeHost(pb->h_pinned);
     for (cudaEvent_t e : pb->events) cudaEventDestroy(e);
     for (cudaEvent_t e : pb->ring_ev)
@@ -901,12 +1211,88 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
                               pb->d_dJ, pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                               pb->d_rhs_scale, pb->d_flags, pb->stream);
         CK_LAUNCH();
-        if (pb->d_G64 || pb->d_G32)
-            launch_pair_generators(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_G64, pb->d_G32,
-                                   pb->d_flags, pb->stream);
+        if (pb->d_G64 || pb->d_G32) launch_full_generators(pb, pb->d_G64, pb->d_G32);
         CK_LAUNCH();
         check_flags(pb, "msd_update_geometry");
         pb->geom_version += 1;  // adjoint operator data is rebuilt on next use
+        return MSD_OK;
+    });
+}
+
+msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes) {
+    return guarded([&]() -> msd_status {
+        if (!pb || chunk_bytes < 0) fail(MSD_ERR_ARG, "msd_set_generator_mode: bad argument");
+        if (mode != MSD_GEN_AUTO && mode != MSD_GEN_STREAMED && mode != MSD_GEN_RECOMPUTE)
+            fail(MSD_ERR_ARG, "msd_set_generator_mode: mode");
+        if (mode == MSD_GEN_AUTO) {
+            size_t free_b = 0, total_b = 0;
+            CK(cudaMemGetInfo(&free_b, &total_b));
+            const double need = (double)pb->gen_elems * (16.0 + 8.0);  // complex128 and complex64 copies
+            mode = need <= 0.5 * (double)free_b ? MSD_GEN_STREAMED : MSD_GEN_RECOMPUTE;
+        }
+        const size_t budget = chunk_bytes ? (size_t)chunk_bytes : (64ull << 20);
+        CK(cudaStreamSynchronize(pb->stream));
+        if (budget != pb->gen_chunk_bytes) free_recompute_plans(pb);
+        pb->gen_chunk_bytes = budget;
+        pb->gen_mode = mode;
+        if (mode == MSD_GEN_RECOMPUTE) {
+            if (pb->d_G64) cudaFree(pb->d_G64);
+            if (pb->d_G32) cudaFree(pb->d_G32);
+            pb->d_G64 = nullptr;
+            pb->d_G32 = nullptr;
+        } else {
+            free_recompute_plans(pb);
+            pb->genbuf.release();
+        }
+        return MSD_OK;
+    });
+}
+
+msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double* tuned_ms) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || !out) fail(MSD_ERR_ARG, "msd_plan_info: bad argument");
+        if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_plan_info: precision");
+        const bool fp64 = precision == MSD_FP64;
+        ensure_generators(pb, fp64);
+        MatvecPlan& plan = get_plan(pb, R, fp64);
+        out[0] = plan.ch.KB;
+        out[1] = plan.ch.RT;
+        out[2] = plan.nsplit;
+        out[3] = plan.candidates;
+        if (tuned_ms) *tuned_ms = plan.tuned_ms;
+        return MSD_OK;
+    });
+}
+
+msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0) fail(MSD_ERR_ARG, "msd_set_tile: bad argument");
+        if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_set_tile: precision");
+        const bool fp64 = precision == MSD_FP64;
+        MatvecChoice cand[64];
+        const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 64);
+        int hit = -1;
+        for (int i = 0; i < nc; ++i)
+            if (cand[i].KB == KB && cand[i].RT == RT) hit = i;
+        if (hit < 0) fail(MSD_ERR_ARG, "msd_set_tile: (KB, RT) is not an instantiated shape that fits");
+        const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
+        auto it = pb->plans.find(key);
+        if (it != pb->plans.end()) {
+            CK(cudaStreamSynchronize(pb->stream));  // the old work list may still be read
+            if (it->second.d_work) cudaFree(it->second.d_work);
+            pb->plans.erase(it);
+        }
+        auto rit = pb->rplans.find(key);
+        if (rit != pb->rplans.end()) {
+            CK(cudaStreamSynchronize(pb->stream));
+            for (auto& ch : rit->second.chunks) {
+                cudaFree(ch.d_cfg);
+                cudaFree(ch.d_blocks);
+                cudaFree(ch.d_work);
+            }
+            pb->rplans.erase(rit);
+        }
+        pb->pinned[key] = cand[hit];
         return MSD_OK;
     });
 }
@@ -1095,7 +1481,8 @@ extern "C" msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, 
         if ((fp64 && !pb->d_G64) || (!fp64 && !pb->d_G32))
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: the generators of this precision are not built yet "
                               "(call msd_matvec or msd_solve_planewaves once first)");
-        if (matvec_smem_bytes(R, pb->Nmax, fp64) > 227 * 1024)
+        const MatvecChoice dc = matvec_default_choice(R, pb->Nmax, fp64);
+        if (matvec_smem_bytes(dc, pb->Nmax, fp64) > 227 * 1024)
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: truncation order too large for the shared-memory tile");
         unsigned char* base = (unsigned char*)static_scratch_address();
         // layout: [work list][xs][partials], each 256-byte aligned
@@ -1111,8 +1498,8 @@ extern "C" msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, 
         int sms = 0, dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const long long slots = (long long)sms * matvec_blocks_per_sm(R, pb->Nmax, fp64);
-        const long long units = tiles * (R / matvec_col_tile(R, pb->Nmax, fp64));
+        const long long slots = (long long)sms * matvec_blocks_per_sm(dc, pb->Nmax, fp64);
+        const long long units = tiles * (R / dc.RT);
         int ns = (int)std::max<long long>(1, std::min<long long>(slots / std::max<long long>(1, units),
                                                                  std::max(1, pb->Mmax / 2)));
         while (ns > 1 && need(ns) > kStaticScratchBytes) --ns;

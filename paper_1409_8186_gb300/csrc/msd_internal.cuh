@@ -70,7 +70,8 @@ struct MsdConfig {
 
 // One CTA of the block-Toeplitz product: a tile of 32 target disks
 // [p0, p0+32) of configuration cfg, summed over sources [q0, q1), writing
-// its raw sums into partial slot `split`.
+// its raw sums into partial slot `split` (pad = 0) or adding them to it
+// (pad = 1: a later source block of a product with recomputed generators).
 struct MatvecWork {
     int cfg, p0, q0, q1, split, pad;
 };
@@ -84,6 +85,26 @@ struct RowChunk {
 
 #define MSD_TILE_P 32
 
+// Tile shape of one product kernel instance: register window KB (modes per
+// thread), column tile RT and register column block RB, I = ceil(n / KB)
+// thread rows.  matvec_default_choice is the cost model; the autotuner in
+// the problem's plan times matvec_candidates and keeps the fastest.
+struct MatvecChoice {
+    int KB, RT, RB, I;
+};
+MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64);
+int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap);
+size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64);
+int matvec_blocks_per_sm(const MatvecChoice& c, int Nmax, bool fp64);
+// the pieces of a product: xs = r .* x; y = x + l .* sum of the partials
+void launch_scale_cols(bool fp64, long long Ntot, int R, const void* rf, const void* x, void* xs, cudaStream_t s);
+void launch_finalize(bool fp64, long long Ntot, int R, int nsplit, const void* lf, const void* x, const void* part,
+                     void* y, cudaStream_t s);
+// the Toeplitz kernel alone on pre-scaled columns xs (autotuner timing,
+// recomputed products); work items with pad != 0 add to their partial slot
+void launch_bt_only(const MatvecChoice& c, bool fp64, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork,
+                    int Nmax, const void* G, const void* xs, void* part, long long Ntot, int R, cudaStream_t s);
+
 // Number of kernels the library has launched (host-side counter, all threads).
 extern std::atomic<long long> g_msd_launches;
 
@@ -96,10 +117,16 @@ void launch_disk_diagonals(const MsdConfig* d_cfg, int Mtot, const int* d_disk_c
                            double2* lf64, double* rf64, float2* lf32, float* rf32,
                            double2* rhs_scale, int* d_flags, cudaStream_t s);
 
-// K2: Toeplitz generators of every ordered pair, complex128 and/or complex64.
-void launch_pair_generators(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
-                            const double2* d_centre, double2* G64, float2* G32,
-                            int* d_flags, cudaStream_t s);
+// K2: Toeplitz generators of the ordered pairs of a list of blocks
+// (configuration, target range [P0, P0+Pc), source range [Q0, Q0+Qb)),
+// complex128 and/or complex64, block e at out[out_off + ((q-Q0) Pc + p-P0) L].
+// item_off is the running count of (q, p) items before the block.
+struct GenBlock {
+    int cfg, P0, Pc, Q0, Qb, pad;
+    long long item_off, out_off;
+};
+void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, int nblocks, long long nitems,
+                             const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s);
 
 // K5: preconditioned plane-wave right-hand sides.
 void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
@@ -111,11 +138,13 @@ void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cf
 void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const double2* G, const double* rf, const double2* lf, long long Ntot,
                        int R, const double2* x, double2* xs, double2* part, int nsplit,
-                       double2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                       double2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                       const MatvecChoice* ch = nullptr);
 void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const float2* G, const float* rf, const float2* lf, long long Ntot,
                        int R, const float2* x, float2* xs, float2* part, int nsplit,
-                       float2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                       float2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                       const MatvecChoice* ch = nullptr);
 
 // K6: far field.
 void launch_farfield(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
@@ -166,11 +195,11 @@ void gm_zero(long long n, double2* x, cudaStream_t s);
 void launch_product_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const double2* G,
                         const double* col_r, const double2* col_c, const double* row_r, const double2* row_c,
                         int add_x, long long Ntot, int R, const double2* x, double2* xs, double2* part, int nsplit,
-                        double2* y, cudaStream_t s);
+                        double2* y, cudaStream_t s, const MatvecChoice* ch = nullptr);
 void launch_product_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float2* G,
                         const float* col_r, const float2* col_c, const float* row_r, const float2* row_c,
                         int add_x, long long Ntot, int R, const float2* x, float2* xs, float2* part, int nsplit,
-                        float2* y, cudaStream_t s);
+                        float2* y, cudaStream_t s, const MatvecChoice* ch = nullptr);
 void launch_adjoint_generators_f64(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg, const double2* G,
                                    double2* GA, cudaStream_t s);
 void launch_adjoint_generators_f32(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg, const float2* G,

@@ -67,6 +67,9 @@ def _load():
         "msd_update_geometry": (I, [P, P, P, P]),
         "msd_grad_farfield_misfit": (I, [P, I, P, I, P, P, ctypes.POINTER(msd_opts), P, P, P, P]),
         "msd_matvec_timing": (I, [P, I, P, P, P, P]),
+        "msd_plan_info": (I, [P, I, I, P, P]),
+        "msd_set_tile": (I, [P, I, I, I, I]),
+        "msd_set_generator_mode": (I, [P, I, ctypes.c_int64]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
     }
@@ -81,7 +84,9 @@ _lib = _load()
 EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "msd_disk_diagonals",
             "msd_pair_generators", "msd_rhs_planewave", "msd_matvec", "msd_solve_planewaves",
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
-            "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_last_error")
+            "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
+            "msd_set_generator_mode",
+            "msd_last_error")
 
 
 def library_path() -> str:
@@ -206,6 +211,22 @@ def msd_matvec_timing(h, enable: int):
     return ms.value, n.value, fl.value, by.value
 
 
+def msd_plan_info(h, R: int, precision: int):
+    """Returns ({"KB", "RT", "nsplit", "candidates"}, tuned_ms) of the product plan for (R, precision)."""
+    out = (ctypes.c_int * 4)()
+    ms = ctypes.c_double()
+    _check(_lib.msd_plan_info(h, R, precision, out, ctypes.byref(ms)))
+    return {"KB": out[0], "RT": out[1], "nsplit": out[2], "candidates": out[3]}, ms.value
+
+
+def msd_set_tile(h, R: int, precision: int, KB: int, RT: int) -> None:
+    _check(_lib.msd_set_tile(h, R, precision, KB, RT))
+
+
+def msd_set_generator_mode(h, mode: int, chunk_bytes: int = 0) -> None:
+    _check(_lib.msd_set_generator_mode(h, mode, chunk_bytes))
+
+
 def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
 
@@ -291,12 +312,21 @@ class Problem:
         msd_matvec(self.handle, R, precision, x, y)
         return y
 
+    def plan_info(self, R: int, precision: int = MSD_FP64):
+        return msd_plan_info(self.handle, R, precision)
+
+    def set_tile(self, R: int, precision: int, KB: int, RT: int) -> None:
+        msd_set_tile(self.handle, R, precision, KB, RT)
+
+    def set_generator_mode(self, mode: int, chunk_bytes: int = 0) -> None:
+        msd_set_generator_mode(self.handle, mode, chunk_bytes)
+
     def solve(self, betas, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64, max_refine=0,
-              inner_tol=0.0, out=None) -> SolveResult:
+              inner_tol=0.0, out=None, gen_mode=MSD_GEN_AUTO) -> SolveResult:
         import torch
         b = self._betas(betas)
         R = b.shape[1]
-        o = msd_opts(tol, restart, maxit, max_refine, inner_tol, precision, MSD_GEN_AUTO)
+        o = msd_opts(tol, restart, maxit, max_refine, inner_tol, precision, gen_mode)
         rho = torch.empty((self.ntot, R), dtype=torch.complex128, device="cuda") if out is None else out
         stats = (msd_stats * (self.C * R))()
         st = msd_solve_planewaves(self.handle, R, b, o, rho, stats)

@@ -170,6 +170,50 @@ def test_matvec_fp32(msd, name, R):
     assert relerr(y, ref) < 1e-5
 
 
+@pytest.mark.parametrize("fp64", [True, False])
+def test_matvec_every_tile_shape(msd, fp64):
+    """Each instantiated tile shape (register window KB, column tile RT),
+    pinned with msd_set_tile, against the oracle; rand70 spans three target
+    tiles with a ragged tail and R = 16 admits every column tile."""
+    cl = CASES["rand70"]()
+    R = 16
+    prec = msd.MSD_FP64 if fp64 else msd.MSD_FP32
+    x = rand_x(cl.ntot, R, seed=77)
+    if not fp64:
+        x = x.astype(np.complex64)
+    ref = dense_pre(cl) @ x.astype(np.complex128)
+    xd = torch.from_numpy(x).cuda()
+    pb = msd.Problem(cl)
+    tried = 0
+    for KB in range(4, 10):
+        for RT in (1, 2, 4, 8, 16):
+            try:
+                pb.set_tile(R, prec, KB, RT)
+            except msd.MsdError:
+                continue
+            info, _ = pb.plan_info(R, prec)
+            assert (info["KB"], info["RT"]) == (KB, RT)
+            y = np_(pb.matvec(xd, prec))
+            assert relerr(y, ref) < (1e-11 if fp64 else 1e-5), (KB, RT)
+            tried += 1
+    n = 2 * cl.N + 1
+    expect = 0
+    for KB in range(4, 8 if fp64 else 10):
+        I = -(-n // KB)
+        expect += sum(1 for RT in ((1,) if fp64 else (1, 2, 4, 8, 16)) if I * (RT // min(RT, 4)) <= 16)
+    assert tried == expect
+
+
+def test_autotuned_plan(msd):
+    cl = CASES["rand70"]()
+    pb = msd.Problem(cl)
+    for prec, R in ((msd.MSD_FP64, 1), (msd.MSD_FP32, 8)):
+        info, ms = pb.plan_info(R, prec)
+        assert info["candidates"] >= 1 and info["nsplit"] >= 1 and R % info["RT"] == 0
+        if info["candidates"] > 1:
+            assert ms > 0
+
+
 def test_matvec_single_disk_is_identity(msd):
     cl = W.Cluster(np.array([[0.3, 0.1]]), np.array([0.8]), np.zeros(1, np.int8), 3.0, 9)
     pb = msd.Problem(cl)
