@@ -172,6 +172,69 @@ def profile_only(what: str):
     torch.cuda.synchronize()
 
 
+def products_table(reps: int = 3):
+    """One JSON line per (workload, columns R, precision, kernel, generator
+    mode): the block-Toeplitz kernel's own time (CUDA events around each
+    launch, averaged over `reps` products after one untimed product) and the
+    whole product (column scaling + kernel + split reduction), with the
+    algorithmic FLOP rate and generator+vector bandwidth.  Kernels: the
+    autotuned plan ("auto", its shape reported), the cost-model CUDA-core
+    shape ("model"), and each tensor-core column tile ("tcNN")."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    F64, F32 = msd.MSD_FP64, msd.MSD_FP32
+    cases = [
+        ("random400 (M=400, N=20)", W.random_cluster_400, [(F64, 1), (F32, 1)], False),
+        ("random200_k10 (M=200, N=22)", W.cluster_200, [(F64, 16), (F32, 16)], False),
+        ("batched6 (6 of the 256 batched clusters)", lambda: W.batched_clusters(count=6), [(F32, 32)], False),
+        ("lattice4000 (M=4000, N=15)", W.lattice_4000, [(F64, 1), (F32, 1), (F32, 64)], True),
+    ]
+    for name, make, shapes, try_recompute in cases:
+        cl = make()
+        for gen in (["streamed", "recompute"] if try_recompute else ["streamed"]):
+            for prec, R in shapes:
+                kinds = ["auto", "model"]
+                if prec == F32:
+                    kinds += [f"tc{rc}" for rc in (16, 32, 64) if R % rc == 0]
+                for kind in kinds:
+                    os.environ["MSD_AUTOTUNE"] = "0" if kind == "model" else "1"
+                    pb = msd.Problem(cl)
+                    if gen == "recompute":
+                        pb.set_generator_mode(msd.MSD_GEN_RECOMPUTE)
+                    if kind.startswith("tc"):
+                        pb.set_tile(R, prec, 0, int(kind[2:]))
+                    dt = torch.complex128 if prec == F64 else torch.complex64
+                    g = torch.Generator(device="cpu").manual_seed(R)
+                    x = torch.randn(pb.ntot, R, dtype=torch.complex128, generator=g).to(dt).cuda()
+                    y = torch.empty_like(x)
+                    info, tuned = pb.plan_info(R, prec)
+                    pb.matvec(x, prec, out=y)
+                    torch.cuda.synchronize()
+                    msd.msd_matvec_timing(pb.handle, 1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        pb.matvec(x, prec, out=y)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    kms, nl, fl, by = msd.msd_matvec_timing(pb.handle, 0)
+                    prod_ms = e0.elapsed_time(e1) / reps
+                    kms /= max(nl, 1)
+                    fl /= max(nl, 1)
+                    by /= max(nl, 1)
+                    print(json.dumps({
+                        "workload": name, "R": R, "precision": "fp64" if prec == F64 else "fp32",
+                        "kernel": kind, "shape": info, "generators": gen,
+                        "kernel_ms": round(kms, 4), "product_ms": round(prod_ms, 4),
+                        "tflops": round(fl / (kms * 1e-3) / 1e12, 2),
+                        "gbs": round(by / (kms * 1e-3) / 1e9, 1)}), flush=True)
+                    pb.close()
+                    del pb, x, y
+                    torch.cuda.empty_cache()
+    os.environ.pop("MSD_AUTOTUNE", None)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,7 +244,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed"], default=None,
                     help="run a minimal workload for a profiler capture and print no JSON line")
+    ap.add_argument("--products", action="store_true",
+                    help="print a table (JSON lines) of block-product kernels over the workloads instead")
     args = ap.parse_args()
+    if args.products:
+        return products_table()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_only:

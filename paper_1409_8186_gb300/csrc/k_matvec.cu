@@ -392,7 +392,8 @@ MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64) { return choose(R
 
 // Every instantiated tile shape that fits this (R, N): FP64 KB = 4..7 with
 // RT = 1; FP32 KB = 4..9 with each column tile RT in {1, 2, 4, 8, 16} that
-// divides R and keeps I * RT / RB <= 16 warps per CTA.
+// divides R and keeps I * RT / RB <= 16 warps per CTA, and the tensor-core
+// kernel with TC in {16, 32, 64} columns dividing R (n <= 128).
 int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap) {
     const int n = 2 * Nmax + 1;
     int cnt = 0;
@@ -411,10 +412,17 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap) {
             ++cnt;
         }
     }
+    if (!fp64)
+        for (int rc = 16; rc <= 64; rc *= 2)
+            if (tc_supported(R, Nmax, rc)) {
+                if (cnt < cap) out[cnt] = Choice{0, rc, 0, 0, rc};
+                ++cnt;
+            }
     return cnt < cap ? cnt : cap;
 }
 
 size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64) {
+    if (c.TC) return tc_smem_bytes(c.TC);
     size_t b = 0;
     dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
     return b;
@@ -422,6 +430,7 @@ size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64) {
 
 // Resident CTAs per SM of one product kernel instance.
 int matvec_blocks_per_sm(const MatvecChoice& c, int Nmax, bool fp64) {
+    if (c.TC) return 1;
     int nb = 1;
     dispatch(c, fp64, [&](auto k) { nb = decltype(k)::occupancy(Nmax); });
     return nb;
@@ -456,7 +465,10 @@ void launch_bt_only(const MatvecChoice& c, bool fp64, const MsdConfig* d_cfg, co
             decltype(k)::launch(d_cfg, d_work, nwork, Nmax, (const double2*)G, (const double2*)xs, (double2*)part,
                                 Ntot, R, s);
         });
-    else
+    else if (c.TC) {
+        launch_bt_tc(c.TC, d_cfg, d_work, nwork, (const float2*)G, (const float2*)xs, (float2*)part, Ntot, R, s);
+        return;  // counted by launch_bt_tc
+    } else
         dispatch32(c, [&](auto k) {
             decltype(k)::launch(d_cfg, d_work, nwork, Nmax, (const float2*)G, (const float2*)xs, (float2*)part,
                                 Ntot, R, s);
@@ -490,9 +502,13 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
-    dispatch32(ch ? *ch : choose(R, Nmax, false), [&](auto k) {
-        decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
-    });
+    const Choice c = ch ? *ch : choose(R, Nmax, false);
+    if (c.TC) {
+        launch_bt_tc(c.TC, d_cfg, d_work, nwork, G, xs, part, Ntot, R, s);
+        g_msd_launches -= 1;  // counted below with the scaling and the reduction
+    } else {
+        dispatch32(c, [&](auto k) { decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); });
+    }
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize<float2><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
     g_msd_launches += 3;
@@ -586,6 +602,25 @@ void launch_product_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nw
                         int add_x, long long Ntot, int R, const float2* x, float2* xs, float2* part, int nsplit,
                         float2* y, cudaStream_t s, const MatvecChoice* ch) {
     const Choice c = ch ? *ch : choose(R, Nmax, false);
+    if (c.TC) {
+        // the same scalings around the tensor-core kernel
+        struct TcLaunch {
+            int RC;
+            void launch(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int, const float2* G,
+                        const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s) const {
+                launch_bt_tc(RC, d_cfg, d_work, nwork, G, xs, part, Ntot, R, s);
+                g_msd_launches -= 1;
+            }
+        };
+        const TcLaunch tl{c.TC};
+        product_general<float2, float>(
+            [&](auto f) {
+                (void)f;
+                tl.launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
+            },
+            d_cfg, d_work, nwork, Nmax, G, col_r, col_c, row_r, row_c, add_x, Ntot, R, x, xs, part, nsplit, y, s);
+        return;
+    }
     product_general<float2, float>([&](auto f) { dispatch32(c, f); }, d_cfg, d_work, nwork, Nmax, G, col_r, col_c,
                                    row_r, row_c, add_x, Ntot, R, x, xs, part, nsplit, y, s);
 }

@@ -210,10 +210,17 @@ void flush_timing(msd_problem* pb) {
     pb->ev_used = 0;
 }
 
+// A pipeline wait of the tensor-core product expired (results invalid).
+void check_tc(const char* where) {
+    const int t = tc_status_and_clear();
+    if (t > 0) fail(MSD_ERR_CUDA, std::string(where) + ": a tensor-core pipeline wait expired");
+}
+
 void check_flags(msd_problem* pb, const char* where) {
     int f = 0;
     CK(cudaMemcpyAsync(&f, pb->d_flags, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
     CK(cudaStreamSynchronize(pb->stream));
+    check_tc(where);
     if (f & 1) fail(MSD_ERR_NONFINITE, std::string(where) + ": non-finite Bessel factor (k a_p at a zero of J_m for a Neumann disk?)");
     if (f & 2) fail(MSD_ERR_RANGE, std::string(where) + ": a Hankel generator exceeds the complex64 range; use MSD_FP64");
 }
@@ -246,14 +253,32 @@ void ensure_generators(msd_problem* pb, bool fp64) {
     check_flags(pb, "pair generators");
 }
 
-// Work list of a plan: every 32-target tile of every configuration, its
+// Target tiles of a product kernel within [P0, P1) (multiples of 32): 32
+// disks for the CUDA-core kernel; for the tensor-core kernel floor(128 / n)
+// disks, restarted at every 32-disk boundary and cut at M.
+void tile_starts(const MsdConfig& c, int P0, int P1, const MatvecChoice& ch, std::vector<int>& out) {
+    out.clear();
+    if (!ch.TC) {
+        for (int p0 = P0; p0 < P1; p0 += MSD_TILE_P) out.push_back(p0);
+        return;
+    }
+    const int tp = tc_tile_disks(c.n);
+    for (int b = P0; b < P1; b += MSD_TILE_P)
+        for (int p0 = b; p0 < b + MSD_TILE_P && p0 < c.M; p0 += tp) out.push_back(p0);
+}
+
+// Work list of a plan: every target tile of every configuration, its
 // sources split into ns ranges.  ns is chosen so that the CTAs fill whole
 // waves of the resident slots: efficiency(ns) = (work items / slots) /
 // ceil(...) times the balance of the largest source range against the mean.
 void build_work(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
     const int rtiles = R / plan.ch.RT;
+    std::vector<int> starts;
     long long tiles = 0;
-    for (auto& c : pb->cfg) tiles += c.Mp / MSD_TILE_P;
+    for (auto& c : pb->cfg) {
+        tile_starts(c, 0, c.Mp, plan.ch, starts);
+        tiles += (long long)starts.size();
+    }
     int sms = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -278,7 +303,8 @@ void build_work(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
     plan.work.clear();
     for (int ci = 0; ci < pb->C; ++ci) {
         const MsdConfig& c = pb->cfg[ci];
-        for (int p0 = 0; p0 < c.Mp; p0 += MSD_TILE_P)
+        tile_starts(c, 0, c.Mp, plan.ch, starts);
+        for (int p0 : starts)
             for (int s = 0; s < ns; ++s) {
                 MatvecWork w;
                 w.cfg = ci;
@@ -353,6 +379,7 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
             CK_LAUNCH();
             CK(cudaEventRecord(e1, pb->stream));
             CK(cudaEventSynchronize(e1));
+            check_tc("autotune");
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (rep > 0) t = std::min(t, (double)ms * nfull / nw);
@@ -437,10 +464,12 @@ RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
     const long long slots = (long long)sms * matvec_blocks_per_sm(rp.ch, pb->Nmax, fp64);
     long long max_units = 1;
     int min_q = 1 << 30;
+    std::vector<int> starts;
     for (auto& g : groups) {
         long long u = 0;
         for (auto& b : g) {
-            u += (long long)(b.Pc / MSD_TILE_P) * (R / rp.ch.RT);
+            tile_starts(pb->cfg[b.cfg], b.P0, b.P0 + b.Pc, rp.ch, starts);
+            u += (long long)starts.size() * (R / rp.ch.RT);
             min_q = std::min(min_q, b.Qb);
         }
         max_units = std::max(max_units, u);
@@ -462,7 +491,8 @@ RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
             ccfg[b.cfg].gen_off = out - ((long long)b.Q0 * b.Pc + b.P0) * c.L;
             items += (long long)b.Qb * b.Pc;
             out += (long long)b.Qb * b.Pc * c.L;
-            for (int p0 = b.P0; p0 < b.P0 + b.Pc; p0 += MSD_TILE_P)
+            tile_starts(c, b.P0, b.P0 + b.Pc, rp.ch, starts);
+            for (int p0 : starts)
                 for (int sp = 0; sp < ns; ++sp) {
                     MatvecWork w;
                     w.cfg = b.cfg;
@@ -953,6 +983,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     std::vector<int> it(S);
     CK(cudaMemcpyAsync(it.data(), cx.iters, S * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    check_tc("msd_solve_planewaves");
     msd_status st = MSD_OK;
     for (int i = 0; i < S; ++i) {
         int flag = relres[i] <= o.tol ? MSD_OK : (stagnated ? MSD_STAGNATED : MSD_NOT_CONVERGED);
@@ -1302,6 +1333,7 @@ msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int
     return guarded([&]() -> msd_status {
         if (!pb) fail(MSD_ERR_ARG, "msd_matvec_timing: bad handle");
         flush_timing(pb);
+        check_tc("msd_matvec_timing");
         if (kernel_ms) *kernel_ms = pb->timed_ms;
         if (launches) *launches = pb->timed_launches;
         if (flops) *flops = pb->timed_flops;

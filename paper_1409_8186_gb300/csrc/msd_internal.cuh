@@ -87,15 +87,24 @@ struct RowChunk {
 
 // Tile shape of one product kernel instance: register window KB (modes per
 // thread), column tile RT and register column block RB, I = ceil(n / KB)
-// thread rows.  matvec_default_choice is the cost model; the autotuner in
+// thread rows; or the tensor-core kernel (TC > 0, FP32, R % TC == 0).  matvec_default_choice is the cost model; the autotuner in
 // the problem's plan times matvec_candidates and keeps the fastest.
 struct MatvecChoice {
     int KB, RT, RB, I;
+    int TC;  // > 0: tensor-core kernel with TC columns per CTA (KB, RB, I unused; RT = TC)
 };
 MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64);
 int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap);
 size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64);
 int matvec_blocks_per_sm(const MatvecChoice& c, int Nmax, bool fp64);
+// tensor-core product (k_matvec_tc.cu): targets in tiles of floor(128 / n)
+// disks that never cross a 32-disk boundary
+bool tc_supported(int R, int Nmax, int RC);
+int tc_tile_disks(int n);
+size_t tc_smem_bytes(int RC);
+void launch_bt_tc(int RC, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, const float2* G,
+                  const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s);
+int tc_status_and_clear();  // bit 0: a pipeline wait of the tensor-core kernel expired
 // the pieces of a product: xs = r .* x; y = x + l .* sum of the partials
 void launch_scale_cols(bool fp64, long long Ntot, int R, const void* rf, const void* x, void* xs, cudaStream_t s);
 void launch_finalize(bool fp64, long long Ntot, int R, int nsplit, const void* lf, const void* x, const void* part,

@@ -112,7 +112,7 @@ def test_generator_mode_switch(msd):
     xd = torch.from_numpy(x).cuda()
     y0 = pb.matvec(xd).cpu().numpy()
     pb.set_generator_mode(msd.MSD_GEN_RECOMPUTE, 40_000)
-    cen = cl.centres + 0.01
+    cen = cl.centres * 1.01  # a dilation changes every b_pq (a translation would not)
     pb.update_geometry(cen, cl.radii, np.array([cl.k]))
     y1 = pb.matvec(xd).cpu().numpy()
     A1 = O_.preconditioned_dense(cen, cl.radii, cl.bc, cl.k, cl.N)

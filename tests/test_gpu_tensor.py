@@ -1,0 +1,99 @@
+"""The tensor-core (tcgen05, 3xTF32) block-Toeplitz product against the oracle.
+
+Shapes: column tiles TC = 16, 32, 64 (R = 64 admits all three); target tiles
+of floor(128 / n) disks restarted at every 32-disk boundary (rand70: n = 25,
+5 disks per tile, ragged at 32, 64 and at M = 70); batched configurations of
+different N; stored and recomputed generators (chunked, accumulating source
+blocks); and an FP32-inner mixed solve running on it.  Tolerance 1e-5
+relative, as for the CUDA-core FP32 product.
+"""
+import numpy as np
+import pytest
+
+import oracle.msd_oracle as O_
+from paper_1409_8186_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def msd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_8186_gb300 import msd as m
+    return m
+
+
+def relerr(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
+
+
+def rand_x(ntot, R, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((ntot, R)) + 1j * rng.standard_normal((ntot, R))).astype(np.complex64)
+
+
+def rand70():
+    return W.random_cluster(seed=8, M=70, half_side=14.0, rmin=0.5, rmax=1.0, gap=0.2, k=2.5, N=12,
+                            neumann_fraction=0.3)
+
+
+@pytest.mark.parametrize("RC", [16, 32, 64])
+def test_tc_product_rand70(msd, RC):
+    cl = rand70()
+    R = 64
+    x = rand_x(cl.ntot, R, seed=RC)
+    ref = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N) @ x.astype(np.complex128)
+    pb = msd.Problem(cl)
+    pb.set_tile(R, msd.MSD_FP32, 0, RC)
+    info, _ = pb.plan_info(R, msd.MSD_FP32)
+    assert info["RT"] == RC and info["KB"] == 0
+    y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
+    assert relerr(y, ref) < 1e-5
+
+
+def test_tc_product_batched_and_recomputed(msd):
+    cls = [W.small_mixed(seed=3, M=6, N=10, k=2.0), rand70(), W.four_disks(),
+           W.random_cluster(seed=9, M=40, half_side=12.0, rmin=0.6, rmax=1.0, gap=0.2, k=3.0, N=20)]
+    R = 16
+    ps = msd.Problem(cls)
+    x = rand_x(ps.ntot, R, seed=4)
+    xd = torch.from_numpy(x).cuda()
+    ps.set_tile(R, msd.MSD_FP32, 0, 16)
+    ys = ps.matvec(xd, msd.MSD_FP32).cpu().numpy()
+    pr = msd.Problem(cls)
+    pr.set_tile(R, msd.MSD_FP32, 0, 16)
+    pr.set_generator_mode(msd.MSD_GEN_RECOMPUTE, 20_000)  # packed and split chunks
+    yr = pr.matvec(xd, msd.MSD_FP32).cpu().numpy()
+    off = 0
+    for cl in cls:
+        A = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N)
+        ref = A @ x[off:off + cl.ntot].astype(np.complex128)
+        assert relerr(ys[off:off + cl.ntot], ref) < 1e-5, cl.name
+        assert relerr(yr[off:off + cl.ntot], ref) < 1e-5, cl.name
+        off += cl.ntot
+
+
+def test_tc_mixed_solve(msd):
+    cl = rand70()
+    betas = W.angles(16)
+    pb = msd.Problem(cl)
+    pb.set_tile(16, msd.MSD_FP32, 0, 16)
+    res = pb.solve(betas, tol=1e-12, precision=msd.MSD_MIXED)
+    assert (res.flags == 0).all(), res.relres
+    rho_ref, _ = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas)
+    assert relerr(res.rho.cpu().numpy(), rho_ref) < 1e-9
+
+
+def test_tc_autotuner_candidates(msd):
+    """R = 32 FP32: the tuner times the CUDA-core shapes and the two
+    tensor-core shapes (TC = 16, 32) and keeps the fastest."""
+    cl = rand70()
+    pb = msd.Problem(cl)
+    info, ms = pb.plan_info(32, msd.MSD_FP32)
+    assert info["candidates"] >= 3 and ms > 0
+    x = rand_x(cl.ntot, 32, seed=1)
+    ref = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N) @ x.astype(np.complex128)
+    y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
+    assert relerr(y, ref) < 1e-5
