@@ -153,9 +153,27 @@ def aggregate(local_ms: float, local_bytes: float, dist, device="cpu"):
 
 def profile_only(what: str):
     """Minimal runs for ncu captures: 'matvec' = three FP64 then three FP32
-    products of the 400-disk operator; 'fp64' / 'mixed' = one solve."""
+    products of the 400-disk operator; 'fp64' / 'mixed' = one solve;
+    'tc' = three tensor-core FP32 products with 64 columns on the first 800
+    sites of the 4000-disk lattice (generators 0.31 GB, above L2);
+    'recompute' = three FP32 products of the same operator with recomputed
+    generators."""
     import torch
     from paper_1409_8186_gb300 import msd, workloads as W
+    if what in ("tc", "recompute"):
+        cl = W.lattice_4000(M=800)
+        pb = msd.Problem(cl)
+        R = 64 if what == "tc" else 1
+        if what == "tc":
+            pb.set_tile(R, msd.MSD_FP32, 0, 64)
+        else:
+            pb.set_generator_mode(msd.MSD_GEN_RECOMPUTE)
+        g = torch.Generator(device="cpu").manual_seed(0)
+        x = torch.randn(cl.ntot, R, dtype=torch.complex128, generator=g).to(torch.complex64).cuda()
+        for _ in range(3):
+            pb.matvec(x, msd.MSD_FP32)
+        torch.cuda.synchronize()
+        return
     cl = W.random_cluster_400()
     pb = msd.Problem(cl)
     if what == "matvec":
@@ -242,7 +260,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed"], default=None,
+    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed", "tc", "recompute"], default=None,
                     help="run a minimal workload for a profiler capture and print no JSON line")
     ap.add_argument("--products", action="store_true",
                     help="print a table (JSON lines) of block-product kernels over the workloads instead")

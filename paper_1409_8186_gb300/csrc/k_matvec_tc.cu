@@ -13,8 +13,9 @@
 //    GEMMs into one FP32 accumulator of 2 RC columns);
 //  * precision: every operand is split into two TF32 parts (x = hi + lo,
 //    hi = tf32(x), lo = tf32(x - hi)) and the products hi*hi + hi*lo + lo*hi
-//    are accumulated ("3xTF32"), which keeps the FP32 accuracy of the
-//    CUDA-core kernel (relative error ~1e-6 of the row sums).
+//    are accumulated ("3xTF32"); each source's sum stays in TMEM only
+//    until it is added to FP32 registers (round-to-nearest), which keeps the
+//    FP32 accuracy of the CUDA-core kernel over thousands of sources.
 //
 // Shared-memory operand layout: K-major without swizzle, 8-row x 16-byte core
 // matrices, 128 bytes between K-adjacent core matrices (LBO), 512 bytes
@@ -47,7 +48,7 @@ struct TcLayout {
     static constexpr int kBBytes = 2 * RC * kKc * 4;
     static constexpr int kStageBytes = 4 * kABytes + 4 * kBBytes;
     static constexpr int kSmem = kTcStages * kStageBytes + 1024;  // + alignment slack
-    static constexpr int kTmemCols = 2 * RC < 32 ? 32 : 2 * RC;    // 32, 64 or 128
+    static constexpr int kTmemCols = 4 * RC;  // two accumulators of 2 RC columns: 64, 128 or 256
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint32_t tmem_sh;
     __shared__ __align__(8) uint64_t mbar[kTcStages];
+    __shared__ __align__(8) uint64_t accbar[2];  // the MMAs of a source into accumulator 0 / 1 are done
 
     const int wi = blockIdx.x / rtiles;
     const int rt = blockIdx.x - wi * rtiles;
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (tid == 0) {
         for (int s = 0; s < kTcStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accbar[s])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -161,19 +164,75 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // B expansion role: column cb, mode quad bq (4 RC items)
     const float2* xq0 = xs + c.row_off * R + col0;
 
+    // Each source is accumulated in TMEM alone (accumulator qi & 1), then
+    // added in FP32 registers with round-to-nearest: the tensor pipe's own
+    // accumulation is not round-to-nearest, and its error over thousands of
+    // sources would exceed the FP32 kernel's.  Register sums: warp -> TMEM
+    // lane quarter (warp & 3) and half of the columns (warp >> 2).
+    constexpr int HC = RC / 2;
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    float sr[HC], si[HC];
+#pragma unroll
+    for (int j = 0; j < HC; ++j) sr[j] = si[j] = 0.f;
+    auto fold = [&](int acc) {
+        float t[HC];
+        const uint32_t a = lane_addr + acc * 2 * RC + half * HC;
+        tmem_ld<HC>(a, t);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < HC; ++j) sr[j] += t[j];
+        tmem_ld<HC>(a + RC, t);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < HC; ++j) si[j] += t[j];
+    };
+
+    // raw values of a stage, loaded one stage ahead into registers so that the
+    // global-memory latency overlaps the expansion and MMAs of the stage before
+    const int bitem = tid < 4 * RC ? tid : -1;  // B item (column cb, mode quad kq); 4 RC <= 256 items
+    const int bcb = bitem % RC, bkq = bitem / RC;
+    auto load_stage = [&](int st_it, float2* ga, float2* xv) {
+        const int sq = w.q0 + st_it / nk;
+        const int sk0 = (st_it % nk) * kKc;
+        const float2* gq = grow + (long long)sq * c.Mp * L;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = sk0 + akh * 8 + j;
+            ga[j] = (arow && k < n) ? __ldg(gq + k) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = sk0 + bkq * 4 + j;
+            xv[j] = (bitem >= 0 && k < n) ? __ldg(xq0 + ((long long)sq * n + k) * R + bcb) : make_float2(0.f, 0.f);
+        }
+    };
+    float2 ga[8], xv[4], gn[8], xn[4];
+
     const int nst = (w.q1 - w.q0) * nk;
+    if (nst > 0) load_stage(0, ga, xv);
     bool ok = true;
     int issued = 0;  // stages whose MMAs were committed
     for (int it = 0; it < nst; ++it) {
         const int b = it % kTcStages;
+        const int qi = it / nk, kc = it - qi * nk;
+        if (it + 1 < nst) load_stage(it + 1, gn, xn);  // in flight during the waits and the expansion
         bool mine = true;  // the MMAs that last read buffer b are done
         if (it >= kTcStages) mine = mbar_wait(smem_u32(&mbar[b]), (uint32_t)((it / kTcStages - 1) & 1));
+        // the accumulator of this source last held source qi - 2: fold it first
+        if (kc == 0 && qi >= 2 && mine) {
+            mine = mbar_wait(smem_u32(&accbar[qi & 1]), (uint32_t)(((qi - 2) >> 1) & 1));
+            if (mine) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                fold(qi & 1);
+                asm volatile("tcgen05.fence::before_thread_sync;");
+            }
+        }
         if (!__syncthreads_and(mine)) {  // uniform decision: no thread leaves the barriers alone
             ok = false;
             break;
         }
-        const int q = w.q0 + it / nk;
-        const int k0 = (it - (it / nk) * nk) * kKc;
+        const int k0 = kc * kKc;
         unsigned char* st = sm + b * Lay::kStageBytes;
         unsigned char* Arh = st;
         unsigned char* Arl = st + kABytes;
@@ -181,42 +240,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned char* Ail = st + 3 * kABytes;
         unsigned char* Bb = st + 4 * kABytes;  // B1h, B1l, B2h, B2l
         // ---- A: Toeplitz rows g_{k-m}, k = k0 + 8 akh + j
-        {
-            const float2* gq = grow + (long long)q * c.Mp * L;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int kq = akh * 2 + h;
-                float re[4], im[4];
+        for (int h = 0; h < 2; ++h) {
+            const int kq = akh * 2 + h;
+            float re[4], im[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int k = k0 + kq * 4 + j;
-                    float2 g = make_float2(0.f, 0.f);
-                    if (arow && k < n) g = __ldg(gq + k);
-                    re[j] = g.x;
-                    im[j] = g.y;
-                }
-                float4 hi, lo;
-                const int off = quad_off(ai, kq);
-                split4(re, hi, lo);
-                *(float4*)(Arh + off) = hi;
-                *(float4*)(Arl + off) = lo;
-                split4(im, hi, lo);
-                *(float4*)(Aih + off) = hi;
-                *(float4*)(Ail + off) = lo;
+            for (int j = 0; j < 4; ++j) {
+                re[j] = ga[h * 4 + j].x;
+                im[j] = ga[h * 4 + j].y;
             }
+            float4 hi, lo;
+            const int off = quad_off(ai, kq);
+            split4(re, hi, lo);
+            *(float4*)(Arh + off) = hi;
+            *(float4*)(Arl + off) = lo;
+            split4(im, hi, lo);
+            *(float4*)(Aih + off) = hi;
+            *(float4*)(Ail + off) = lo;
         }
         // ---- B: [Re X | Im X] and [-Im X | Re X] of source q, modes k0 .. k0+15
-        for (int item = tid; item < 4 * RC; item += kTcThreads) {
-            const int cb = item % RC, kq = item / RC;
+        if (bitem >= 0) {
+            const int cb = bcb, kq = bkq;
             float xr[4], xi[4], nxi[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int k = k0 + kq * 4 + j;
-                float2 v = make_float2(0.f, 0.f);
-                if (k < n) v = __ldg(xq0 + ((long long)q * n + k) * R + cb);
-                xr[j] = v.x;
-                xi[j] = v.y;
-                nxi[j] = -v.y;
+                xr[j] = xv[j].x;
+                xi[j] = xv[j].y;
+                nxi[j] = -xv[j].y;
             }
             float4 hi, lo;
             split4(xr, hi, lo);  // Re X: B1 row cb, B2 row RC + cb
@@ -249,17 +299,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int t = 0; t < 6; ++t) {
                     const uint64_t da = umma_desc(a_addr[t] + ks * 2 * kLbo);
                     const uint64_t db = umma_desc(b_addr[t] + ks * 2 * kLbo);
-                    const uint32_t acc = (it > 0 || ks > 0 || t > 0) ? 1u : 0u;
+                    const uint32_t acc = (kc > 0 || ks > 0 || t > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                            tmem + (uint32_t)((qi & 1) * 2 * RC)),
                         "l"(da), "l"(db), "r"(id), "r"(acc));
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar[b])));
+            if (kc == nk - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&accbar[qi & 1])));
         }
         issued = it + 1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ga[j] = gn[j];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xv[j] = xn[j];
     }
     // wait for the last committed stage (a commit covers all earlier MMAs)
     bool drained = true;
@@ -272,19 +330,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (ok && drained) {
-        // epilogue: warp -> TMEM lane quarter (warp & 3), half of the columns (warp >> 2)
-        constexpr int HC = RC / 2;
-        const int quarter = warp & 3, half = warp >> 2;
-        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-        float vr[HC], vi[HC];
-        if (issued > 0) {
-            tmem_ld<HC>(lane_addr + half * HC, vr);
-            tmem_ld<HC>(lane_addr + RC + half * HC, vi);
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-        } else {
-#pragma unroll
-            for (int j = 0; j < HC; ++j) vr[j] = vi[j] = 0.f;  // empty source range
-        }
+        // fold the last one or two sources (every MMA is complete here)
+        const int nsrc = w.q1 - w.q0;
+        for (int s2 = nsrc >= 2 ? nsrc - 2 : 0; s2 < nsrc; ++s2) fold(s2 & 1);
         const int i = quarter * 32 + lane;
         const int pl = i / n, m = i - pl * n;
         if (pl < np) {
@@ -292,7 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float2* out = part + (long long)w.split * Ntot * R + row * R + col0 + half * HC;
 #pragma unroll
             for (int j = 0; j < HC; ++j) {
-                float2 v = make_float2(vr[j], vi[j]);
+                float2 v = make_float2(sr[j], si[j]);
                 if (w.pad) {
                     const float2 u = out[j];
                     v.x += u.x;

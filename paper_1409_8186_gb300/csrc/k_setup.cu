@@ -107,86 +107,206 @@ void launch_disk_diagonals(const MsdConfig* d_cfg, int Mtot, const int* d_disk_c
 // b_pq = O_p - O_q, e^{i alpha_pq} = b_pq/|b_pq|; for l >= 0:
 // g_l = H_l(k b) e^{i l alpha}, g_{-l} = (-1)^l H_l(k b) e^{-i l alpha}.
 // Padded targets (p >= M) and the diagonal p == q get zeros.
-__global__ void k_pair_generators(const MsdConfig* __restrict__ cfg, const GenBlock* __restrict__ blocks,
-                                  int nblocks, long long nitems, const double2* __restrict__ centre,
-                                  double2* G64, float2* G32, int* flags) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nitems) return;
+//
+// Far pairs (x = k b > 20 and 2N <= x: J and Y both by forward recurrence
+// from Hankel's expansion of orders 0 and 1) are done by their own thread;
+// near pairs (Miller's backward sweep, ~100 FP64 steps) are collected per
+// block and done afterwards by the first threads of the block, so that a
+// warp of far pairs never waits on a near one.  F32: the far pairs of a
+// complex64-only build use FP32 arithmetic after an FP64 phase (sin/cos of
+// x and the unit vector b/|b|); relative error ~1e-6, for products that run
+// in FP32 anyway.
+namespace {
+
+constexpr int kGenThreads = 128;
+
+struct PairRef {
+    GenBlock g;
+    long long li;
+    int q, p;
+};
+
+__device__ __forceinline__ PairRef resolve_pair(const GenBlock* __restrict__ blocks, int nblocks, long long idx) {
     int lo = 0, hi = nblocks - 1;  // last block with item_off <= idx
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (blocks[mid].item_off <= idx) lo = mid;
         else hi = mid - 1;
     }
-    const GenBlock g = blocks[lo];
-    const MsdConfig c = cfg[g.cfg];
-    const long long li = idx - g.item_off;
-    const int q = g.Q0 + (int)(li / g.Pc);
-    const int p = g.P0 + (int)(li % g.Pc);
-    const int N = c.N, L = c.L, lmax = 2 * N;
-    const long long base = g.out_off + li * L;
-    if (p >= c.M || p == q) {
-        for (int l = 0; l < L; ++l) {
-            if (G64) G64[base + l] = make_double2(0.0, 0.0);
-            if (G32) G32[base + l] = make_float2(0.f, 0.f);
-        }
-        return;
+    PairRef r;
+    r.g = blocks[lo];
+    r.li = idx - r.g.item_off;
+    r.q = r.g.Q0 + (int)(r.li / r.g.Pc);
+    r.p = r.g.P0 + (int)(r.li % r.g.Pc);
+    return r;
+}
+
+// Hankel's expansion in FP32 (the FP64 routine's steps), x > 20.
+__device__ inline void bessel_asymptotic_f32(float x, int nu, float sx, float cx, float* Jn, float* Yn) {
+    const float mu = 4.0f * nu * nu;
+    const float z8 = 8.0f * x;
+    float t = 1.0f, P = 1.0f, Q = 0.0f;
+    for (int k = 1; k < 40; ++k) {
+        const float odd = 2.0f * k - 1.0f;
+        const float tn = t * (mu - odd * odd) / (k * z8);
+        if (k > 2 && fabsf(tn) > fabsf(t)) break;
+        t = tn;
+        if (k & 1) Q += (((k - 1) >> 1) & 1) ? -t : t;
+        else P += ((k >> 1) & 1) ? -t : t;
+        if (fabsf(t) < 1e-9f) break;
     }
-    const double2 Op = centre[c.disk_off + p], Oq = centre[c.disk_off + q];
-    const double dx = Op.x - Oq.x, dy = Op.y - Oq.y;
-    const double b = hypot(dx, dy);
-    const double2 e1 = make_double2(dx / b, dy / b);
-    const double x = c.k * b;
-    double2 e = make_double2(1.0, 0.0);  // e^{i l alpha}
-    int bad = 0;
-    auto put = [&](int l, double Jl, double Yl) {
-        const double2 H = make_double2(Jl, Yl);
-        const double2 gp = cmul(H, e);                  // g_l
-        double2 gm = cmul(H, cconj(e));                 // H_l e^{-i l alpha}
-        if (l & 1) gm = make_double2(-gm.x, -gm.y);    // g_{-l} = (-1)^l H_l e^{-i l alpha}
-        if (G64) {
-            G64[base + lmax + l] = gp;
-            G64[base + lmax - l] = gm;
-        }
-        if (G32) {
-            if (!(fabs(gp.x) < 3.0e38 && fabs(gp.y) < 3.0e38)) bad = 1;
-            G32[base + lmax + l] = make_float2((float)gp.x, (float)gp.y);
-            G32[base + lmax - l] = make_float2((float)gm.x, (float)gm.y);
-        }
-        e = cmul(e, e1);
-    };
-    if (x > 20.0 && (double)(lmax < 1 ? 1 : lmax) <= x) {
-        // far pair: J and Y both by forward recurrence from Hankel's
-        // expansion of orders 0 and 1 (the same steps as bessel_jy), on the fly
-        double sx, cx, J0, J1, Y0, Y1;
-        sincos(x, &sx, &cx);
-        bessel_asymptotic(x, 0, sx, cx, &J0, &Y0);
-        bessel_asymptotic(x, 1, sx, cx, &J1, &Y1);
-        put(0, J0, Y0);
-        for (int l = 1; l <= lmax; ++l) {
-            put(l, J1, Y1);
-            const double f = 2.0 * l / x;
-            const double J2 = f * J1 - J0, Y2 = f * Y1 - Y0;
-            J0 = J1;
-            J1 = J2;
-            Y0 = Y1;
-            Y1 = Y2;
-        }
+    const float r2 = 0.70710678f;
+    float cc, ss;
+    if (nu == 0) {
+        cc = (cx + sx) * r2;
+        ss = (sx - cx) * r2;
     } else {
+        cc = (sx - cx) * r2;
+        ss = -(sx + cx) * r2;
+    }
+    const float amp = sqrtf(2.0f / (3.14159265f * x));
+    *Jn = amp * (P * cc - Q * ss);
+    *Yn = amp * (P * ss + Q * cc);
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kGenThreads)
+    k_pair_generators(const MsdConfig* __restrict__ cfg, const GenBlock* __restrict__ blocks, int nblocks,
+                      long long nitems, const double2* __restrict__ centre, double2* G64, float2* G32, int* flags) {
+    __shared__ int near_list[kGenThreads];
+    __shared__ int n_near;
+    if (threadIdx.x == 0) n_near = 0;
+    __syncthreads();
+    int bad = 0;
+    const long long idx = (long long)blockIdx.x * kGenThreads + threadIdx.x;
+    if (idx < nitems) {
+        const PairRef r = resolve_pair(blocks, nblocks, idx);
+        const MsdConfig c = cfg[r.g.cfg];
+        const int L = c.L, lmax = 2 * c.N;
+        const long long base = r.g.out_off + r.li * L;
+        if (r.p >= c.M || r.p == r.q) {
+            for (int l = 0; l < L; ++l) {
+                if (G64) G64[base + l] = make_double2(0.0, 0.0);
+                if (G32) G32[base + l] = make_float2(0.f, 0.f);
+            }
+        } else {
+            const double2 Op = centre[c.disk_off + r.p], Oq = centre[c.disk_off + r.q];
+            const double dx = Op.x - Oq.x, dy = Op.y - Oq.y;
+            const double b = hypot(dx, dy);
+            const double x = c.k * b;
+            if (!(x > 20.0 && (double)lmax <= x)) {
+                near_list[atomicAdd(&n_near, 1)] = threadIdx.x;
+            } else if (F32) {
+                double sxd, cxd;
+                sincos(x, &sxd, &cxd);
+                const float xf = (float)x;
+                float J0, J1, Y0, Y1;
+                bessel_asymptotic_f32(xf, 0, (float)sxd, (float)cxd, &J0, &Y0);
+                bessel_asymptotic_f32(xf, 1, (float)sxd, (float)cxd, &J1, &Y1);
+                const float2 e1 = make_float2((float)(dx / b), (float)(dy / b));
+                const float two_x = 2.0f / xf;
+                float2 e = make_float2(1.f, 0.f);
+                auto put = [&](int l, float Jl, float Yl) {
+                    const float2 gp = make_float2(Jl * e.x - Yl * e.y, Jl * e.y + Yl * e.x);
+                    float2 gm = make_float2(Jl * e.x + Yl * e.y, Yl * e.x - Jl * e.y);
+                    if (l & 1) gm = make_float2(-gm.x, -gm.y);
+                    G32[base + lmax + l] = gp;
+                    G32[base + lmax - l] = gm;
+                    e = make_float2(e.x * e1.x - e.y * e1.y, e.x * e1.y + e.y * e1.x);
+                };
+                put(0, J0, Y0);
+                for (int l = 1; l <= lmax; ++l) {
+                    put(l, J1, Y1);
+                    const float f = l * two_x;
+                    const float J2 = f * J1 - J0, Y2 = f * Y1 - Y0;
+                    J0 = J1;
+                    J1 = J2;
+                    Y0 = Y1;
+                    Y1 = Y2;
+                }
+            } else {
+                const double2 e1 = make_double2(dx / b, dy / b);
+                double2 e = make_double2(1.0, 0.0);  // e^{i l alpha}
+                auto put = [&](int l, double Jl, double Yl) {
+                    const double2 H = make_double2(Jl, Yl);
+                    const double2 gp = cmul(H, e);                  // g_l
+                    double2 gm = cmul(H, cconj(e));                 // H_l e^{-i l alpha}
+                    if (l & 1) gm = make_double2(-gm.x, -gm.y);    // g_{-l} = (-1)^l H_l e^{-i l alpha}
+                    if (G64) {
+                        G64[base + lmax + l] = gp;
+                        G64[base + lmax - l] = gm;
+                    }
+                    if (G32) {
+                        G32[base + lmax + l] = make_float2((float)gp.x, (float)gp.y);
+                        G32[base + lmax - l] = make_float2((float)gm.x, (float)gm.y);
+                    }
+                    e = cmul(e, e1);
+                };
+                double sx, cx, J0, J1, Y0, Y1;
+                sincos(x, &sx, &cx);
+                bessel_asymptotic(x, 0, sx, cx, &J0, &Y0);
+                bessel_asymptotic(x, 1, sx, cx, &J1, &Y1);
+                put(0, J0, Y0);
+                for (int l = 1; l <= lmax; ++l) {
+                    put(l, J1, Y1);
+                    const double f = 2.0 * l / x;
+                    const double J2 = f * J1 - J0, Y2 = f * Y1 - Y0;
+                    J0 = J1;
+                    J1 = J2;
+                    Y0 = Y1;
+                    Y1 = Y2;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // the near pairs of this block, one per thread, in FP64 (Miller's sweep)
+    if ((int)threadIdx.x < n_near) {
+        const long long nidx = (long long)blockIdx.x * kGenThreads + near_list[threadIdx.x];
+        const PairRef r = resolve_pair(blocks, nblocks, nidx);
+        const MsdConfig c = cfg[r.g.cfg];
+        const int L = c.L, lmax = 2 * c.N;
+        const long long base = r.g.out_off + r.li * L;
+        const double2 Op = centre[c.disk_off + r.p], Oq = centre[c.disk_off + r.q];
+        const double dx = Op.x - Oq.x, dy = Op.y - Oq.y;
+        const double b = hypot(dx, dy);
+        const double2 e1 = make_double2(dx / b, dy / b);
         double J[MAXL], Y[MAXL];
-        bessel_jy(x, lmax, J, Y);
-        for (int l = 0; l <= lmax; ++l) put(l, J[l], Y[l]);
+        bessel_jy(c.k * b, lmax, J, Y);
+        double2 e = make_double2(1.0, 0.0);
+        for (int l = 0; l <= lmax; ++l) {
+            const double2 H = make_double2(J[l], Y[l]);
+            const double2 gp = cmul(H, e);
+            double2 gm = cmul(H, cconj(e));
+            if (l & 1) gm = make_double2(-gm.x, -gm.y);
+            if (G64) {
+                G64[base + lmax + l] = gp;
+                G64[base + lmax - l] = gm;
+            }
+            if (G32) {
+                if (!(fabs(gp.x) < 3.0e38 && fabs(gp.y) < 3.0e38)) bad = 1;
+                G32[base + lmax + l] = make_float2((float)gp.x, (float)gp.y);
+                G32[base + lmax - l] = make_float2((float)gm.x, (float)gm.y);
+            }
+            e = cmul(e, e1);
+        }
     }
     if (bad) atomicOr(flags, FLAG_RANGE32);
 }
 
+}  // namespace
+
 void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, int nblocks, long long nitems,
-                             const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s) {
+                             const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s,
+                             bool f32_math) {
     if (nitems <= 0) return;
-    const int threads = 128;
-    const long long blocks = (nitems + threads - 1) / threads;
-    k_pair_generators<<<(unsigned)blocks, threads, 0, s>>>(d_cfg, d_blocks, nblocks, nitems, d_centre, G64, G32,
-                                                            d_flags);
+    const long long blocks = (nitems + kGenThreads - 1) / kGenThreads;
+    if (f32_math && !G64 && G32)
+        k_pair_generators<true><<<(unsigned)blocks, kGenThreads, 0, s>>>(d_cfg, d_blocks, nblocks, nitems, d_centre,
+                                                                         G64, G32, d_flags);
+    else
+        k_pair_generators<false><<<(unsigned)blocks, kGenThreads, 0, s>>>(d_cfg, d_blocks, nblocks, nitems,
+                                                                          d_centre, G64, G32, d_flags);
     g_msd_launches += 1;
 }
 

@@ -536,7 +536,7 @@ void matvec_recompute_dev(msd_problem* pb, int R, bool fp64, const void* x, void
         CK(cudaMemsetAsync(pb->d_flags, 0, sizeof(int), pb->stream));
         for (auto& ch : rp.chunks)
             launch_generator_blocks(pb->d_cfg, ch.d_blocks, ch.nblocks, ch.nitems, pb->d_centre, nullptr,
-                                    (float2*)gbuf, pb->d_flags, pb->stream);
+                                    (float2*)gbuf, pb->d_flags, pb->stream, true);
         CK_LAUNCH();
         check_flags(pb, "recomputed generators");
         pb->rc_checked = pb->geom_version;
@@ -562,7 +562,7 @@ void matvec_recompute_dev(msd_problem* pb, int R, bool fp64, const void* x, void
     for (auto& ch : rp.chunks) {
         launch_generator_blocks(pb->d_cfg, ch.d_blocks, ch.nblocks, ch.nitems, pb->d_centre,
                                 fp64 ? (double2*)gbuf : nullptr, fp64 ? nullptr : (float2*)gbuf, pb->d_flags,
-                                pb->stream);
+                                pb->stream, !fp64);
         launch_bt_only(rp.ch, fp64, ch.d_cfg, ch.d_work, ch.nwork, pb->Nmax, gbuf, xs, part, pb->Ntot, R,
                        pb->stream);
     }

@@ -134,8 +134,10 @@ struct GenBlock {
     int cfg, P0, Pc, Q0, Qb, pad;
     long long item_off, out_off;
 };
+// f32_math: complex64-only output with FP32 arithmetic for the far pairs
 void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, int nblocks, long long nitems,
-                             const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s);
+                             const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s,
+                             bool f32_math = false);
 
 // K5: preconditioned plane-wave right-hand sides.
 void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
