@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "block-matvec GB/s (% HBM peak) & solve time at relres 1e-10, FP64 vs mixed"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
+TF32_OVER_BF16 = 1.1 / 2.25                    # nominal dense TF32 / bf16 tensor rate
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
 # product kernel (window length 7) on this workload, from an ncu capture
 # (216.42 MB read + 5.75 MB written); the algorithmic stream is 207.7 MB
@@ -202,6 +204,9 @@ def products_table(reps: int = 3):
     import torch
     from paper_1409_8186_gb300 import msd, workloads as W
     F64, F32 = msd.MSD_FP64, msd.MSD_FP32
+    peaks = measured_peaks() or {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_OVER_BF16  # measured bf16 x nominal ratio
     cases = [
         ("random400 (M=400, N=20)", W.random_cluster_400, [(F64, 1), (F32, 1)], False),
         ("random200_k10 (M=200, N=22)", W.cluster_200, [(F64, 16), (F32, 16)], False),
@@ -241,12 +246,20 @@ def products_table(reps: int = 3):
                     kms /= max(nl, 1)
                     fl /= max(nl, 1)
                     by /= max(nl, 1)
+                    tf = fl / (kms * 1e-3) / 1e12
+                    gbs = by / (kms * 1e-3) / 1e9
+                    if prec == F64:
+                        bound, peak = "fp64 alu", FP64_PEAK_TFLOPS
+                    elif info["KB"] == 0:  # tensor cores: 3 TF32 products per real multiply-add
+                        bound, peak = "tf32 tensor (3x executed)", tf32_peak / 3.0
+                    else:
+                        bound, peak = "fp32 alu", FP32_PEAK_TFLOPS
                     print(json.dumps({
                         "workload": name, "R": R, "precision": "fp64" if prec == F64 else "fp32",
                         "kernel": kind, "shape": info, "generators": gen,
                         "kernel_ms": round(kms, 4), "product_ms": round(prod_ms, 4),
-                        "tflops": round(fl / (kms * 1e-3) / 1e12, 2),
-                        "gbs": round(by / (kms * 1e-3) / 1e9, 1)}), flush=True)
+                        "tflops": round(tf, 2), "bound": bound, "peak_frac": round(tf / peak, 3),
+                        "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}), flush=True)
                     pb.close()
                     del pb, x, y
                     torch.cuda.empty_cache()

@@ -32,17 +32,12 @@ constexpr int kU = 16;   // basis vectors per update block
 
 template <typename V> __device__ __forceinline__ double2 to_d2(V v) { return make_double2(v.x, v.y); }
 
-// Column lanes RC = min(R, 32); row lanes RY = largest power of two with RY * RC <= threads.
-// (a power of two, so that lanes of one column are xor-shuffle partners)
+// Column lanes RC = the smallest power of two >= min(R, 32), so that lanes
+// of one column are xor-shuffle partners.
 __host__ __device__ inline int col_lanes(int R) {
     int c = 1;
     while (c < R && c < 32) c *= 2;
     return c;
-}
-__device__ inline int row_lanes(int RC) {
-    int RY = 1;
-    while (RY * 2 * RC <= (int)blockDim.x) RY *= 2;
-    return RY;
 }
 
 __device__ __forceinline__ void atomic_add_v(double2* p, double2 v) {
@@ -119,6 +114,71 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
             s.y += red[wv][cl][ii].y;
         }
         part[((long long)blockIdx.x * nvv + (i0 + ii)) * R + rr] = s;
+    }
+}
+
+// The same partial sums with one warp per vector i over the chunk's flat
+// elements e = row * R + r (R divides 32, or R = 64): lane l reads elements
+// e0 + l + 32 k, eight loads in flight, so a warp streams one contiguous
+// stretch of its vector and of w.  The column of element e is e mod R, fixed
+// per lane (Q = 1) or alternating between two columns (Q = 2, R = 64); lanes
+// that hold the same column are folded by shuffles.  No block-level
+// reduction: blocks are independent groups of eight vectors.
+template <typename V, int Q>
+__global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restrict__ chunks, int R,
+                                                        const V* __restrict__ Vb, long long vstride, int nv,
+                                                        int self, const V* __restrict__ w,
+                                                        const int* __restrict__ skip, double2* __restrict__ part) {
+    const RowChunk ch = chunks[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.y * (kThreads / 32) + warp;
+    const int nvv = nv + self;
+    if (i >= nvv) return;  // a whole warp
+    const V* u = i < nv ? Vb + (long long)i * vstride : w;
+    const long long e0 = ch.row0 * R, e1 = ch.row1 * R;
+    typedef decltype(V{}.x) A;
+    A ax[Q], ay[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) ax[q] = ay[q] = A(0);
+    constexpr int U = 8;  // a multiple of Q: the column phase of k survives the stride
+    long long e = e0 + lane;
+    for (; e + 32LL * (U - 1) < e1; e += 32LL * U) {
+        V uv[U], wv[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            uv[k] = u[e + 32LL * k];
+            wv[k] = w[e + 32LL * k];
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int q = k % Q;
+            ax[q] = fma(uv[k].x, wv[k].x, fma(uv[k].y, wv[k].y, ax[q]));  // conj(u) * w
+            ay[q] = fma(uv[k].x, wv[k].y, fma(-uv[k].y, wv[k].x, ay[q]));
+        }
+    }
+    for (int k = 0; e < e1; e += 32, ++k) {
+        const V uv = u[e], wv = w[e];
+        if (Q == 2 && (k & 1)) {
+            ax[Q - 1] = fma(uv.x, wv.x, fma(uv.y, wv.y, ax[Q - 1]));
+            ay[Q - 1] = fma(uv.x, wv.y, fma(-uv.y, wv.x, ay[Q - 1]));
+        } else {
+            ax[0] = fma(uv.x, wv.x, fma(uv.y, wv.y, ax[0]));
+            ay[0] = fma(uv.x, wv.y, fma(-uv.y, wv.x, ay[0]));
+        }
+    }
+    if (Q == 1) {
+        for (int off = 16; off >= R; off >>= 1) {
+            ax[0] += __shfl_xor_sync(0xffffffffu, ax[0], off);
+            ay[0] += __shfl_xor_sync(0xffffffffu, ay[0], off);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (Q == 1 && lane >= R) break;
+        const int r = (int)((e0 + lane + 32 * q) % R);
+        const bool sk = skip && skip[ch.cfg * R + r];
+        part[((long long)blockIdx.x * nvv + i) * R + r] =
+            sk ? make_double2(0.0, 0.0) : make_double2((double)ax[q], (double)ay[q]);
     }
 }
 
@@ -228,15 +288,30 @@ __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* _
     }
 }
 
-// Selective re-orthogonalisation flags: need[s] = 1 for an active system
-// whose first projection left ||w'||^2 < ||w||^2 / 2.
+// Selective re-orthogonalisation flags, one CTA per system: ||w'||^2 after
+// the first projection is ||w||^2 - sum_i |h_i|^2 (Pythagoras, V orthonormal);
+// need[s] = 1 for an active system where that is below ||w||^2 / 2.  The
+// estimate is written to wn2 (the subdiagonal when no second pass runs);
+// where cancellation makes it inaccurate the second pass runs and measures
+// the norm itself.
 __global__ void k_reorth_flags(int S, const double2* __restrict__ h1, int hstride, int j,
-                               const double2* __restrict__ wn2, const int* __restrict__ active,
+                               double2* __restrict__ wn2, const int* __restrict__ active,
                                int* __restrict__ skip2) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    const double before = h1[(long long)s * hstride + j + 1].x;  // ||w||^2 before the projection
-    const double after = wn2[(long long)s * hstride].x;
+    const int s = blockIdx.x;
+    const double2* h = h1 + (long long)s * hstride;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) acc += cabs2(h[i]);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ double part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double ss = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) ss += part[k];
+    const double before = h[j + 1].x;  // ||w||^2 before the projection
+    const double after = before - ss;
+    wn2[(long long)s * hstride] = make_double2(after, 0.0);
     skip2[s] = !(active[s] && after < 0.5 * before);
 }
 
@@ -267,10 +342,47 @@ struct Aff {
 __device__ __forceinline__ Aff compose(const Aff& second, const Aff& first) {
     return Aff{cmul(second.A, first.A), cadd(cmul(second.A, first.B), second.B)};
 }
+// the same maps in FP32 (z_j of the FP32 inner sweeps of a mixed solve)
+struct AffF {
+    float2 A, B;
+};
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ AffF compose(const AffF& second, const AffF& first) {
+    const float2 ab = cmulf(second.A, first.B);
+    return AffF{cmulf(second.A, first.A), make_float2(ab.x + second.B.x, ab.y + second.B.y)};
+}
+template <typename M> struct AffOps;
+template <> struct AffOps<Aff> {
+    __device__ static Aff id() { return Aff{make_double2(1.0, 0.0), make_double2(0.0, 0.0)}; }
+    __device__ static Aff step(double2 c, double2 sv, double2 hn1) {
+        return Aff{cscale(cconj(sv), -1.0), cscale(hn1, c.x)};
+    }
+    __device__ static double2 apply(const Aff& f, double2 z) { return cadd(cmul(f.A, z), f.B); }
+};
+template <> struct AffOps<AffF> {
+    __device__ static AffF id() { return AffF{make_float2(1.f, 0.f), make_float2(0.f, 0.f)}; }
+    __device__ static AffF step(double2 c, double2 sv, double2 hn1) {
+        return AffF{make_float2((float)-sv.x, (float)sv.y), make_float2((float)(hn1.x * c.x), (float)(hn1.y * c.x))};
+    }
+    __device__ static double2 apply(const AffF& f, double2 z) {
+        const float2 r = cmulf(f.A, make_float2((float)z.x, (float)z.y));
+        return make_double2((double)r.x + f.B.x, (double)r.y + f.B.y);
+    }
+};
 
 // Arnoldi step j for one system per CTA: column h = h1 + h2 (h2 only where
-// the second projection ran), h[j+1] = ||w||, previous rotations by scan,
-// new rotation, g, convergence state.
+// the second projection ran), h[j+1] = ||w||.  The step needs only the last
+// entry z_j of the rotated column (for the new rotation and the residual
+// estimate): z_j = A_{j-1}(...A_0(h_0)) with A_i(z) = c_i h_{i+1} -
+// conj(s_i) z, an ordered reduction of affine maps over the CTA, in FP64
+// (Map = Aff) or, for the FP32 inner sweeps of a mixed solve, in FP32 (Map =
+// AffF: a warp-wide FP64 instruction costs ~64 cycles of an SM sub-partition
+// on this GPU, and the chain made the step ~20 us).  The rotation itself is
+// formed in FP64.  The raw column is stored; k_apply_rotations rotates all
+// columns at the end of the cycle in FP64, in parallel across columns.
+template <typename Map>
 __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2* __restrict__ h1,
                                                      const double2* __restrict__ h2, int hstride,
                                                      const double2* __restrict__ wn2a,
@@ -281,11 +393,11 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
                                                      double2* __restrict__ sn, double2* __restrict__ g,
                                                      double* __restrict__ vscale, int* __restrict__ active,
                                                      int* __restrict__ kconv, int* __restrict__ iters,
-                                                     int* __restrict__ any_active, int* __restrict__ nonfinite) {
+                                                     int* __restrict__ any_active, int* __restrict__ nonfinite,
+                                                     double2* __restrict__ rdiag) {
     const int s = blockIdx.x;
     if (!active[s]) return;
-    __shared__ Aff pre[kThreads];
-    __shared__ double2 zj_sh;
+    __shared__ Map red[kThreads];
     const int tid = threadIdx.x, T = blockDim.x;
     const bool second = !skip2[s];
     const double2* a = h1 + (long long)s * hstride;
@@ -298,42 +410,21 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
         if (second) v = cadd(v, b[i]);
         return v;
     };
+    for (int i = tid; i <= j; i += T) Hc[i] = hval(i);  // raw column
     // segment of rotations [lo, hi) owned by this thread
     const int per = (j + T - 1) / T;
     const int lo = min(j, tid * per), hi = min(j, lo + per);
-    Aff seg{make_double2(1.0, 0.0), make_double2(0.0, 0.0)};
-    for (int i = lo; i < hi; ++i) {
-        const Aff st{cscale(cconj(snj[i]), -1.0), cscale(hval(i + 1), csj[i].x)};
-        seg = compose(st, seg);
-    }
-    pre[tid] = seg;
+    Map seg = AffOps<Map>::id();
+    for (int i = lo; i < hi; ++i) seg = compose(AffOps<Map>::step(csj[i], snj[i], hval(i + 1)), seg);
+    red[tid] = seg;
     __syncthreads();
-    // inclusive Hillis-Steele scan of the segment maps in thread order
+    // ordered tree: later segments compose onto earlier ones
     for (int off = 1; off < T; off *= 2) {
-        Aff v = pre[tid];
-        if (tid >= off) v = compose(v, pre[tid - off]);
-        __syncthreads();
-        pre[tid] = v;
+        if ((tid & (2 * off - 1)) == 0 && tid + off < T) red[tid] = compose(red[tid + off], red[tid]);
         __syncthreads();
     }
-    const double2 z0 = hval(0);
-    double2 z = z0;
-    if (tid > 0) {
-        const Aff p = pre[tid - 1];
-        z = cadd(cmul(p.A, z0), p.B);
-    }
-    for (int i = lo; i < hi; ++i) {
-        const double2 c = csj[i], sv = snj[i], hn1 = hval(i + 1);
-        Hc[i] = cadd(cscale(z, c.x), cmul(sv, hn1));
-        z = csub(cscale(hn1, c.x), cmul(cconj(sv), z));
-    }
-    if (hi == j && lo <= j && (lo < hi || tid == 0)) {
-        // the thread owning the last rotation (or thread 0 when j == 0)
-        if (lo < hi || j == 0) zj_sh = z;
-    }
-    __syncthreads();
     if (tid != 0) return;
-    const double2 hjj = zj_sh;
+    const double2 hjj = AffOps<Map>::apply(red[0], hval(0));
     const double wn = second ? wn2b[(long long)s * hstride].x : wn2a[(long long)s * hstride].x;
     const double hn = sqrt(fmax(wn, 0.0));
     const double ajj = sqrt(cabs2(hjj));
@@ -353,8 +444,7 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
     cs[(long long)s * m + j] = c;
     sn[(long long)s * m + j] = sv;
     const double2 rjj = cadd(cscale(hjj, c.x), cscale(sv, hn));
-    Hc[j] = rjj;
-    Hc[j + 1] = make_double2(0.0, 0.0);
+    rdiag[(long long)s * m + j] = make_double2(hn, 0.0);  // R_jj is formed in FP64 at the end of the cycle
     double2* gs = g + (long long)s * (m + 1);
     const double2 gj = gs[j];
     gs[j + 1] = cscale(cmul(cconj(sv), gj), -1.0);
@@ -371,6 +461,30 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
         vscale[s] = 1.0 / hn;
         atomicOr(any_active, 1);
     }
+}
+
+// End of a cycle: rotate every stored column j < kconv (raw h_0..h_j) by the
+// rotations 0..j-1 into the triangle R, in FP64, and form R_jj from the
+// rotated z_j with rotation j and the stored subdiagonal ||w_j||; one thread
+// per column, all columns and systems in parallel.
+__global__ void k_apply_rotations(int m, double2* __restrict__ H, const double2* __restrict__ cs,
+                                  const double2* __restrict__ sn, const double2* __restrict__ rdiag,
+                                  const int* __restrict__ kconv) {
+    const int s = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kconv[s]) return;
+    double2* Hc = H + ((long long)s * m + j) * (m + 1);
+    const double2* csj = cs + (long long)s * m;
+    const double2* snj = sn + (long long)s * m;
+    double2 z = Hc[0];
+    for (int i = 0; i < j; ++i) {
+        const double2 c = csj[i], sv = snj[i], hn1 = Hc[i + 1];
+        Hc[i] = cadd(cscale(z, c.x), cmul(sv, hn1));
+        z = csub(cscale(hn1, c.x), cmul(cconj(sv), z));
+    }
+    // R_jj = c_j z_j + s_j ||w_j|| (the subdiagonal entry, real)
+    Hc[j] = cadd(cscale(z, csj[j].x), cscale(snj[j], rdiag[(long long)s * m + j].x));
+    Hc[j + 1] = make_double2(0.0, 0.0);
 }
 
 // Back substitution H y = g on the leading kconv x kconv triangle, one CTA
@@ -428,8 +542,17 @@ void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
              int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
              cudaStream_t s) {
     const int nvv = nv + self;
-    dim3 g(d.nchunk, rgroups(d.R), (nvv + kI - 1) / kI);
-    k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, part);
+    constexpr int WPB = kThreads / 32;
+    if (32 % d.R == 0) {
+        k_dots_warp<V, 1><<<dim3(d.nchunk, (nvv + WPB - 1) / WPB), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv,
+                                                                                    self, w, skip, part);
+    } else if (d.R == 64) {
+        k_dots_warp<V, 2><<<dim3(d.nchunk, (nvv + WPB - 1) / WPB), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv,
+                                                                                    self, w, skip, part);
+    } else {
+        dim3 g(d.nchunk, rgroups(d.R), (nvv + kI - 1) / kI);
+        k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, part);
+    }
     const long long tot = (long long)d.S * nvv;
     k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
     g_msd_launches += 2;
@@ -451,9 +574,9 @@ void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const do
     g_msd_launches += 1;
 }
 
-void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, const double2* wn2,
+void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, double2* wn2,
                      const int* active, int* skip2, cudaStream_t s) {
-    k_reorth_flags<<<blocks_for(d.S, 128), 128, 0, s>>>(d.S, h1, hstride, j, wn2, active, skip2);
+    k_reorth_flags<<<d.S, 128, 0, s>>>(d.S, h1, hstride, j, wn2, active, skip2);
     g_msd_launches += 1;
 }
 
@@ -467,16 +590,21 @@ void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* 
 void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride, const double2* wn2a,
                const double2* wn2b, const int* skip2, const double* tol_cycle, double2* H, double2* cs,
                double2* sn, double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
-               int* nonfinite, cudaStream_t s) {
-    k_givens<<<d.S, kThreads, 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H, cs, sn, g, vscale,
-                                      active, kconv, iters, any_active, nonfinite);
+               int* nonfinite, double2* rdiag, bool fp32_maps, cudaStream_t s) {
+    if (fp32_maps)
+        k_givens<AffF><<<d.S, kThreads, 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H, cs, sn, g,
+                                                vscale, active, kconv, iters, any_active, nonfinite, rdiag);
+    else
+        k_givens<Aff><<<d.S, kThreads, 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H, cs, sn, g,
+                                               vscale, active, kconv, iters, any_active, nonfinite, rdiag);
     g_msd_launches += 1;
 }
 
-void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y, double2* work,
-            cudaStream_t s) {
+void gm_lsq(const GmresDims& d, double2* H, const double2* cs, const double2* sn, const double2* rdiag,
+            const double2* g, const int* kconv, double2* y, double2* work, cudaStream_t s) {
+    k_apply_rotations<<<dim3(blocks_for(d.m, 128), d.S), 128, 0, s>>>(d.m, H, cs, sn, rdiag, kconv);
     k_lsq<<<d.S, kThreads, 0, s>>>(d.m, H, g, kconv, y, work);
-    g_msd_launches += 1;
+    g_msd_launches += 2;
 }
 
 void gm_residual(long long n, const double2* b, const double2* Ax, double2* r, cudaStream_t s) {

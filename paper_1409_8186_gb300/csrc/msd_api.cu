@@ -116,6 +116,7 @@ struct MatvecPlan {
     MatvecWork* d_work = nullptr;
     int nsplit = 1;
     MatvecChoice ch{0, 1, 1, 0};  // tile shape of the product kernel
+    int ns_div = 1;               // split count = the wave model's / ns_div
     int candidates = 0;           // shapes the autotuner timed (0: model choice)
     double tuned_ms = 0;          // kernel time of the chosen shape in the tuning run
 };
@@ -180,6 +181,11 @@ struct msd_problem {
     std::vector<RowChunk> chunks;
     RowChunk* d_chunks = nullptr;
     int* d_cfg_chunk_off = nullptr;
+    // coarse reduction chunks (>= 4096 rows): projections onto many basis
+    // vectors give each thread enough rows to amortise its reductions
+    std::vector<RowChunk> chunks_coarse;
+    RowChunk* d_chunks_coarse = nullptr;
+    int* d_cfg_chunk_off_coarse = nullptr;
     int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags
     cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf xs, part, sbuf[24];
@@ -299,6 +305,7 @@ void build_work(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
             ns = t;
         }
     }
+    ns = std::max(1, ns / plan.ns_div);
     plan.nsplit = ns;
     plan.work.clear();
     for (int ci = 0; ci < pb->C; ++ci) {
@@ -329,10 +336,15 @@ bool autotune_enabled() {
 }
 
 typedef std::tuple<int, int, int, int, long long, int, int> TuneKey;  // Nmax R fp64 C Ntot Mmax device
+struct TuneResult {
+    MatvecChoice ch;
+    int ns_div;
+    double ms;
+};
 
 void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
     static std::mutex mu;
-    static std::map<TuneKey, std::pair<MatvecChoice, double>> cache;
+    static std::map<TuneKey, TuneResult> cache;
     int dev = 0;
     CK(cudaGetDevice(&dev));
     const TuneKey key{pb->Nmax, R, fp64 ? 1 : 0, pb->C, pb->Ntot, pb->Mmax, dev};
@@ -342,8 +354,9 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            plan.ch = it->second.first;
-            plan.tuned_ms = it->second.second;
+            plan.ch = it->second.ch;
+            plan.ns_div = it->second.ns_div;
+            plan.tuned_ms = it->second.ms;
             plan.candidates = nc;
             return;
         }
@@ -363,10 +376,18 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
     DBuf dwork;
     double best_ms = 1e300;
     MatvecChoice best = plan.ch;
-    for (int i = 0; i < nc; ++i) {
+    int best_div = 1;
+    // every shape at the wave model's split count and at a quarter of it
+    // (fewer, longer source ranges: less partial-sum traffic and per-CTA
+    // set-up, at some cost in wave fill)
+    int model_ns = 1;
+    for (int i = 0; i < 2 * nc; ++i) {
+        if ((i & 1) && model_ns == 1) continue;  // a quarter of one split is the same plan
         MatvecPlan trial;
-        trial.ch = cand[i];
+        trial.ch = cand[i / 2];
+        trial.ns_div = (i & 1) ? 4 : 1;
         build_work(pb, trial, R, fp64);
+        if (!(i & 1)) model_ns = trial.nsplit;
         const int nfull = (int)trial.work.size();
         const int nw = std::max(1, std::min(nfull, (int)std::ceil(frac * nfull)));
         MatvecWork* dw = (MatvecWork*)dwork.get(nfull * sizeof(MatvecWork));
@@ -375,7 +396,7 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
         double t = 1e300;
         for (int rep = 0; rep < 3; ++rep) {  // first run warms caches and the module
             CK(cudaEventRecord(e0, pb->stream));
-            launch_bt_only(cand[i], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
+            launch_bt_only(cand[i / 2], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
             CK_LAUNCH();
             CK(cudaEventRecord(e1, pb->stream));
             CK(cudaEventSynchronize(e1));
@@ -386,17 +407,19 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
         }
         if (t < best_ms) {
             best_ms = t;
-            best = cand[i];
+            best = cand[i / 2];
+            best_div = trial.ns_div;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     dwork.release();
     plan.ch = best;
+    plan.ns_div = best_div;
     plan.tuned_ms = best_ms;
     plan.candidates = nc;
     std::lock_guard<std::mutex> lk(mu);
-    cache[key] = {best, best_ms};
+    cache[key] = TuneResult{best, best_div, best_ms};
 }
 
 MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
@@ -421,13 +444,9 @@ MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
 // into blocks of Qb >= 32 sources by Pc targets (multiples of 32), one
 // chunk each.  Work items split each block's sources into ns ranges; the
 // items of blocks with Q0 > 0 add to the partial sums (pad = 1).
-RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
-    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
-    auto it = pb->rplans.find(key);
-    if (it != pb->rplans.end()) return it->second;
+RecomputePlan build_recompute_plan(msd_problem* pb, int R, bool fp64, const MatvecChoice& choice) {
     RecomputePlan rp;
-    auto pin = pb->pinned.find(key);
-    rp.ch = pin != pb->pinned.end() ? pin->second : matvec_default_choice(R, pb->Nmax, fp64);
+    rp.ch = choice;
     const size_t elem = fp64 ? 16 : 8;
     const long long budget = std::max<long long>(1, (long long)(pb->gen_chunk_bytes / (elem * (4 * pb->Nmax + 1))));
     // blocks grouped into chunks
@@ -513,16 +532,79 @@ RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
         rp.buf_elems = std::max(rp.buf_elems, (size_t)out);
         rp.chunks.push_back(ch);
     }
+    return rp;
+}
+
+void free_recompute_plan(RecomputePlan& rp) {
+    for (auto& ch : rp.chunks) {
+        cudaFree(ch.d_cfg);
+        cudaFree(ch.d_blocks);
+        cudaFree(ch.d_work);
+    }
+    rp.chunks.clear();
+}
+
+// Time the product kernel of a recompute plan on its first chunk (whose
+// generators are evaluated once beforehand).
+double time_first_chunk(msd_problem* pb, RecomputePlan& rp, int R, bool fp64) {
+    const size_t elem = fp64 ? 16 : 8;
+    void* gbuf = pb->genbuf.get(rp.buf_elems * elem);
+    void* xs = pb->xs.get((size_t)pb->Ntot * R * elem);
+    void* part = pb->part.get((size_t)rp.nsplit * pb->Ntot * R * elem);
+    CK(cudaMemsetAsync(xs, 0, (size_t)pb->Ntot * R * elem, pb->stream));
+    const RecomputeChunk& ch = rp.chunks[0];
+    launch_generator_blocks(pb->d_cfg, ch.d_blocks, ch.nblocks, ch.nitems, pb->d_centre,
+                            fp64 ? (double2*)gbuf : nullptr, fp64 ? nullptr : (float2*)gbuf, pb->d_flags, pb->stream,
+                            !fp64);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double t = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, pb->stream));
+        launch_bt_only(rp.ch, fp64, ch.d_cfg, ch.d_work, ch.nwork, pb->Nmax, gbuf, xs, part, pb->Ntot, R, pb->stream);
+        CK_LAUNCH();
+        CK(cudaEventRecord(e1, pb->stream));
+        CK(cudaEventSynchronize(e1));
+        check_tc("recompute autotune");
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) t = std::min(t, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return t;
+}
+
+// The recompute plan of (R, precision): a pinned shape, else the faster on
+// the first chunk of the cost-model CUDA-core shape and (FP32, R divisible
+// by 16) the widest tensor-core shape.
+RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
+    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
+    auto it = pb->rplans.find(key);
+    if (it != pb->rplans.end()) return it->second;
+    auto pin = pb->pinned.find(key);
+    if (pin != pb->pinned.end())
+        return pb->rplans.emplace(key, build_recompute_plan(pb, R, fp64, pin->second)).first->second;
+    RecomputePlan rp = build_recompute_plan(pb, R, fp64, matvec_default_choice(R, pb->Nmax, fp64));
+    int rc = 0;
+    for (int c = 64; c >= 16 && !fp64; c /= 2)
+        if (tc_supported(R, pb->Nmax, c)) {
+            rc = c;
+            break;
+        }
+    if (rc && autotune_enabled() && !rp.chunks.empty()) {
+        RecomputePlan rt = build_recompute_plan(pb, R, fp64, MatvecChoice{0, rc, 0, 0, rc});
+        const double ta = time_first_chunk(pb, rp, R, fp64);
+        const double tb = time_first_chunk(pb, rt, R, fp64);
+        if (tb < ta) std::swap(rp, rt);
+        free_recompute_plan(rt);
+    }
     return pb->rplans.emplace(key, std::move(rp)).first->second;
 }
 
 void free_recompute_plans(msd_problem* pb) {
-    for (auto& kv : pb->rplans)
-        for (auto& ch : kv.second.chunks) {
-            cudaFree(ch.d_cfg);
-            cudaFree(ch.d_blocks);
-            cudaFree(ch.d_work);
-        }
+    for (auto& kv : pb->rplans) free_recompute_plan(kv.second);
     pb->rplans.clear();
 }
 
@@ -719,7 +801,7 @@ struct SolveCtx {
     // FP64 vectors [Ntot][R]
     double2 *b, *x, *r, *Ax;
     // per-system arrays ([S][hstride] for projections and norms)
-    double2 *h1, *h2, *wn2, *wn2b, *H, *cs, *sn, *g, *y, *lsq_work;
+    double2 *h1, *h2, *wn2, *wn2b, *H, *cs, *sn, *g, *y, *lsq_work, *rdiag;
     double *beta, *vscale, *tol_abs, *tol_cycle;
     int *active, *kconv, *iters, *skip2, *flags;  // flags[0] any_active, flags[1] nonfinite
     int hstride;
@@ -732,6 +814,9 @@ void norm2_f64(SolveCtx& cx, const double2* u, double2* out) {
     gm_dots<double2>(cx.d, cx.pb->d_chunks, cx.pb->d_cfg_chunk_off, nullptr, 0, 0, 1, u, nullptr, cx.part, out,
                      cx.hstride, cx.pb->stream);
 }
+
+// Basis size from which projections run over the coarse row chunks.
+constexpr int kCoarseFrom = 64;
 
 // One restart cycle of GMRES on P^-1 A d = r (x += d), basis type V.
 template <typename V>
@@ -765,18 +850,24 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         }
         V* vj = Vb + (long long)j * vstride;
         operator_dev(pb, d.R, fp64, cx.adjoint, vj, w);
+        // projections (not updates) onto many basis vectors use the coarse row chunks
+        const bool coarse = j + 1 >= kCoarseFrom;
+        GmresDims db = d;
+        if (coarse) db.nchunk = (int)pb->chunks_coarse.size();
+        const RowChunk* chb = coarse ? pb->d_chunks_coarse : ch;
+        const int* cob = coarse ? pb->d_cfg_chunk_off_coarse : co;
         // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1
-        gm_dots<V>(d, ch, co, Vb, vstride, j + 1, 1, w, nullptr, cx.part, cx.h1, cx.hstride, s);
+        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, nullptr, cx.part, cx.h1, cx.hstride, s);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, nullptr, -1.0, w, s);
-        gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, nullptr, cx.part, cx.wn2, cx.hstride, s);
         // second projection only where the first removed more than half of ||w||^2
         gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
-        gm_dots<V>(d, ch, co, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s);
+        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h2, cx.hstride, cx.skip2, -1.0, w, s);
         gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s);
         CK(cudaMemsetAsync(cx.flags, 0, sizeof(int), s));
         gm_givens(d, j, cx.h1, cx.h2, cx.hstride, cx.wn2, cx.wn2b, cx.skip2, cx.tol_cycle, cx.H, cx.cs, cx.sn,
-                  cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, s);
+                  cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, cx.rdiag,
+                  sizeof(V) == sizeof(float2), s);
         gm_scale<V, V>(d, ch, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
         CK_LAUNCH();
         const int slot = j % kRing;
@@ -802,7 +893,7 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         CK(cudaStreamSynchronize(s));
     }
     *steps_taken = j;
-    gm_lsq(d, cx.H, cx.g, cx.kconv, cx.y, cx.lsq_work, s);
+    gm_lsq(d, cx.H, cx.cs, cx.sn, cx.rdiag, cx.g, cx.kconv, cx.y, cx.lsq_work, s);
     // x += V y, each system over its own kconv columns (y is zero beyond it)
     gm_update<V, double2>(d, ch, Vb, vstride, j, cx.y, cx.m, nullptr, 1.0, cx.x, s);
     CK_LAUNCH();
@@ -876,7 +967,8 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     cx.cs = (double2*)sb((size_t)S * m * 16);
     cx.sn = (double2*)sb((size_t)S * m * 16);
     cx.g = (double2*)sb((size_t)S * (m + 1) * 16);
-    cx.y = (double2*)sb((size_t)S * m * 16);
+    cx.y = (double2*)sb((size_t)S * m * 2 * 16);
+    cx.rdiag = cx.y + (size_t)S * m;
     double* dsys = (double*)sb((size_t)S * 4 * 8);
     cx.beta = dsys;
     cx.vscale = dsys + S;
@@ -1101,23 +1193,28 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             // reduction chunks: at least 512 rows each (two or more rows per
             // thread of a reduction block) and about 256 overall, never
             // across configurations
-            const long long target_rows = std::max<long long>(512, row / 256);
-            std::vector<int> coff(C + 1, 0);
-            for (int c = 0; c < C; ++c) {
-                const MsdConfig& m = pb->cfg[c];
-                const long long rows = (long long)m.M * m.n;
-                for (long long r0 = 0; r0 < rows; r0 += target_rows) {
-                    RowChunk ch;
-                    ch.cfg = c;
-                    ch.pad = 0;
-                    ch.row0 = m.row_off + r0;
-                    ch.row1 = m.row_off + std::min(rows, r0 + target_rows);
-                    pb->chunks.push_back(ch);
+            auto make_chunks = [&](long long target_rows, std::vector<RowChunk>& out, RowChunk** d_out,
+                                   int** d_off) {
+                std::vector<int> coff(C + 1, 0);
+                for (int c = 0; c < C; ++c) {
+                    const MsdConfig& m = pb->cfg[c];
+                    const long long rows = (long long)m.M * m.n;
+                    for (long long r0 = 0; r0 < rows; r0 += target_rows) {
+                        RowChunk ch;
+                        ch.cfg = c;
+                        ch.pad = 0;
+                        ch.row0 = m.row_off + r0;
+                        ch.row1 = m.row_off + std::min(rows, r0 + target_rows);
+                        out.push_back(ch);
+                    }
+                    coff[c + 1] = (int)out.size();
                 }
-                coff[c + 1] = (int)pb->chunks.size();
-            }
-            pb->d_chunks = dalloc_copy(pb->chunks.data(), pb->chunks.size());
-            pb->d_cfg_chunk_off = dalloc_copy(coff.data(), coff.size());
+                *d_out = dalloc_copy(out.data(), out.size());
+                *d_off = dalloc_copy(coff.data(), coff.size());
+            };
+            make_chunks(std::max<long long>(512, row / 256), pb->chunks, &pb->d_chunks, &pb->d_cfg_chunk_off);
+            make_chunks(std::max<long long>(4096, row / 64), pb->chunks_coarse, &pb->d_chunks_coarse,
+                        &pb->d_cfg_chunk_off_coarse);
             launch_disk_diagonals(pb->d_cfg, Mtot, pb->d_disk_cfg, pb->d_radius, pb->d_bc, pb->Nmax, pb->d_J,
                                   pb->d_dJ, pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                                   pb->d_rhs_scale, pb->d_flags, pb->stream);
@@ -1138,6 +1235,7 @@ void msd_destroy(msd_problem* pb) {
     void* ptrs[] = {pb->d_cfg, pb->d_centre, pb->d_radius, pb->d_bc, pb->d_disk_cfg, pb->d_J, pb->d_dJ,
                     pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rhs_scale, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                     pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off,
+                    pb->d_chunks_coarse, pb->d_cfg_chunk_off_coarse,
                     pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -189,16 +189,18 @@ void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long lon
 template <typename Vin, typename Vout>
 void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale, const int* active,
               Vout* v, cudaStream_t s);
-void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, const double2* wn2,
+// ||w'||^2 estimate (written to wn2) and the re-orthogonalisation flags
+void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, double2* wn2,
                      const int* active, int* skip2, cudaStream_t s);
 void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* tol_abs, double* beta,
               double* vscale, double2* g, int* active, int* kconv, int* any_active, cudaStream_t s);
 void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride, const double2* wn2a,
                const double2* wn2b, const int* skip2, const double* tol_cycle, double2* H, double2* cs,
                double2* sn, double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
-               int* nonfinite, cudaStream_t s);
-void gm_lsq(const GmresDims& d, const double2* H, const double2* g, const int* kconv, double2* y, double2* work,
-            cudaStream_t s);
+               int* nonfinite, double2* rdiag, bool fp32_maps, cudaStream_t s);
+// end of a cycle: rotate the stored raw columns into R (in place), then back-substitute
+void gm_lsq(const GmresDims& d, double2* H, const double2* cs, const double2* sn, const double2* rdiag,
+            const double2* g, const int* kconv, double2* y, double2* work, cudaStream_t s);
 void gm_residual(long long n, const double2* b, const double2* Ax, double2* r, cudaStream_t s);
 void gm_zero(long long n, double2* x, cudaStream_t s);
 
