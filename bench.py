@@ -266,6 +266,68 @@ def products_table(reps: int = 3):
     os.environ.pop("MSD_AUTOTUNE", None)
 
 
+def grad_timing(reps: int = 3):
+    """One JSON line per precision: the adjoint gradient of the far-field
+    misfit on the 200-disk workload (M = 200, k = 10, N = 22, 16 incidences,
+    360 far-field samples; target = the perturbed configuration's far field):
+    forward solve, far field, misfit, adjoint solve, pair and per-disk
+    gradient kernels, timed with CUDA events around the whole C-ABI call
+    (host outputs), after one untimed call."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cl = W.cluster_200()
+    betas, th = W.angles(16), W.angles(360)
+    tgt = W.perturbed_target(cl, seed=40)
+    pt = msd.Problem(tgt)
+    rt = pt.solve(betas, tol=1e-13, precision=msd.MSD_MIXED)
+    Ft = pt.farfield(rt.rho, th).cpu().numpy()
+    pt.close()
+    pb = msd.Problem(cl)
+    for prec, name in ((msd.MSD_FP64, "fp64"), (msd.MSD_MIXED, "mixed")):
+        pb.grad_farfield_misfit(betas, th, Ft, tol=1e-12, precision=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            J, dO, da, dk = pb.grad_farfield_misfit(betas, th, Ft, tol=1e-12, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "random200_k10 (M=200, N=22, 16 incidences, 360 samples)",
+                          "what": "J and dJ/d(centres, radii, k) by the adjoint method, solves to relres 1e-12",
+                          "precision": name, "ms_per_gradient": round(e0.elapsed_time(e1) / reps, 2),
+                          "J": float(J[0]), "grad_norm": float(np.sqrt((dO ** 2).sum() + (da ** 2).sum() + dk[0] ** 2))}),
+              flush=True)
+    pb.close()
+
+
+def batched_timing(count: int = 16):
+    """Batched solves: `count` clusters of the batched recipe (mixed
+    Dirichlet/Neumann, k ~ U[1, 8], N = ceil(k) + 8, area fraction 0.2, gap
+    0.01; M restricted to 50..150 so that a solve ends in minutes) with 32
+    incidences each, in one batch (count x 32 systems), to relres 1e-10,
+    plain FP64 and mixed precision; CUDA events around each solve."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cls = W.batched_clusters(count=count, m_lo=50, m_hi=150)
+    R = 32
+    betas = np.stack([W.angles(R)] * len(cls))
+    pb = msd.Problem(cls)
+    for prec, name in ((msd.MSD_FP64, "fp64"), (msd.MSD_MIXED, "mixed")):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = pb.solve(betas, tol=1e-10, precision=prec, maxit=8000)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": f"batched recipe, {count} clusters (M 50..150), {R} incidences each",
+                          "systems": int(len(cls) * R), "unknowns": int(pb.ntot), "precision": name,
+                          "solve_ms": round(e0.elapsed_time(e1), 1), "status": int(res.status),
+                          "iters_max": int(res.iters.max()), "refine_steps": int(res.refine_steps.max()),
+                          "relres_max": float(res.relres.max())}), flush=True)
+    pb.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,9 +339,17 @@ def main():
                     help="run a minimal workload for a profiler capture and print no JSON line")
     ap.add_argument("--products", action="store_true",
                     help="print a table (JSON lines) of block-product kernels over the workloads instead")
+    ap.add_argument("--grad", action="store_true",
+                    help="print the timing (JSON lines) of the far-field misfit gradient instead")
+    ap.add_argument("--batched", action="store_true",
+                    help="print FP64 and mixed batched solve times (JSON lines) instead")
     args = ap.parse_args()
+    if args.batched:
+        return batched_timing()
     if args.products:
         return products_table()
+    if args.grad:
+        return grad_timing()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_only:

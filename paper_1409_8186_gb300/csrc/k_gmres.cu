@@ -239,21 +239,15 @@ __global__ void k_update(const RowChunk* __restrict__ chunks, int R, const V* __
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
         A ax[4] = {A(0), A(0), A(0), A(0)}, ay[4] = {A(0), A(0), A(0), A(0)};
         const V* vp = Vb + (long long)i0 * vstride + row * R + r;
-        int i = 0;
-        for (; i + 4 <= cnt; i += 4) {
+        // all kU loads of the row in flight before the multiply-adds
+        V vv[kU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const V vv = vp[(long long)(i + u) * vstride];
-                const V hh = hsm[i + u][tx];
-                ax[u] = fma(vv.x, hh.x, fma(-vv.y, hh.y, ax[u]));
-                ay[u] = fma(vv.x, hh.y, fma(vv.y, hh.x, ay[u]));
-            }
-        }
-        for (; i < cnt; ++i) {
-            const V vv = vp[(long long)i * vstride];
-            const V hh = hsm[i][tx];
-            ax[0] = fma(vv.x, hh.x, fma(-vv.y, hh.y, ax[0]));
-            ay[0] = fma(vv.x, hh.y, fma(vv.y, hh.x, ay[0]));
+        for (int u = 0; u < kU; ++u) vv[u] = u < cnt ? vp[(long long)u * vstride] : V{A(0), A(0)};
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const V hh = hsm[u][tx];  // zero beyond cnt
+            ax[u & 3] = fma(vv[u].x, hh.x, fma(-vv[u].y, hh.y, ax[u & 3]));
+            ay[u & 3] = fma(vv[u].x, hh.y, fma(vv[u].y, hh.x, ay[u & 3]));
         }
         const double2 d = make_double2((double)((ax[0] + ax[1]) + (ax[2] + ax[3])),
                                        (double)((ay[0] + ay[1]) + (ay[2] + ay[3])));

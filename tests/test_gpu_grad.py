@@ -4,8 +4,8 @@ against centred finite differences (h = 1e-6) of the GPU misfit.
 
 Tolerances: 1e-7 relative against the oracle (both are adjoint gradients of
 the same discrete misfit; the GPU solves to relres 1e-13 here); 1e-5 against
-finite differences at full size (the benchmark spec's bound: FD truncation h^2 and
-solve error / h).
+finite differences at full size (the gradient bound of this project: FD
+truncation h^2 and solve error / h).
 """
 import numpy as np
 import pytest
