@@ -211,6 +211,8 @@ def products_table(reps: int = 3):
         ("random400 (M=400, N=20)", W.random_cluster_400, [(F64, 1), (F32, 1)], False),
         ("random200_k10 (M=200, N=22)", W.cluster_200, [(F64, 16), (F32, 16)], False),
         ("batched6 (6 of the 256 batched clusters)", lambda: W.batched_clusters(count=6), [(F32, 32)], False),
+        ("batched256 (all 256 batched clusters, 3.1 M unknowns)", lambda: W.batched_clusters(count=256),
+         [(F32, 32)], False),
         ("lattice4000 (M=4000, N=15)", W.lattice_4000, [(F64, 1), (F32, 1), (F32, 64)], True),
     ]
     for name, make, shapes, try_recompute in cases:

@@ -83,6 +83,10 @@ typedef struct {
     int refine_steps;  /* FP64 residual evaluations after the first (MSD_MIXED)         */
     int reserved;
     double relres;     /* final FP64 relative residual of the preconditioned system     */
+    double true_relres;/* ||b - A rho|| / ||b|| of the unpreconditioned system, from the
+                          final residual and the diagonal preconditioner (section 5);
+                          -1 for adjoint solves and for R > 64                          */
+    double solve_ms;   /* wall time of the whole call (host clock), every system       */
 } msd_stats;
 
 /* Create a problem.  Section 4.1 (geometry), section 5 (truncation).

@@ -310,6 +310,48 @@ void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, i
     g_msd_launches += 1;
 }
 
+// ---------------------------------------------------------------- true residual
+
+// Unpreconditioned norms of two vectors: the single-scattering preconditioner
+// P is the diagonal of the self blocks (section 4.2), P_mm = (i pi a/2)
+// J_m H_m on Dirichlet rows and (i pi k a/2) J_m H'_m on Neumann rows, so
+// ||P u||^2 = sum |P_row|^2 |u_row|^2.  One CTA per row chunk; part[chunk][r]
+// = (sum |P|^2 |u|^2, sum |P|^2 |v|^2) over the chunk's rows.
+__global__ void k_weighted_norms(const MsdConfig* __restrict__ cfg, const RowChunk* __restrict__ chunks, int R,
+                                 const double* __restrict__ radius, const int8_t* __restrict__ bc,
+                                 const double2* __restrict__ J, const double2* __restrict__ H,
+                                 const double2* __restrict__ dH, const double2* __restrict__ u,
+                                 const double2* __restrict__ v, double2* __restrict__ part) {
+    __shared__ double su[64], sv[64];
+    for (int t = threadIdx.x; t < R; t += blockDim.x) su[t] = sv[t] = 0.0;
+    __syncthreads();
+    const RowChunk ch = chunks[blockIdx.x];
+    const MsdConfig c = cfg[ch.cfg];
+    const long long tot = (ch.row1 - ch.row0) * R;
+    for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+        const long long row = ch.row0 + t / R;
+        const int r = (int)(t % R);
+        const int p = (int)((row - c.row_off) / c.n);
+        const double a = radius[c.disk_off + p];
+        const double2 jj = J[row];
+        const double2 hh = bc[c.disk_off + p] ? dH[row] : H[row];
+        const double sc = bc[c.disk_off + p] ? 0.5 * M_PI * c.k * a : 0.5 * M_PI * a;
+        const double w2 = sc * sc * cabs2(jj) * cabs2(hh);
+        atomicAdd(&su[r], w2 * cabs2(u[row * R + r]));
+        atomicAdd(&sv[r], w2 * cabs2(v[row * R + r]));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < R; t += blockDim.x)
+        part[(long long)blockIdx.x * R + t] = make_double2(su[t], sv[t]);
+}
+
+void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int nchunk, int R,
+                           const double* d_radius, const int8_t* d_bc, const double2* J, const double2* H,
+                           const double2* dH, const double2* u, const double2* v, double2* part, cudaStream_t s) {
+    k_weighted_norms<<<nchunk, 256, 0, s>>>(d_cfg, d_chunks, R, d_radius, d_bc, J, H, dH, u, v, part);
+    g_msd_launches += 1;
+}
+
 // ---------------------------------------------------------------- K5
 
 // One thread per (disk, column r).  d^p_m = sqrt(2 pi a_p) e^{i k beta_hat . O_p}

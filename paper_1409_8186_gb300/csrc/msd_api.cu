@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -905,6 +906,7 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
 msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts_in,
                       void* rho_out, msd_stats* stats_host, const double2* b_dev = nullptr, bool adjoint = false) {
     if (!pb || R <= 0 || (!betas_host && !b_dev) || !rho_out) fail(MSD_ERR_ARG, "msd_solve_planewaves: bad argument");
+    const auto t_start = std::chrono::steady_clock::now();
     msd_opts o;
     memset(&o, 0, sizeof(o));
     if (opts_in) o = *opts_in;
@@ -1074,8 +1076,29 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     }
     std::vector<int> it(S);
     CK(cudaMemcpyAsync(it.data(), cx.iters, S * 4, cudaMemcpyDeviceToHost, s));
+    // unpreconditioned relative residual ||P r'|| / ||P b'|| from the final
+    // FP64 residual r' of the preconditioned system
+    std::vector<double> true_relres(S, -1.0);
+    if (!adjoint && R <= 64) {
+        const int nch = (int)pb->chunks.size();
+        launch_weighted_norms(pb->d_cfg, pb->d_chunks, nch, R, pb->d_radius, pb->d_bc, pb->d_J, pb->d_H, pb->d_dH,
+                              cx.r, cx.b, cx.part, s);
+        CK_LAUNCH();
+        std::vector<double2> wp((size_t)nch * R);
+        CK(cudaMemcpyAsync(wp.data(), cx.part, wp.size() * 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::vector<double> nu(S, 0.0), nv2(S, 0.0);
+        for (int k = 0; k < nch; ++k)
+            for (int r = 0; r < R; ++r) {
+                nu[pb->chunks[k].cfg * R + r] += wp[(size_t)k * R + r].x;
+                nv2[pb->chunks[k].cfg * R + r] += wp[(size_t)k * R + r].y;
+            }
+        for (int i = 0; i < S; ++i) true_relres[i] = nv2[i] > 0 ? std::sqrt(nu[i] / nv2[i]) : 0.0;
+    }
     CK(cudaStreamSynchronize(s));
     check_tc("msd_solve_planewaves");
+    const double solve_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     msd_status st = MSD_OK;
     for (int i = 0; i < S; ++i) {
         int flag = relres[i] <= o.tol ? MSD_OK : (stagnated ? MSD_STAGNATED : MSD_NOT_CONVERGED);
@@ -1086,6 +1109,8 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
             stats_host[i].refine_steps = sweeps > 0 ? sweeps - 1 : 0;
             stats_host[i].reserved = 0;
             stats_host[i].relres = relres[i];
+            stats_host[i].true_relres = true_relres[i];
+            stats_host[i].solve_ms = solve_ms;
         }
     }
     return st;

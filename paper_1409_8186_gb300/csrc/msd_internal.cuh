@@ -139,6 +139,12 @@ void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, i
                              const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s,
                              bool f32_math = false);
 
+// ||P u||^2 and ||P v||^2 per (row chunk, column) with the preconditioner's
+// diagonal P (unpreconditioned residual norms); R <= 64.
+void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int nchunk, int R,
+                           const double* d_radius, const int8_t* d_bc, const double2* J, const double2* H,
+                           const double2* dH, const double2* u, const double2* v, double2* part, cudaStream_t s);
+
 // K5: preconditioned plane-wave right-hand sides.
 void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
                           const double2* d_centre, const double* d_radius,

@@ -44,7 +44,8 @@ class msd_opts(ctypes.Structure):
 
 class msd_stats(ctypes.Structure):
     _fields_ = [("flag", ctypes.c_int), ("iters", ctypes.c_int), ("refine_steps", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("relres", ctypes.c_double)]
+                ("reserved", ctypes.c_int), ("relres", ctypes.c_double), ("true_relres", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
 
 
 def _load():
@@ -241,6 +242,8 @@ class SolveResult:
     iters: np.ndarray
     refine_steps: np.ndarray
     relres: np.ndarray
+    true_relres: np.ndarray = None   # ||b - A rho|| / ||b|| (unpreconditioned); -1 where not computed
+    solve_ms: float = 0.0
 
 
 class Problem:
@@ -331,7 +334,8 @@ class Problem:
         stats = (msd_stats * (self.C * R))()
         st = msd_solve_planewaves(self.handle, R, b, o, rho, stats)
         return SolveResult(rho, st, np.array([s.flag for s in stats]), np.array([s.iters for s in stats]),
-                           np.array([s.refine_steps for s in stats]), np.array([s.relres for s in stats]))
+                           np.array([s.refine_steps for s in stats]), np.array([s.relres for s in stats]),
+                           np.array([s.true_relres for s in stats]), float(stats[0].solve_ms) if len(stats) else 0.0)
 
     def farfield(self, rho, thetas, out=None):
         import torch

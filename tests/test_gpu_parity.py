@@ -264,6 +264,23 @@ def test_solve_random_cluster(msd, precision):
     assert relerr(F, Fref) < 50 * tol
 
 
+@pytest.mark.parametrize("name", ["four_disks", "mixed6"])
+def test_true_relres_matches_oracle(msd, name):
+    """stats.true_relres = ||b - A rho|| / ||b|| of the unpreconditioned system
+    (section 5), recomputed here with the oracle's assembled A and b = -U."""
+    cl = CASES[name]()
+    betas = np.array([0.0, 1.1])
+    pb = msd.Problem(cl)
+    for prec in (msd.MSD_FP64, msd.MSD_MIXED):
+        res = pb.solve(betas, tol=1e-10, precision=prec)
+        rho = np_(res.rho)
+        A = O_.assemble(cl.centres, cl.radii, cl.bc, cl.k, cl.N)
+        b = O_.rhs_planewave(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas)
+        ref = np.linalg.norm(A @ rho - b, axis=0) / np.linalg.norm(b, axis=0)
+        assert np.all(np.abs(res.true_relres - ref) <= 0.05 * ref + 1e-14), (res.true_relres, ref)
+        assert res.solve_ms > 0
+
+
 def test_farfield_host_buffers(msd):
     """Host in, host out (the end-to-end path of the C ABI)."""
     cl = CASES["mixed6"]()
