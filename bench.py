@@ -461,6 +461,24 @@ def main():
     kern_gbs = r64["kernel_bytes"] / kern_s / 1e9 if kern_s > 0 else 0.0
     mix_kern_s = rmx["kernel_ms"] * 1e-3
 
+    # the other steps of the path, each timed alone after the timed region
+    # (CUDA events around 10 calls; update_geometry includes its host-side
+    # flag check)
+    rhs_buf = torch.empty((cl.ntot, 1), dtype=torch.complex128, device="cuda")
+    stage_ms = {}
+    for sname, fn in (("k1_k2_update_geometry", lambda: msd.msd_update_geometry(h, cen_d, rad_d, None)),
+                      ("k5_rhs_planewave", lambda: msd.msd_rhs_planewave(h, 1, beta, rhs_buf)),
+                      ("k6_farfield_360", lambda: msd.msd_farfield(h, rho, 1, thetas, F))):
+        fn()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(10):
+            fn()
+        s1.record()
+        torch.cuda.synchronize()
+        stage_ms[sname] = round(s0.elapsed_time(s1) / 10, 4)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         sample = list(range(0, cl.M, cl.M // 8))[:8]
@@ -483,6 +501,7 @@ def main():
         "iters_fp64": r64["iters"][-1], "iters_mixed": rmx["iters"][-1],
         "relres_fp64": r64["relres"], "relres_mixed": rmx["relres"],
         "status_fp64": r64["status"][-1], "status_mixed": rmx["status"][-1],
+        "stage_ms": stage_ms,
         "matvec_fp64": {"kernel_ms_avg": r64["kernel_ms"] / max(1, r64["kernel_launches"]),
                         "launches": r64["kernel_launches"], "GB_s": kern_gbs, "hbm_frac": kern_gbs / hbm,
                         "TFLOP_s": achieved_tf},

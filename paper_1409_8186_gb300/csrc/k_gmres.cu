@@ -136,6 +136,21 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
     if (i >= nvv) return;  // a whole warp
     const V* u = i < nv ? Vb + (long long)i * vstride : w;
     const long long e0 = ch.row0 * R, e1 = ch.row1 * R;
+    // systems with skip set (no second projection) need no sums: a warp whose
+    // columns are all skipped only writes its zeros
+    if (skip) {
+        bool live = false;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) live |= !skip[ch.cfg * R + (int)((e0 + lane + 32 * q) % R)];
+        if (!__any_sync(0xffffffffu, live)) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (Q == 2 || lane < R)
+                    part[((long long)blockIdx.x * nvv + i) * R + (int)((e0 + lane + 32 * q) % R)] =
+                        make_double2(0.0, 0.0);
+            return;
+        }
+    }
     typedef decltype(V{}.x) A;
     A ax[Q], ay[Q];
 #pragma unroll
