@@ -227,7 +227,8 @@ __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_ch
 // sweep).  With more than one vector group the groups meet in atomics;
 // with one group the result is stored directly.
 template <typename V, typename W>
-__global__ void k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
+__global__ void __launch_bounds__(kThreads, 4)
+    k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
                          int nv, const double2* __restrict__ h, int hstride, const int* __restrict__ skip,
                          double sign, W* __restrict__ w) {
     typedef decltype(V{}.x) A;

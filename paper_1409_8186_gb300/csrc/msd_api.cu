@@ -851,8 +851,10 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         }
         V* vj = Vb + (long long)j * vstride;
         operator_dev(pb, d.R, fp64, cx.adjoint, vj, w);
-        // projections (not updates) onto many basis vectors use the coarse row chunks
-        const bool coarse = j + 1 >= kCoarseFrom;
+        // projections onto many basis vectors: the coarse row chunks when the
+        // block-reduction kernel serves this column count (warp-per-vector
+        // kernels need no reduction and run on the fine chunks: more warps)
+        const bool coarse = j + 1 >= kCoarseFrom && !(32 % d.R == 0 || d.R == 64);
         GmresDims db = d;
         if (coarse) db.nchunk = (int)pb->chunks_coarse.size();
         const RowChunk* chb = coarse ? pb->d_chunks_coarse : ch;
