@@ -259,14 +259,18 @@ msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes
  *
  * msd_plan_info: the shape used for (R, precision), precision MSD_FP64 or
  *   MSD_FP32, creating the plan (and tuning) if needed.  out[4] receives
- *   {KB, RT, nsplit, number of shapes timed (0: not tuned)}; tuned_ms (may
+ *   {KB (encoded as for msd_set_tile), RT, nsplit, number of shapes timed
+ *   (0: not tuned)}; tuned_ms (may
  *   be NULL) the kernel time of the chosen shape in the tuning run (0 if
  *   not tuned).  Needs the generators of that precision (builds them).
  * msd_set_tile: fix the shape (KB, RT) for later products of (R, precision)
  *   of this problem, replacing any plan made before.  MSD_ERR_ARG if
  *   (KB, RT) is not one of the instantiated shapes that fit (FP64: KB 4..7,
  *   RT 1; FP32: KB 4..9, RT in {1,2,4,8,16} dividing R, at most 16 warps
- *   per CTA, shared memory <= 227 KB). */
+ *   per CTA, shared memory <= 227 KB; FP32 KB + 100 selects the same window
+ *   with each complex multiply-add issued as two paired FP32 FMAs; KB = 0,
+ *   RT in {16, 32, 64} dividing R: the tensor-core kernel).  KB reported by
+ *   msd_plan_info uses the same encoding. */
 msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double* tuned_ms);
 msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT);
 

@@ -95,10 +95,48 @@ struct Mac3 {
     }
 };
 
-template <typename V, int KB, int RB> struct MacFor { typedef Mac4<V, KB, RB> type; };
-template <int KB, int RB> struct MacFor<double2, KB, RB> { typedef Mac3<double2, KB, RB> type; };
+// Mac2: the FP32 complex multiply-add as two paired FMAs (fma.rn.f32x2, one
+// instruction for the real and the imaginary part, IEEE round-to-nearest per
+// lane): with g = gx + i gy and x = a + i b,
+//   (re, im) += (gx, gy) * (a, a) + (-gy, gx) * (b, b).
+// The pairs of g are formed once per generator value entering the register
+// window and those of x once per source value, so the FP32 kernel, which is
+// bound by instruction issue, issues half the FMA instructions of Mac4.
+__device__ __forceinline__ unsigned long long pk2(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+template <int KB, int RB>
+struct Mac2 {
+    typedef unsigned long long P;
+    struct G { P g1, g2; };
+    struct X { P xa, xb; };
+    P acc[KB][RB];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int b = 0; b < KB; ++b)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[b][r] = 0ull;  // (0.0f, 0.0f)
+    }
+    __device__ __forceinline__ static G gen(float2 v) { return G{pk2(v.x, v.y), pk2(-v.y, v.x)}; }
+    __device__ __forceinline__ static X src(float2 v) { return X{pk2(v.x, v.x), pk2(v.y, v.y)}; }
+    __device__ __forceinline__ void mac(int b, int r, const G& g, const X& x) {
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[b][r]) : "l"(g.g1), "l"(x.xa));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[b][r]) : "l"(g.g2), "l"(x.xb));
+    }
+    __device__ __forceinline__ float2 result(int b, int r) const {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[b][r]));
+        return make_float2(lo, hi);
+    }
+};
 
-template <typename V, int RT, int RB, int KB>
+template <typename V, int KB, int RB, int P> struct MacFor { typedef Mac4<V, KB, RB> type; };
+template <int KB, int RB> struct MacFor<double2, KB, RB, 0> { typedef Mac3<double2, KB, RB> type; };
+template <int KB, int RB> struct MacFor<float2, KB, RB, 1> { typedef Mac2<KB, RB> type; };
+
+template <typename V, int RT, int RB, int KB, int P>
 __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
                                                    const MatvecWork* __restrict__ works,
                                                    const V* __restrict__ G, const V* __restrict__ xs,
@@ -166,7 +204,7 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
         }
     };
 
-    typedef typename MacFor<V, KB, RB>::type Mac;
+    typedef typename MacFor<V, KB, RB, P>::type Mac;
     Mac acc;
     acc.init();
 
@@ -308,12 +346,12 @@ Choice choose(int R, int Nmax, bool fp64) {
     return best;
 }
 
-template <typename V, int RT, int RB, int KB>
+template <typename V, int RT, int RB, int KB, int P = 0>
 struct Bt {
     static void attr() {
         static bool done = false;
         if (!done) {
-            cudaFuncSetAttribute(k_bt_matvec<V, RT, RB, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_bt_matvec<V, RT, RB, KB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  227 * 1024);
             done = true;
         }
@@ -330,14 +368,14 @@ struct Bt {
                        const V* xs, V* part, long long Ntot, int R, cudaStream_t s) {
         attr();
         const int rtiles = R / RT;
-        k_bt_matvec<V, RT, RB, KB><<<(unsigned)(nwork * rtiles), block(Nmax), smem(Nmax), s>>>(
+        k_bt_matvec<V, RT, RB, KB, P><<<(unsigned)(nwork * rtiles), block(Nmax), smem(Nmax), s>>>(
             d_cfg, d_work, G, xs, part, Ntot, R, rtiles);
     }
     static int occupancy(int Nmax) {
         attr();
         const dim3 b = block(Nmax);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB, KB>, b.x * b.y,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB, KB, P>, b.x * b.y,
                                                           smem(Nmax)) != cudaSuccess) {
             cudaGetLastError();
             nb = 1;
@@ -347,15 +385,20 @@ struct Bt {
 };
 
 // Dispatch on (RT, RB) for a fixed KB (FP32), or KB alone (FP64).
+template <int KB, int P, typename F>
+void with_f32_p(const Choice& c, F&& f) {
+    switch (c.RT) {
+        case 1: f(Bt<float2, 1, 1, KB, P>()); break;
+        case 2: f(Bt<float2, 2, 2, KB, P>()); break;
+        case 4: f(Bt<float2, 4, 4, KB, P>()); break;
+        case 8: f(Bt<float2, 8, 4, KB, P>()); break;
+        default: f(Bt<float2, 16, 4, KB, P>()); break;
+    }
+}
 template <int KB, typename F>
 void with_f32(const Choice& c, F&& f) {
-    switch (c.RT) {
-        case 1: f(Bt<float2, 1, 1, KB>()); break;
-        case 2: f(Bt<float2, 2, 2, KB>()); break;
-        case 4: f(Bt<float2, 4, 4, KB>()); break;
-        case 8: f(Bt<float2, 8, 4, KB>()); break;
-        default: f(Bt<float2, 16, 4, KB>()); break;
-    }
+    if (c.P2) with_f32_p<KB, 1>(c, f);
+    else with_f32_p<KB, 0>(c, f);
 }
 
 template <typename F>
@@ -404,12 +447,14 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap) {
             if (R % rt) break;
             const int rb = rt < 4 ? rt : 4;
             if (I * (rt / rb) > 16) continue;
-            Choice c{KB, rt, rb, I};
-            size_t b = 0;
-            dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
-            if (b > 227 * 1024) continue;
-            if (cnt < cap) out[cnt] = c;
-            ++cnt;
+            for (int p2 = 0; p2 <= (fp64 ? 0 : 1); ++p2) {
+                Choice c{KB, rt, rb, I, 0, p2};
+                size_t b = 0;
+                dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
+                if (b > 227 * 1024) continue;
+                if (cnt < cap) out[cnt] = c;
+                ++cnt;
+            }
         }
     }
     if (!fp64)

@@ -349,8 +349,8 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     const TuneKey key{pb->Nmax, R, fp64 ? 1 : 0, pb->C, pb->Ntot, pb->Mmax, dev};
-    MatvecChoice cand[64];
-    const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 64);
+    MatvecChoice cand[128];
+    const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 128);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -1411,7 +1411,7 @@ msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double
         const bool fp64 = precision == MSD_FP64;
         ensure_generators(pb, fp64);
         MatvecPlan& plan = get_plan(pb, R, fp64);
-        out[0] = plan.ch.KB;
+        out[0] = plan.ch.KB + 100 * plan.ch.P2;
         out[1] = plan.ch.RT;
         out[2] = plan.nsplit;
         out[3] = plan.candidates;
@@ -1425,11 +1425,11 @@ msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT) {
         if (!pb || R <= 0) fail(MSD_ERR_ARG, "msd_set_tile: bad argument");
         if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_set_tile: precision");
         const bool fp64 = precision == MSD_FP64;
-        MatvecChoice cand[64];
-        const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 64);
+        MatvecChoice cand[128];
+        const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 128);
         int hit = -1;
         for (int i = 0; i < nc; ++i)
-            if (cand[i].KB == KB && cand[i].RT == RT) hit = i;
+            if (cand[i].KB + 100 * cand[i].P2 == KB && cand[i].RT == RT) hit = i;
         if (hit < 0) fail(MSD_ERR_ARG, "msd_set_tile: (KB, RT) is not an instantiated shape that fits");
         const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
         auto it = pb->plans.find(key);

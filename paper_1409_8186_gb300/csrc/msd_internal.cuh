@@ -92,6 +92,7 @@ struct RowChunk {
 struct MatvecChoice {
     int KB, RT, RB, I;
     int TC;  // > 0: tensor-core kernel with TC columns per CTA (KB, RB, I unused; RT = TC)
+    int P2;  // FP32: 1 = complex multiply-adds as paired FMAs (fma.rn.f32x2), 0 = four FFMAs
 };
 MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64);
 int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap);
