@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ uint32_t tmem_sh;
     __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ __align__(8) uint64_t accbar[2];  // the MMAs of a source into accumulator 0 / 1 are done
+    __shared__ int abort_sh;                      // a pipeline wait ran out
 
     const int wi = blockIdx.x / rtiles;
     const int rt = blockIdx.x - wi * rtiles;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
+        abort_sh = 0;
         for (int s = 0; s < kTcStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
         for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accbar[s])));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -217,21 +219,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int b = it % kTcStages;
         const int qi = it / nk, kc = it - qi * nk;
         if (it + 1 < nst) load_stage(it + 1, gn, xn);  // in flight during the waits and the expansion
+        // One CTA barrier per stage (after the expansion).  A wait that runs
+        // out records the failure and the thread carries on through the same
+        // barriers (no thread leaves them), so the results are discarded at
+        // the end; warp-collective TMEM loads only run for whole warps.
         bool mine = true;  // the MMAs that last read buffer b are done
         if (it >= kTcStages) mine = mbar_wait(smem_u32(&mbar[b]), (uint32_t)((it / kTcStages - 1) & 1));
         // the accumulator of this source last held source qi - 2: fold it first
-        if (kc == 0 && qi >= 2 && mine) {
-            mine = mbar_wait(smem_u32(&accbar[qi & 1]), (uint32_t)(((qi - 2) >> 1) & 1));
-            if (mine) {
+        if (kc == 0 && qi >= 2) {
+            bool acc_ready = mine && mbar_wait(smem_u32(&accbar[qi & 1]), (uint32_t)(((qi - 2) >> 1) & 1));
+            acc_ready = __all_sync(0xffffffffu, acc_ready);
+            if (acc_ready) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 fold(qi & 1);
                 asm volatile("tcgen05.fence::before_thread_sync;");
             }
+            mine = mine && acc_ready;
         }
-        if (!__syncthreads_and(mine)) {  // uniform decision: no thread leaves the barriers alone
-            ok = false;
-            break;
-        }
+        if (!mine) abort_sh = 1;
         const int k0 = kc * kKc;
         unsigned char* st = sm + b * Lay::kStageBytes;
         unsigned char* Arh = st;
@@ -326,6 +331,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         drained = mbar_wait(smem_u32(&mbar[last % kTcStages]), (uint32_t)((last / kTcStages) & 1));
     }
     drained = __syncthreads_and(drained);
+    ok = abort_sh == 0;  // read after the barrier above
     if ((!ok || !drained) && tid == 0) atomicOr(&g_tc_status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
 
