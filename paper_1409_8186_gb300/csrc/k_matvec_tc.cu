@@ -35,7 +35,8 @@ __device__ int g_tc_status;  // bit 0: a pipeline wait expired
 namespace {
 
 constexpr int kTcM = 128;       // rows of one MMA
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 288;   // 8 expansion / accumulator warps + 1 MMA warp
+constexpr int kExpThreads = 256;
 constexpr int kTcStages = 3;
 constexpr int kKc = 16;         // modes per stage (two K-steps of 8)
 constexpr int kLbo = 128;
@@ -159,9 +160,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tmem = tmem_sh;
 
     // A expansion role: row ai = (target pl, mode m), modes 8*akh .. 8*akh+7 of the stage
-    const int ai = tid & (kTcM - 1), akh = tid >> 7;
+    // warp 8 only issues the MMAs; warps 0-7 expand the operands and hold the
+    // accumulator sums (warp & 3 = TMEM lane quarter, warp >> 2 = half of the columns)
+    const bool mma_warp = warp == kExpThreads / 32;
+    const int ai = tid & (kTcM - 1), akh = (tid >> 7) & 1;
     const int apl = ai / n, am = ai - apl * n;
-    const bool arow = apl < np;
+    const bool arow = !mma_warp && apl < np;
     const float2* grow = G + c.gen_off + (long long)(w.p0 + (arow ? apl : 0)) * L + 2 * N - am;
     // B expansion role: column cb, mode quad bq (4 RC items)
     const float2* xq0 = xs + c.row_off * R + col0;
@@ -193,6 +197,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // raw values of a stage, loaded one stage ahead into registers so that the
     // global-memory latency overlaps the expansion and MMAs of the stage before
     const int bitem = tid < 4 * RC ? tid : -1;  // B item (column cb, mode quad kq); 4 RC <= 256 items
+                                                // (so the MMA warp has none)
     const int bcb = bitem % RC, bkq = bitem / RC;
     auto load_stage = [&](int st_it, float2* ga, float2* xv) {
         const int sq = w.q0 + st_it / nk;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bool mine = true;  // the MMAs that last read buffer b are done
         if (it >= kTcStages) mine = mbar_wait(smem_u32(&mbar[b]), (uint32_t)((it / kTcStages - 1) & 1));
         // the accumulator of this source last held source qi - 2: fold it first
-        if (kc == 0 && qi >= 2) {
+        if (kc == 0 && qi >= 2 && !mma_warp) {
             bool acc_ready = mine && mbar_wait(smem_u32(&accbar[qi & 1]), (uint32_t)(((qi - 2) >> 1) & 1));
             acc_ready = __all_sync(0xffffffffu, acc_ready);
             if (acc_ready) {
@@ -245,23 +250,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned char* Ail = st + 3 * kABytes;
         unsigned char* Bb = st + 4 * kABytes;  // B1h, B1l, B2h, B2l
         // ---- A: Toeplitz rows g_{k-m}, k = k0 + 8 akh + j
+        if (!mma_warp) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int kq = akh * 2 + h;
-            float re[4], im[4];
+            for (int h = 0; h < 2; ++h) {
+                const int kq = akh * 2 + h;
+                float re[4], im[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                re[j] = ga[h * 4 + j].x;
-                im[j] = ga[h * 4 + j].y;
+                for (int j = 0; j < 4; ++j) {
+                    re[j] = ga[h * 4 + j].x;
+                    im[j] = ga[h * 4 + j].y;
+                }
+                float4 hi, lo;
+                const int off = quad_off(ai, kq);
+                split4(re, hi, lo);
+                *(float4*)(Arh + off) = hi;
+                *(float4*)(Arl + off) = lo;
+                split4(im, hi, lo);
+                *(float4*)(Aih + off) = hi;
+                *(float4*)(Ail + off) = lo;
             }
-            float4 hi, lo;
-            const int off = quad_off(ai, kq);
-            split4(re, hi, lo);
-            *(float4*)(Arh + off) = hi;
-            *(float4*)(Arl + off) = lo;
-            split4(im, hi, lo);
-            *(float4*)(Aih + off) = hi;
-            *(float4*)(Ail + off) = lo;
         }
         // ---- B: [Re X | Im X] and [-Im X | Re X] of source q, modes k0 .. k0+15
         if (bitem >= 0) {
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == kExpThreads) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             constexpr uint32_t id = idesc_tf32(kTcM, 2 * RC);
             const uint32_t a_addr[6] = {smem_u32(Arh), smem_u32(Arh), smem_u32(Arl),
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if ((!ok || !drained) && tid == 0) atomicOr(&g_tc_status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
 
-    if (ok && drained) {
+    if (ok && drained && !mma_warp) {
         // fold the last one or two sources (every MMA is complete here)
         const int nsrc = w.q1 - w.q0;
         for (int s2 = nsrc >= 2 ? nsrc - 2 : 0; s2 < nsrc; ++s2) fold(s2 & 1);
