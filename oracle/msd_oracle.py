@@ -158,6 +158,36 @@ def rhs_planewave(O, a, bc, k, N, betas) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
+def pointsource_coefficients(O, a, k, N, source) -> np.ndarray:
+    """Point-source proposition of section 4.3: for u_inc = G(x, s) =
+    (i/4) H_0(k |x - s|) the trace coefficients are U^p_m = d'^p_m J_m(k a_p)
+    with d'^p_m = (i pi a_p / 2) H_m(k r_p(s)) exp(-i m theta_p(s)) / sqrt(2 pi a_p)
+    = (i/4) sqrt(2 pi a_p) H_m(k r_p(s)) exp(-i m theta_p(s)), (r_p, theta_p) the
+    polar coordinates of s - O_p (Graf's addition theorem, |s - O_p| > a_p).
+    Returns [M, 2N+1]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    s = np.asarray(source, dtype=np.float64)
+    m = modes(N)[None, :]
+    d = s[None, :] - O
+    r = np.hypot(d[:, 0], d[:, 1])
+    th = np.arctan2(d[:, 1], d[:, 0])
+    return (0.25j * np.sqrt(2 * np.pi * a)[:, None] * special.hankel1(m, k * r[:, None])
+            * np.exp(-1j * m * th[:, None]))
+
+
+def rhs_pointsource(O, a, bc, k, N, sources) -> np.ndarray:
+    """b = -U for point sources (one column per source s_r, [R, 2]):
+    Dirichlet rows U^p_m = d'^p_m J_m(k a_p), Neumann rows k d'^p_m J_m'(k a_p)."""
+    J, dJ, _, _ = bessel_diagonals(a, k, N)
+    cols = []
+    for src in np.atleast_2d(np.asarray(sources, dtype=np.float64)):
+        d = pointsource_coefficients(O, a, k, N, src)
+        U = np.where(np.asarray(bc)[:, None] == DIRICHLET, d * J, k * d * dJ)
+        cols.append(-U.reshape(-1))
+    return np.stack(cols, axis=1)
+
+
 # --------------------------------------------------------------------------
 # Section 5: single-scattering preconditioner, direct and Krylov solves
 # --------------------------------------------------------------------------
@@ -316,14 +346,23 @@ def preconditioned_dense(O, a, bc, k, N) -> np.ndarray:
     return np.concatenate([preconditioned_block_row(O, a, bc, k, N, p) for p in range(len(a))], axis=0)
 
 
-def preconditioned_rhs(O, a, bc, k, N, betas) -> np.ndarray:
-    """P^-1 b with P the diagonal of the blocks A^pp (section 5)."""
+def preconditioner_diagonal(a, bc, k, N) -> np.ndarray:
+    """The diagonal of the blocks A^pp (section 5), [N_tot]."""
     a = np.asarray(a, dtype=np.float64)
     J, dJ, H, dH = bessel_diagonals(a, k, N)
-    diag = np.where(np.asarray(bc)[:, None] == DIRICHLET,
+    return np.where(np.asarray(bc)[:, None] == DIRICHLET,
                     0.5j * np.pi * a[:, None] * J * H,
                     0.5j * np.pi * k * a[:, None] * J * dH).reshape(-1)
-    return rhs_planewave(O, a, bc, k, N, betas) / diag[:, None]
+
+
+def preconditioned_rhs(O, a, bc, k, N, betas) -> np.ndarray:
+    """P^-1 b with P the diagonal of the blocks A^pp (section 5)."""
+    return rhs_planewave(O, a, bc, k, N, betas) / preconditioner_diagonal(a, bc, k, N)[:, None]
+
+
+def preconditioned_rhs_pointsource(O, a, bc, k, N, sources) -> np.ndarray:
+    """P^-1 b for point sources."""
+    return rhs_pointsource(O, a, bc, k, N, sources) / preconditioner_diagonal(a, bc, k, N)[:, None]
 
 
 # --------------------------------------------------------------------------
