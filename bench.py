@@ -330,6 +330,35 @@ def batched_timing(count: int = 16):
     pb.close()
 
 
+def nearfield_timing(n: int = 512):
+    """Scattered field (Prop. 4.3, kernel K8) of the 400-disk solution on an
+    n x n grid over [-55, 55]^2 (points inside disks return 0): CUDA events
+    around the C-ABI call with device buffers, after one untimed call."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cl = W.random_cluster_400()
+    pb = msd.Problem(cl)
+    res = pb.solve([cl.meta["beta"]], tol=1e-10, precision=msd.MSD_MIXED)
+    g = np.linspace(-55.0, 55.0, n)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    pts = torch.from_numpy(np.stack([X.ravel(), Y.ravel()], axis=1)).cuda()
+    u = torch.empty((n * n, 1), dtype=torch.complex128, device="cuda")
+    msd.msd_nearfield(pb.handle, 0, res.rho, 1, pts, u)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        msd.msd_nearfield(pb.handle, 0, res.rho, 1, pts, u)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    print(json.dumps({"workload": f"random400 solution, {n}x{n} grid over [-55,55]^2", "points": n * n,
+                      "disks": cl.M, "modes": cl.n, "ms": round(ms, 3),
+                      "point_disk_pairs_per_s": n * n * cl.M / (ms * 1e-3)}), flush=True)
+    pb.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +374,11 @@ def main():
                     help="print the timing (JSON lines) of the far-field misfit gradient instead")
     ap.add_argument("--batched", action="store_true",
                     help="print FP64 and mixed batched solve times (JSON lines) instead")
+    ap.add_argument("--nearfield", action="store_true",
+                    help="print the timing (JSON line) of the near field on a grid instead")
     args = ap.parse_args()
+    if args.nearfield:
+        return nearfield_timing()
     if args.batched:
         return batched_timing()
     if args.products:

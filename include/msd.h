@@ -231,6 +231,39 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
 msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int64_t* launches,
                              double* flops, double* bytes);
 
+/* Point sources (section 4.3, point-source proposition): the incident wave
+ * is the Green's function u_inc(x) = (i/4) H_0(k |x - s|) of a source s
+ * outside every disk; its trace coefficients are U^p_m = d'^p_m J_m(k a_p)
+ * (Dirichlet rows; k d'^p_m J_m'(k a_p) on Neumann rows) with
+ * d'^p_m = (i/4) sqrt(2 pi a_p) H_m(k b) e^{-i m phi}, (b, phi) the polar
+ * coordinates of s - O_p (kernel K5').
+ *   sources  [C][R][2] host: source (x, y) of column r of configuration c
+ * msd_rhs_pointsource: out (host or device, complex128 [N_tot][R]) = P^-1(-U),
+ *   the preconditioned right-hand side, as msd_rhs_planewave.
+ * msd_solve_pointsources: as msd_solve_planewaves with these right-hand sides.
+ * A source on or inside a disk gives non-finite coefficients
+ * (MSD_ERR_NONFINITE from the solve). */
+msd_status msd_rhs_pointsource(msd_problem* pb, int R, const double* sources, void* out);
+msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources, const msd_opts* opts,
+                                  void* rho_out, msd_stats* stats_host);
+
+/* Prop. 4.3: the scattered field at points x outside the disks,
+ *   u(x)[r] = sum_p sum_m rho^p_m[r] (i pi a_p / 2) J_m(k a_p) H_m(k r_p)
+ *             e^{i m theta_p} / sqrt(2 pi a_p),
+ * (r_p, theta_p) the polar coordinates of x - O_p, for configuration
+ * `config` of the problem (kernel K8).
+ *   rho     host or device, complex128 [N_tot][R] (all configurations)
+ *   P       number of points
+ *   points  host or device, double [P][2] (x, y)
+ *   u_out   host or device, complex128 [P][R]
+ * Points inside a disk of the configuration get 0 (the expansion holds
+ * outside the disks only).  Far point-disk pairs (k r_p > 20 and N <= k r_p)
+ * evaluate the Hankel functions in FP32 after an FP64 phase (relative error
+ * ~1e-6 of the field); near pairs in FP64.  Synchronises the stream when
+ * u_out is host memory. */
+msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, int64_t P, const double* points,
+                         void* u_out);
+
 /* Generators of the forward products (the Toeplitz storage of section 5).
  *   MSD_GEN_STREAMED (default): the 4N+1 values of every ordered pair are
  *     stored in HBM (complex128, plus complex64 for FP32 products) and read

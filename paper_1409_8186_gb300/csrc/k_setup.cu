@@ -294,6 +294,127 @@ __global__ void __launch_bounds__(kGenThreads)
     if (bad) atomicOr(flags, FLAG_RANGE32);
 }
 
+// ---------------------------------------------------------------- near field (Prop. 4.3)
+
+// W[row][r] = c^p_m rho^p_m[r] with c^p_m = (i pi a_p / 2) J_m(k a_p) / sqrt(2 pi a_p):
+// the weight of H_m(k r_p) e^{i m theta_p} in the single-layer potential.
+__global__ void k_nf_weights(const MsdConfig* __restrict__ cfg, int ci, const double* __restrict__ radius,
+                             const double2* __restrict__ J, const double2* __restrict__ rho, int R,
+                             double2* __restrict__ W) {
+    const MsdConfig c = cfg[ci];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)c.M * c.n * R) return;
+    const long long lrow = t / R;
+    const int p = (int)(lrow / c.n);
+    const long long row = c.row_off + lrow;
+    const double a = radius[c.disk_off + p];
+    const double s = 0.5 * M_PI * a / sqrt(2.0 * M_PI * a);
+    const double2 cm = make_double2(-s * J[row].y, s * J[row].x);  // i s J_m
+    W[row * R + (t % R)] = cmul(cm, rho[row * R + (t % R)]);
+}
+
+// u(x)[r] = sum_p sum_m W^p_m[r] H_m(k r_p) e^{i m theta_p}, x = points[t],
+// for x outside every disk (points inside a disk get 0).  One thread per
+// point, disks in order (the warp reads the same disk's weights together).
+// Far pairs (k r > 20, N <= k r): J_m, Y_m by FP32 forward recurrence from
+// Hankel's expansion after an FP64 phase; near pairs: FP64 (Miller).  The m
+// sum of one disk is formed in FP32 (far) or FP64 (near) and added to FP64
+// sums per point.  Columns r0 .. r0 + RC - 1 of R.
+template <int RC>
+__global__ void __launch_bounds__(128) k_nearfield(const MsdConfig* __restrict__ cfg, int ci,
+                                                   const double2* __restrict__ centre,
+                                                   const double* __restrict__ radius,
+                                                   const double2* __restrict__ W, int R, int r0, int ncol,
+                                                   const double2* __restrict__ pts, long long P,
+                                                   double2* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P) return;
+    const MsdConfig c = cfg[ci];
+    const int N = c.N, n = c.n;
+    const double2 x = pts[t];
+    double2 u[RC];
+#pragma unroll
+    for (int j = 0; j < RC; ++j) u[j] = make_double2(0.0, 0.0);
+    bool inside = false;
+    for (int p = 0; p < c.M && !inside; ++p) {
+        const double2 O = centre[c.disk_off + p];
+        const double dx = x.x - O.x, dy = x.y - O.y;
+        const double r = hypot(dx, dy);
+        if (r <= radius[c.disk_off + p]) {
+            inside = true;
+            break;
+        }
+        const double kr = c.k * r;
+        const double2* w = W + (c.row_off + (long long)p * n + N) * R + r0;  // mode m = 0
+        if (kr > 20.0 && (double)(N < 1 ? 1 : N) <= kr) {
+            double sxd, cxd;
+            sincos(kr, &sxd, &cxd);
+            const float xf = (float)kr;
+            float J0, J1, Y0, Y1;
+            bessel_asymptotic_f32(xf, 0, (float)sxd, (float)cxd, &J0, &Y0);
+            bessel_asymptotic_f32(xf, 1, (float)sxd, (float)cxd, &J1, &Y1);
+            const float2 e1 = make_float2((float)(dx / r), (float)(dy / r));
+            const float two_x = 2.0f / xf;
+            float2 e = make_float2(1.f, 0.f);
+            float2 acc[RC];
+#pragma unroll
+            for (int j = 0; j < RC; ++j) {
+                const double2 w0 = w[j];
+                acc[j] = make_float2((float)(w0.x * J0 - w0.y * Y0), (float)(w0.x * Y0 + w0.y * J0));
+            }
+            for (int m = 1; m <= N; ++m) {
+                e = make_float2(e.x * e1.x - e.y * e1.y, e.x * e1.y + e.y * e1.x);
+                // H_m e^{i m th} and H_{-m} e^{-i m th} = (-1)^m H_m e^{-i m th}
+                const float2 hp = make_float2(J1 * e.x - Y1 * e.y, J1 * e.y + Y1 * e.x);
+                float2 hm = make_float2(J1 * e.x + Y1 * e.y, Y1 * e.x - J1 * e.y);
+                if (m & 1) hm = make_float2(-hm.x, -hm.y);
+#pragma unroll
+                for (int j = 0; j < RC; ++j) {
+                    if (j >= ncol) break;
+                    const double2 wp = w[(long long)m * R + j], wm = w[-(long long)m * R + j];
+                    const float2 a = make_float2((float)wp.x, (float)wp.y), b = make_float2((float)wm.x, (float)wm.y);
+                    acc[j].x += a.x * hp.x - a.y * hp.y + b.x * hm.x - b.y * hm.y;
+                    acc[j].y += a.x * hp.y + a.y * hp.x + b.x * hm.y + b.y * hm.x;
+                }
+                const float f = m * two_x;
+                const float J2 = f * J1 - J0, Y2 = f * Y1 - Y0;
+                J0 = J1;
+                J1 = J2;
+                Y0 = Y1;
+                Y1 = Y2;
+            }
+#pragma unroll
+            for (int j = 0; j < RC; ++j) {
+                u[j].x += acc[j].x;
+                u[j].y += acc[j].y;
+            }
+        } else {
+            double J[MAXL], Y[MAXL];
+            bessel_jy(kr, N, J, Y);
+            const double2 e1 = make_double2(dx / r, dy / r);
+            double2 e = make_double2(1.0, 0.0);
+            for (int m = 0; m <= N; ++m) {
+                const double2 H = make_double2(J[m], Y[m]);
+                const double2 hp = cmul(H, e);
+                double2 hm = cmul(H, cconj(e));
+                if (m & 1) hm = make_double2(-hm.x, -hm.y);
+#pragma unroll
+                for (int j = 0; j < RC; ++j) {
+                    if (j >= ncol) break;
+                    u[j] = cadd(u[j], cmul(w[(long long)m * R + j], hp));
+                    if (m > 0) u[j] = cadd(u[j], cmul(w[-(long long)m * R + j], hm));
+                }
+                e = cmul(e, e1);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+        if (j >= ncol) break;
+        out[t * R + r0 + j] = inside ? make_double2(0.0, 0.0) : u[j];
+    }
+}
+
 }  // namespace
 
 void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, int nblocks, long long nitems,
@@ -352,6 +473,25 @@ void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int
     g_msd_launches += 1;
 }
 
+void launch_nearfield(const MsdConfig* d_cfg, int ci, const MsdConfig& h_cfg, const double2* d_centre,
+                      const double* d_radius, const double2* J, const double2* rho, int R, double2* W,
+                      const double2* d_pts, long long P, double2* out, cudaStream_t s) {
+    const long long nw = (long long)h_cfg.M * h_cfg.n * R;
+    k_nf_weights<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d_cfg, ci, d_radius, J, rho, R, W);
+    const unsigned blocks = (unsigned)((P + 127) / 128);
+    for (int r0 = 0; r0 < R; r0 += 8) {
+        const int nc = R - r0 < 8 ? R - r0 : 8;
+        if (nc <= 1)
+            k_nearfield<1><<<blocks, 128, 0, s>>>(d_cfg, ci, d_centre, d_radius, W, R, r0, nc, d_pts, P, out);
+        else if (nc <= 4)
+            k_nearfield<4><<<blocks, 128, 0, s>>>(d_cfg, ci, d_centre, d_radius, W, R, r0, nc, d_pts, P, out);
+        else
+            k_nearfield<8><<<blocks, 128, 0, s>>>(d_cfg, ci, d_centre, d_radius, W, R, r0, nc, d_pts, P, out);
+        g_msd_launches += 1;
+    }
+    g_msd_launches += 1;
+}
+
 // ---------------------------------------------------------------- K5
 
 // One thread per (disk, column r).  d^p_m = sqrt(2 pi a_p) e^{i k beta_hat . O_p}
@@ -382,6 +522,52 @@ __global__ void k_rhs_planewave(const MsdConfig* __restrict__ cfg, int Mtot,
         const long long row = row0 + (mm + c.N);
         out[row * R + r] = cmul(rhs_scale[row], dm);
     }
+}
+
+// Point sources (section 4.3, point-source proposition): u_inc = (i/4)
+// H_0(k |x - s|).  One thread per (disk, column r) with source s = src[cfg][r]:
+// d'_m = (i/4) sqrt(2 pi a_p) H_m(k b) e^{-i m phi}, (b, phi) the polar
+// coordinates of s - O_p (Graf, b > a_p), H_{-m} = (-1)^m H_m; out =
+// rhs_scale * d', i.e. P^-1(-U) or P^-1(-dU) as for plane waves.
+__global__ void k_rhs_pointsource(const MsdConfig* __restrict__ cfg, int Mtot, const int* __restrict__ disk_cfg,
+                                  const double2* __restrict__ centre, const double* __restrict__ radius,
+                                  const double2* __restrict__ rhs_scale, int R, const double2* __restrict__ src,
+                                  double2* out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Mtot * R) return;
+    const int d = (int)(idx / R), r = (int)(idx % R);
+    const int ci = disk_cfg[d];
+    const MsdConfig c = cfg[ci];
+    const double2 s = src[(long long)ci * R + r];
+    const double2 O = centre[d];
+    const double dx = s.x - O.x, dy = s.y - O.y;
+    const double b = hypot(dx, dy);
+    const double2 e1 = make_double2(dx / b, dy / b);  // e^{i phi}
+    double J[MAXL], Y[MAXL];
+    bessel_jy(c.k * b, c.N, J, Y);
+    const double amp = 0.25 * sqrt(2.0 * M_PI * radius[d]);
+    const long long row0 = c.row_off + (long long)(d - c.disk_off) * c.n + c.N;  // mode 0
+    double2 e = make_double2(1.0, 0.0);  // e^{i m phi}
+    for (int m = 0; m <= c.N; ++m) {
+        const double2 iH = make_double2(-amp * Y[m], amp * J[m]);  // (i/4) sqrt(2 pi a) H_m
+        const double2 dp = cmul(iH, cconj(e));                      // m: e^{-i m phi}
+        out[(row0 + m) * R + r] = cmul(rhs_scale[row0 + m], dp);
+        if (m > 0) {
+            double2 dm = cmul(iH, e);  // -m: (-1)^m H_m e^{+i m phi}
+            if (m & 1) dm = make_double2(-dm.x, -dm.y);
+            out[(row0 - m) * R + r] = cmul(rhs_scale[row0 - m], dm);
+        }
+        e = cmul(e, e1);
+    }
+}
+
+void launch_rhs_pointsource(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg, const double2* d_centre,
+                            const double* d_radius, const double2* rhs_scale, int R, const double2* d_src,
+                            double2* out, cudaStream_t s) {
+    const long long n = (long long)Mtot * R;
+    k_rhs_pointsource<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d_cfg, Mtot, d_disk_cfg, d_centre, d_radius,
+                                                                  rhs_scale, R, d_src, out);
+    g_msd_launches += 1;
 }
 
 void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,

@@ -190,7 +190,8 @@ struct msd_problem {
     int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags
     cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf xs, part, sbuf[24];
-    DBuf gbuf[9];  // gradient work buffers
+    DBuf gbuf[9];   // gradient work buffers
+    DBuf nfbuf[4];  // near-field buffers: rho, points, weights, output stage
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
     double offdiag_L = 0, offdiag_n2 = 0;
@@ -1279,6 +1280,7 @@ void msd_destroy(msd_problem* pb) {
     pb->part.release();
     for (auto& b : pb->sbuf) b.release();
     for (auto& b : pb->gbuf) b.release();
+    for (auto& b : pb->nfbuf) b.release();
     delete pb;
 }
 
@@ -1562,6 +1564,51 @@ msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T, const do
         OutStage o(pb, pb->sbuf[23], F_out, (size_t)pb->C * T * R * 16);
         launch_farfield(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_radius, pb->d_J, R, T, d_th, d_rho,
                         nullptr, (double2*)o.dev, pb->stream);
+        CK_LAUNCH();
+        o.finish();
+        return MSD_OK;
+    });
+}
+
+msd_status msd_rhs_pointsource(msd_problem* pb, int R, const double* sources_host, void* out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || !sources_host || !out) fail(MSD_ERR_ARG, "msd_rhs_pointsource: bad argument");
+        double2* d_src = (double2*)pb->sbuf[21].get((size_t)pb->C * R * 16);
+        CK(cudaMemcpyAsync(d_src, sources_host, (size_t)pb->C * R * 16, cudaMemcpyHostToDevice, pb->stream));
+        OutStage o(pb, pb->sbuf[20], out, (size_t)pb->Ntot * R * 16);
+        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale, R,
+                               d_src, (double2*)o.dev, pb->stream);
+        CK_LAUNCH();
+        o.finish();
+        return MSD_OK;
+    });
+}
+
+msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources_host, const msd_opts* opts,
+                                  void* rho_out, msd_stats* stats_host) {
+    return guarded([&]() -> msd_status {
+        if (!pb || R <= 0 || !sources_host || !rho_out) fail(MSD_ERR_ARG, "msd_solve_pointsources: bad argument");
+        double2* d_src = (double2*)pb->nfbuf[1].get((size_t)pb->C * R * 16);
+        CK(cudaMemcpyAsync(d_src, sources_host, (size_t)pb->C * R * 16, cudaMemcpyHostToDevice, pb->stream));
+        double2* b = (double2*)pb->nfbuf[2].get((size_t)pb->Ntot * R * 16);
+        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale, R,
+                               d_src, b, pb->stream);
+        CK_LAUNCH();
+        return solve_impl(pb, R, nullptr, opts, rho_out, stats_host, b);
+    });
+}
+
+msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, int64_t P, const double* points,
+                         void* u_out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !rho || R <= 0 || P <= 0 || !points || !u_out || config < 0 || config >= pb->C)
+            fail(MSD_ERR_ARG, "msd_nearfield: bad argument");
+        const double2* d_rho = (const double2*)stage_in(pb, pb->nfbuf[0], rho, (size_t)pb->Ntot * R * 16);
+        const double2* d_pts = (const double2*)stage_in(pb, pb->nfbuf[1], points, (size_t)P * 16);
+        double2* W = (double2*)pb->nfbuf[2].get((size_t)pb->Ntot * R * 16);
+        OutStage o(pb, pb->nfbuf[3], u_out, (size_t)P * R * 16);
+        launch_nearfield(pb->d_cfg, config, pb->cfg[config], pb->d_centre, pb->d_radius, pb->d_J, d_rho, R, W,
+                         d_pts, P, (double2*)o.dev, pb->stream);
         CK_LAUNCH();
         o.finish();
         return MSD_OK;

@@ -146,6 +146,17 @@ void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int
                            const double* d_radius, const int8_t* d_bc, const double2* J, const double2* H,
                            const double2* dH, const double2* u, const double2* v, double2* part, cudaStream_t s);
 
+// Near field (Prop. 4.3): u(points)[r] of configuration ci for densities rho
+// [N_tot][R]; W is a work buffer of N_tot * R complex128.
+void launch_nearfield(const MsdConfig* d_cfg, int ci, const MsdConfig& h_cfg, const double2* d_centre,
+                      const double* d_radius, const double2* J, const double2* rho, int R, double2* W,
+                      const double2* d_pts, long long P, double2* out, cudaStream_t s);
+
+// K5': preconditioned point-source right-hand sides, sources [C][R] (x, y).
+void launch_rhs_pointsource(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg, const double2* d_centre,
+                            const double* d_radius, const double2* rhs_scale, int R, const double2* d_src,
+                            double2* out, cudaStream_t s);
+
 // K5: preconditioned plane-wave right-hand sides.
 void launch_rhs_planewave(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
                           const double2* d_centre, const double* d_radius,

@@ -71,6 +71,9 @@ def _load():
         "msd_plan_info": (I, [P, I, I, P, P]),
         "msd_set_tile": (I, [P, I, I, I, I]),
         "msd_set_generator_mode": (I, [P, I, ctypes.c_int64]),
+        "msd_nearfield": (I, [P, I, P, I, ctypes.c_int64, P, P]),
+        "msd_rhs_pointsource": (I, [P, I, P, P]),
+        "msd_solve_pointsources": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
     }
@@ -86,7 +89,7 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_pair_generators", "msd_rhs_planewave", "msd_matvec", "msd_solve_planewaves",
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
-            "msd_set_generator_mode",
+            "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
             "msd_last_error")
 
 
@@ -228,6 +231,23 @@ def msd_set_generator_mode(h, mode: int, chunk_bytes: int = 0) -> None:
     _check(_lib.msd_set_generator_mode(h, mode, chunk_bytes))
 
 
+def msd_rhs_pointsource(h, R: int, sources, out) -> None:
+    src = np.ascontiguousarray(sources, dtype=np.float64)
+    _check(_lib.msd_rhs_pointsource(h, R, _ptr(src), _ptr(out)))
+
+
+def msd_solve_pointsources(h, R: int, sources, opts: msd_opts | None, rho_out, stats_out=None) -> int:
+    src = np.ascontiguousarray(sources, dtype=np.float64)
+    return _check(_lib.msd_solve_pointsources(h, R, _ptr(src), ctypes.byref(opts) if opts else None, _ptr(rho_out),
+                                              ctypes.addressof(stats_out) if stats_out is not None else None),
+                  allow_positive=True)
+
+
+def msd_nearfield(h, config: int, rho, R: int, points, u_out) -> None:
+    pts = points if hasattr(points, "data_ptr") else np.ascontiguousarray(points, dtype=np.float64)
+    _check(_lib.msd_nearfield(h, config, _ptr(rho), R, int(pts.shape[0]), _ptr(pts), _ptr(u_out)))
+
+
 def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
 
@@ -344,6 +364,42 @@ class Problem:
         F = torch.empty((self.C, len(th), R), dtype=torch.complex128, device="cuda") if out is None else out
         msd_farfield(self.handle, rho, R, th, F)
         return F
+
+    def _sources(self, sources):
+        src = np.asarray(sources, dtype=np.float64)
+        if src.ndim == 2:  # [R, 2] shared by every configuration
+            src = np.broadcast_to(src, (self.C,) + src.shape)
+        return np.ascontiguousarray(src)
+
+    def rhs_pointsource(self, sources):
+        import torch
+        src = self._sources(sources)
+        out = torch.empty((self.ntot, src.shape[1]), dtype=torch.complex128, device="cuda")
+        msd_rhs_pointsource(self.handle, src.shape[1], src, out)
+        return out
+
+    def solve_pointsources(self, sources, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64,
+                           out=None) -> SolveResult:
+        import torch
+        src = self._sources(sources)
+        R = src.shape[1]
+        o = msd_opts(tol, restart, maxit, 0, 0.0, precision, MSD_GEN_AUTO)
+        rho = torch.empty((self.ntot, R), dtype=torch.complex128, device="cuda") if out is None else out
+        stats = (msd_stats * (self.C * R))()
+        st = msd_solve_pointsources(self.handle, R, src, o, rho, stats)
+        return SolveResult(rho, st, np.array([s.flag for s in stats]), np.array([s.iters for s in stats]),
+                           np.array([s.refine_steps for s in stats]), np.array([s.relres for s in stats]),
+                           np.array([s.true_relres for s in stats]), float(stats[0].solve_ms) if len(stats) else 0.0)
+
+    def nearfield(self, rho, points, config: int = 0, out=None):
+        """Scattered field at points [P, 2] outside the disks of `config`
+        (complex128 [P, R] on the device; 0 inside a disk)."""
+        import torch
+        R = rho.shape[1]
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        u = torch.empty((pts.shape[0], R), dtype=torch.complex128, device="cuda") if out is None else out
+        msd_nearfield(self.handle, config, rho, R, pts, u)
+        return u
 
     def update_geometry(self, centres=None, radii=None, k=None):
         msd_update_geometry(self.handle, centres, radii, k)
