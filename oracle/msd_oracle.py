@@ -26,7 +26,11 @@ Readings of the paper taken here:
     (section 5), applied on the left; GMRES starts from x0 = 0 and measures
     relres = ||P^-1 (b - A x)|| / ||P^-1 b||;
   * far field: the single-layer coefficient vector of section 4.4 (the a_L
-    formula); a_M is not used.
+    formula); a_M is not used;
+  * time reversal (section 7): the mirror angles are alpha_j = 2 pi j /
+    n_alpha from 0, the far field of incidence alpha_j is measured at
+    alpha_i + pi (row i of F), and T = conj(F)^T F carries no quadrature
+    weight h_alpha (as printed; a weight only scales the eigenvalues).
 """
 from __future__ import annotations
 
@@ -417,6 +421,30 @@ def farfield(O, a, k, N, rho, thetas) -> np.ndarray:
         rho = rho[:, None]
     C = np.stack([farfield_coefficients(O, a, k, N, t) for t in np.atleast_1d(thetas)])
     return C @ rho
+
+
+def dort_far_field_matrix(O, a, bc, k, N, n_alpha):
+    """Section 7 (Example III, far-field time reversal): the mirror emits the
+    plane waves of incidence alpha_j = 2 pi j / n_alpha (j = 0..n_alpha-1)
+    and measures the far field in the opposite directions alpha_i + pi.
+    Column j of F holds that measured far field for incidence alpha_j:
+    F[i, j] = a_L(alpha_i + pi; alpha_j) (section 4.4), densities from the
+    LU solve of the section 5 system.  Returns (alphas, F [n_alpha, n_alpha])."""
+    alphas = 2.0 * np.pi * np.arange(n_alpha) / n_alpha
+    rho, _ = solve(O, a, bc, k, N, alphas, method="lu")
+    return alphas, farfield(O, a, k, N, rho, alphas + np.pi)
+
+
+def time_reversal_matrix(F) -> np.ndarray:
+    """Section 7: T = conj(F)^T F (Hermitian, positive semi-definite)."""
+    F = np.asarray(F)
+    return F.conj().T @ F
+
+
+def dort_eigenvalues(T) -> np.ndarray:
+    """Section 7: the eigenvalues of T (LAPACK Hermitian solver), largest
+    first."""
+    return np.linalg.eigvalsh(T)[::-1]
 
 
 def rcs(F) -> np.ndarray:

@@ -171,6 +171,15 @@ def lattice_4000(seed: int = 5, M: int = 4000) -> Cluster:
     return Cluster(sites, np.full(M, 0.3), np.zeros(M, np.int8), 5.0, 15, f"lattice{M}_k5")
 
 
+def dort_three_disks(bc: int = DIRICHLET) -> Cluster:
+    """Three small, well separated disks of the time-reversal example
+    (section 7): centres (0, 20), (10, -10), (-10, -20), radii 0.02, 0.01,
+    0.005, k = 2*pi (k a <= 0.126), N = 4, one boundary condition for all."""
+    O = np.array([[0.0, 20.0], [10.0, -10.0], [-10.0, -20.0]])
+    a = np.array([0.02, 0.01, 0.005])
+    return Cluster(O, a, np.full(3, bc, np.int8), 2.0 * np.pi, 4, "dort3")
+
+
 def small_mixed(seed: int = 11, M: int = 6, N: int = 10, k: float = 2.3,
                 half_side: float = 8.0) -> Cluster:
     """Small mixed Dirichlet/Neumann cluster for unit tests."""
