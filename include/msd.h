@@ -264,6 +264,39 @@ msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources,
 msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, int64_t P, const double* points,
                          void* u_out);
 
+/* Time reversal, DORT (section 7, far-field mirror): for every
+ * configuration the mirror emits the plane waves of incidence
+ * alpha_j = 2 pi j / n_alpha (j = 0..n_alpha-1) and measures the far field
+ * a_L of section 4.4 in the opposite directions alpha_i + pi.  With
+ *   F[i][j] = a_L(alpha_i + pi; alpha_j)   (densities from one batched solve
+ *             of the section 5 system with n_alpha right-hand sides)
+ * the time-reversal matrix is T = conj(F)^T F (Hermitian, positive
+ * semi-definite) and eig holds its eigenvalues, largest first (Householder
+ * tridiagonalisation and Sturm bisection on the device, absolute error a
+ * small multiple of 1e-16 ||T||).  No quadrature weight h_alpha is applied.
+ *   n_alpha  1..MSD_MAX_DORT mirror angles
+ *   opts     solver options of the batched solve (NULL: defaults)
+ *   F_out    NULL or host/device complex128 [C][n_alpha][n_alpha]
+ *   T_out    NULL or host/device complex128 [C][n_alpha][n_alpha]
+ *   eig_out  host or device double [C][n_alpha]
+ *   stats_host  NULL or [C*n_alpha] (system c*n_alpha + j)
+ * Returns the status of the solve (MSD_NOT_CONVERGED / MSD_STAGNATED still
+ * write every output).  Synchronises the stream. */
+#define MSD_MAX_DORT 2048
+msd_status msd_dort(msd_problem* pb, int n_alpha, const msd_opts* opts, void* F_out, void* T_out, void* eig_out,
+                    msd_stats* stats_host);
+
+/* The second half of msd_dort for far-field matrices the caller supplies
+ * (computed elsewhere or measured by a mirror): T = conj(F)^T F and its
+ * eigenvalues, largest first, for each of the problem's C configurations
+ * (only the problem's stream and work buffers are used).
+ *   F        host or device complex128 [C][n_alpha][n_alpha], row i the
+ *            receiving direction, column j the emitting one
+ *   T_out    NULL or host/device complex128 [C][n_alpha][n_alpha]
+ *   eig_out  host or device double [C][n_alpha]
+ * Synchronises the stream. */
+msd_status msd_dort_eigen(msd_problem* pb, int n_alpha, const void* F, void* T_out, void* eig_out);
+
 /* Generators of the forward products (the Toeplitz storage of section 5).
  *   MSD_GEN_STREAMED (default): the 4N+1 values of every ordered pair are
  *     stored in HBM (complex128, plus complex64 for FP32 products) and read

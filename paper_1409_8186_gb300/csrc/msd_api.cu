@@ -192,6 +192,7 @@ struct msd_problem {
     DBuf xs, part, sbuf[24];
     DBuf gbuf[9];   // gradient work buffers
     DBuf nfbuf[4];  // near-field buffers: rho, points, weights, output stage
+    DBuf dortbuf[6];  // time reversal: rho, angles, F, T, eigenvalues, eigen work
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
     double offdiag_L = 0, offdiag_n2 = 0;
@@ -1281,6 +1282,7 @@ void msd_destroy(msd_problem* pb) {
     for (auto& b : pb->sbuf) b.release();
     for (auto& b : pb->gbuf) b.release();
     for (auto& b : pb->nfbuf) b.release();
+    for (auto& b : pb->dortbuf) b.release();
     delete pb;
 }
 
@@ -1611,6 +1613,77 @@ msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, in
                          d_pts, P, (double2*)o.dev, pb->stream);
         CK_LAUNCH();
         o.finish();
+        return MSD_OK;
+    });
+}
+
+}  // extern "C"
+
+namespace {
+
+// T = conj(F)^T F and its eigenvalues for pb->C far-field matrices F (device,
+// [C][n][n]); outputs to caller buffers (host or device, T_out may be NULL).
+void dort_eigen(msd_problem* pb, int n, const double2* F, void* T_out, void* eig_out) {
+    cudaStream_t s = pb->stream;
+    const size_t nn = (size_t)pb->C * n * n;
+    double2* T = (double2*)pb->dortbuf[3].get(nn * 16);
+    double* eig = (double*)pb->dortbuf[4].get((size_t)pb->C * n * 8);
+    void* work = pb->dortbuf[5].get(dort_work_bytes(pb->C, n));
+    CK(dort_set_smem_limits(n));
+    launch_dort(pb->C, n, F, T, work, eig, s);
+    CK_LAUNCH();
+    auto out = [&](void* dst, const void* src, size_t bytes) {
+        if (dst)
+            CK(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               s));
+    };
+    out(T_out, T, nn * 16);
+    out(eig_out, eig, (size_t)pb->C * n * 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+msd_status msd_dort(msd_problem* pb, int n_alpha, const msd_opts* opts, void* F_out, void* T_out, void* eig_out,
+                    msd_stats* stats_host) {
+    return guarded([&]() -> msd_status {
+        if (!pb || n_alpha <= 0 || n_alpha > MSD_MAX_DORT || !eig_out) fail(MSD_ERR_ARG, "msd_dort: bad argument");
+        const int n = n_alpha, C = pb->C;
+        const double pi = 3.14159265358979323846;
+        std::vector<double> betas((size_t)C * n), thetas(n);
+        for (int j = 0; j < n; ++j) {
+            const double a = 2.0 * pi * j / n;
+            thetas[j] = a + pi;  // measured opposite to the emitting direction
+            for (int c = 0; c < C; ++c) betas[(size_t)c * n + j] = a;
+        }
+        cudaStream_t s = pb->stream;
+        const size_t nn = (size_t)C * n * n;
+        double2* rho = (double2*)pb->dortbuf[0].get((size_t)pb->Ntot * n * 16);
+        const msd_status st = solve_impl(pb, n, betas.data(), opts, rho, stats_host);
+        double* d_th = (double*)pb->dortbuf[1].get((size_t)n * 8);
+        CK(cudaMemcpyAsync(d_th, thetas.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        double2* F = (double2*)pb->dortbuf[2].get(nn * 16);
+        launch_farfield(pb->d_cfg, C, pb->cfg.data(), pb->d_centre, pb->d_radius, pb->d_J, n, n, d_th, rho, nullptr,
+                        F, s);
+        CK_LAUNCH();
+        if (F_out)
+            CK(cudaMemcpyAsync(F_out, F, nn * 16,
+                               is_device_ptr(F_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        dort_eigen(pb, n, F, T_out, eig_out);
+        CK(cudaStreamSynchronize(s));
+        return st;
+    });
+}
+
+msd_status msd_dort_eigen(msd_problem* pb, int n_alpha, const void* F, void* T_out, void* eig_out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || n_alpha <= 0 || n_alpha > MSD_MAX_DORT || !F || !eig_out)
+            fail(MSD_ERR_ARG, "msd_dort_eigen: bad argument");
+        const size_t nn = (size_t)pb->C * n_alpha * n_alpha;
+        const double2* d_F = (const double2*)stage_in(pb, pb->dortbuf[2], F, nn * 16);
+        dort_eigen(pb, n_alpha, d_F, T_out, eig_out);
+        CK(cudaStreamSynchronize(pb->stream));
         return MSD_OK;
     });
 }

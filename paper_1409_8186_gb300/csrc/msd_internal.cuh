@@ -176,6 +176,14 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
                        const MatvecChoice* ch = nullptr);
 
 // K6: far field.
+// Time reversal (section 7): T = conj(F)^T F for C far-field matrices
+// F [C][n][n] and the eigenvalues of every T, largest first (eig [C][n]).
+// work: dort_work_bytes(C, n) bytes.  dort_set_smem_limits(n) once before
+// the first launch with that n.
+size_t dort_work_bytes(int C, int n);
+cudaError_t dort_set_smem_limits(int n);
+void launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, cudaStream_t s);
+
 void launch_farfield(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
                      const double2* d_centre, const double* d_radius, const double2* J,
                      int R, int T, const double* d_thetas, const double2* rho,

@@ -24,6 +24,7 @@ MSD_DIRICHLET, MSD_NEUMANN = 0, 1
 MSD_FP64, MSD_MIXED, MSD_FP32 = 0, 1, 2
 MSD_GEN_AUTO, MSD_GEN_STREAMED, MSD_GEN_RECOMPUTE = 0, 1, 2
 MSD_MAX_N = 63
+MSD_MAX_DORT = 2048
 
 STATUS_NAMES = {0: "MSD_OK", 1: "MSD_NOT_CONVERGED", 3: "MSD_STAGNATED", -1: "MSD_ERR_ARG",
                 -2: "MSD_ERR_OVERLAP", -3: "MSD_ERR_CUDA", -4: "MSD_ERR_OOM",
@@ -74,6 +75,8 @@ def _load():
         "msd_nearfield": (I, [P, I, P, I, ctypes.c_int64, P, P]),
         "msd_rhs_pointsource": (I, [P, I, P, P]),
         "msd_solve_pointsources": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P]),
+        "msd_dort": (I, [P, I, ctypes.POINTER(msd_opts), P, P, P, P]),
+        "msd_dort_eigen": (I, [P, I, P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
     }
@@ -90,7 +93,7 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
-            "msd_last_error")
+            "msd_dort", "msd_dort_eigen", "msd_last_error")
 
 
 def library_path() -> str:
@@ -248,6 +251,19 @@ def msd_nearfield(h, config: int, rho, R: int, points, u_out) -> None:
     _check(_lib.msd_nearfield(h, config, _ptr(rho), R, int(pts.shape[0]), _ptr(pts), _ptr(u_out)))
 
 
+def msd_dort(h, n_alpha: int, opts: msd_opts | None, F_out, T_out, eig_out, stats_out=None) -> int:
+    p = lambda a: _ptr(a) if a is not None else None  # noqa: E731
+    return _check(_lib.msd_dort(h, n_alpha, ctypes.byref(opts) if opts else None, p(F_out), p(T_out), _ptr(eig_out),
+                                ctypes.addressof(stats_out) if stats_out is not None else None),
+                  allow_positive=True)
+
+
+def msd_dort_eigen(h, n_alpha: int, F, T_out, eig_out) -> None:
+    if not hasattr(F, "data_ptr"):
+        F = np.ascontiguousarray(F, dtype=np.complex128)
+    _check(_lib.msd_dort_eigen(h, n_alpha, _ptr(F), _ptr(T_out) if T_out is not None else None, _ptr(eig_out)))
+
+
 def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
 
@@ -400,6 +416,30 @@ class Problem:
         u = torch.empty((pts.shape[0], R), dtype=torch.complex128, device="cuda") if out is None else out
         msd_nearfield(self.handle, config, rho, R, pts, u)
         return u
+
+    def dort(self, n_alpha: int, tol=1e-12, precision=MSD_FP64, restart=0, maxit=3000, want_F=True,
+             want_T=True):
+        """Time reversal (section 7): returns (eig [C, n_alpha] largest first,
+        F [C, n_alpha, n_alpha] or None, T [C, n_alpha, n_alpha] or None,
+        status), device tensors."""
+        import torch
+        o = msd_opts(tol, restart, maxit, 0, 0.0, precision, MSD_GEN_AUTO)
+        shape = (self.C, n_alpha, n_alpha)
+        F = torch.empty(shape, dtype=torch.complex128, device="cuda") if want_F else None
+        T = torch.empty(shape, dtype=torch.complex128, device="cuda") if want_T else None
+        eig = torch.empty((self.C, n_alpha), dtype=torch.float64, device="cuda")
+        st = msd_dort(self.handle, n_alpha, o, F, T, eig)
+        return eig, F, T, st
+
+    def dort_eigen(self, F, want_T=False):
+        """T = conj(F)^T F and its eigenvalues (largest first) for caller
+        far-field matrices F [C, n, n]; returns (eig, T or None)."""
+        import torch
+        n = F.shape[-1]
+        T = torch.empty((self.C, n, n), dtype=torch.complex128, device="cuda") if want_T else None
+        eig = torch.empty((self.C, n), dtype=torch.float64, device="cuda")
+        msd_dort_eigen(self.handle, n, F, T, eig)
+        return eig, T
 
     def update_geometry(self, centres=None, radii=None, k=None):
         msd_update_geometry(self.handle, centres, radii, k)
