@@ -359,6 +359,53 @@ def nearfield_timing(n: int = 512):
     pb.close()
 
 
+def dort_timing():
+    """Time reversal (section 7): the whole msd_dort call (batched solve of
+    n_alpha incidences to relres 1e-12, far field at the opposite angles,
+    T = conj(F)^T F, eigenvalues) and the eigen stage alone (msd_dort_eigen
+    on the same F), CUDA events after one untimed call.  Workloads: the
+    three small sound-soft disks of the example with 512 mirror angles; a
+    100-disk cluster (radii 0.5..1, k = 2) with 256 angles; the eigen stage
+    of random 1024 and 2048 matrices."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    scenes = [(W.dort_three_disks(0), 512, "three small sound-soft disks (example), 512 angles"),
+              (W.random_cluster(seed=21, M=100, half_side=20.0, rmin=0.5, rmax=1.0, gap=0.3, k=2.0, N=10),
+               256, "random100_k2 (M=100, N=10), 256 angles")]
+    for cl, n, name in scenes:
+        pb = msd.Problem(cl)
+        for prec, pname in ((msd.MSD_FP64, "fp64"), (msd.MSD_MIXED, "mixed")):
+            ms, (eig, F, _, st) = timed(lambda: pb.dort(n, precision=prec, want_T=False))
+            ms_e, _ = timed(lambda: pb.dort_eigen(F))
+            e = eig.cpu().numpy()[0]
+            print(json.dumps({"workload": name, "unknowns": int(pb.ntot), "n_alpha": n, "precision": pname,
+                              "dort_ms": round(ms, 3), "eigen_ms": round(ms_e, 3), "status": int(st),
+                              "significant": int((e > 1e-3 * e[0]).sum()),
+                              "top": [float(x) for x in e[:4]]}), flush=True)
+        pb.close()
+    pb = msd.Problem(W.four_disks())
+    rng = np.random.default_rng(0)
+    for n in (1024, 2048):
+        F = torch.from_numpy(rng.standard_normal((1, n, n)) + 1j * rng.standard_normal((1, n, n))).cuda()
+        ms_e, _ = timed(lambda: pb.dort_eigen(F), reps=2)
+        print(json.dumps({"workload": f"eigen stage, random {n} x {n} complex F", "n_alpha": n,
+                          "eigen_ms": round(ms_e, 3), "householder_launches": 2 * (n - 2)}), flush=True)
+    pb.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +423,11 @@ def main():
                     help="print FP64 and mixed batched solve times (JSON lines) instead")
     ap.add_argument("--nearfield", action="store_true",
                     help="print the timing (JSON line) of the near field on a grid instead")
+    ap.add_argument("--dort", action="store_true",
+                    help="print the timing (JSON lines) of the time-reversal matrix and its eigenvalues instead")
     args = ap.parse_args()
+    if args.dort:
+        return dort_timing()
     if args.nearfield:
         return nearfield_timing()
     if args.batched:

@@ -6,14 +6,17 @@
 // Hermitian tridiagonal matrix (n - 2 steps; step k maps column k below the
 // diagonal onto a multiple of e_1 with H = I - tau v v^H and applies
 // H B H = B - v w^H - w v^H to the trailing block B, p = tau B v,
-// w = p - (tau/2)(v^H p) v).  A diagonal unitary similarity makes the
-// off-diagonal entries real and non-negative (their moduli), and the
-// eigenvalues of that real symmetric tridiagonal matrix are found one per
-// thread by bisection on the Sturm count (the number of negative pivots of
-// the LDL^T factorisation of the shifted matrix is the number of
-// eigenvalues below the shift).  Every step runs over all configurations
-// at once (grid.y = configuration).
+// w = p - (tau/2)(v^H p) v), all steps in one persistent cooperative launch
+// with grid barriers between the two phases of a step.  A diagonal unitary
+// similarity makes the off-diagonal entries real and non-negative (their
+// moduli), and the eigenvalues of that real symmetric tridiagonal matrix
+// are bracketed by Sturm counts (the number of sign changes of the leading
+// principal minors of the shifted matrix is the number of eigenvalues below
+// the shift), one warp per eigenvalue with 32 shifts per round.  Every
+// kernel runs over all configurations at once.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "msd_internal.cuh"
 
@@ -43,209 +46,402 @@ __global__ void __launch_bounds__(kGramTile* kGramTile)
     if (i < n && j < n) T[((long long)c * n + i) * n + j] = s;
 }
 
-constexpr int kHhThreads = 256;
-constexpr int kHhRows = kHhThreads / 32;  // one warp per row
+constexpr int kTdThreads = 128;
+constexpr int kTdWarps = kTdThreads / 32;  // one warp per row of the trailing block
+constexpr long long kBarrierCycles = 2000000000LL;  // ~1 s at 2 GHz
 
-__device__ double block_sum_256(double v, double* red) {
+__device__ double block_sum_td(double v, double* red) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < kHhThreads / 32; ++w) s += red[w];
+    for (int w = 0; w < kTdWarps; ++w) s += red[w];
     __syncthreads();
     return s;
 }
 
-// Householder step k, part 1: every CTA builds v and tau from column k
-// (rows k+1..n-1, untouched by this step) and forms p = tau B v for its
-// rows of the trailing block B = A[k+1:, k+1:].  CTA 0 stores v, tau,
-// d_k = Re A[k][k] and e_k = ||A[k+1:, k]||.  Dynamic shared memory: the
-// m = n - k - 1 entries of v.
-__global__ void __launch_bounds__(kHhThreads)
-    k_dort_hh_mv(int n, int k, double2* __restrict__ Aall, double2* __restrict__ vall, double2* __restrict__ pall,
-                 double* __restrict__ tau_all, double* __restrict__ d_all, double* __restrict__ e_all) {
-    extern __shared__ double2 v_sh[];
-    __shared__ double red[kHhThreads / 32];
-    const int c = blockIdx.y, m = n - k - 1;
-    double2* A = Aall + (long long)c * n * n;
-    double nrm2 = 0.0;
-    for (int r = threadIdx.x; r < m; r += kHhThreads) {
-        const double2 x = A[(long long)(k + 1 + r) * n + k];
-        v_sh[r] = x;
-        nrm2 += cabs2(x);
-    }
-    nrm2 = block_sum_256(nrm2, red);
-    const double sigma = sqrt(nrm2);
-    const double2 x0 = A[(long long)(k + 1) * n + k];
-    const double ax0 = sqrt(cabs2(x0));
-    // v = x + e^{i arg x0} sigma e_1 maps x onto -e^{i arg x0} sigma e_1;
-    // ||v||^2 = 2 sigma (sigma + |x0|), tau = 2 / ||v||^2
-    const double tau = sigma > 0.0 ? 1.0 / (sigma * (sigma + ax0)) : 0.0;
-    if (threadIdx.x == 0 && sigma > 0.0) {
-        const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-        v_sh[0] = cadd(x0, cscale(ph, sigma));
+// Grid-wide barrier of a cooperative launch: the counter reaches
+// gridDim.x * epoch when every CTA has arrived at barrier number epoch.
+// The wait is bounded (~1 s of SM clock); on expiry *err is set, and once
+// it is set no CTA waits again (the results are then invalid and the host
+// reports the error).
+__device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned epoch, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        const unsigned target = gridDim.x * epoch;
+        if (!*(volatile int*)err) {
+            const long long t0 = clock64();
+            while (*(volatile unsigned*)counter < target) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
     }
     __syncthreads();
-    if (blockIdx.x == 0) {
-        for (int r = threadIdx.x; r < m; r += kHhThreads) vall[(long long)c * n + r] = v_sh[r];
-        if (threadIdx.x == 0) {
-            tau_all[c] = tau;
-            d_all[(long long)c * n + k] = A[(long long)k * n + k].x;
-            e_all[(long long)c * n + k] = sigma;
+}
+
+// B[r][j] - v_r conj(w_j) - w_r conj(v_j): one entry of H B H (8 FMAs).
+__device__ __forceinline__ double2 rank2(double2 b, double2 vr, double2 wr, double2 wj, double2 vj) {
+    double re = fma(-wr.y, vj.y, b.x);
+    re = fma(-wr.x, vj.x, re);
+    re = fma(-vr.y, wj.y, re);
+    re = fma(-vr.x, wj.x, re);
+    double im = fma(wr.x, vj.y, b.y);
+    im = fma(-wr.y, vj.x, im);
+    im = fma(vr.x, wj.y, im);
+    im = fma(-vr.y, wj.x, im);
+    return make_double2(re, im);
+}
+
+constexpr int kTdBatch = 8;  // row entries per lane whose loads are issued together
+
+// Householder tridiagonalisation of C Hermitian matrices A [C][n][n] in
+// place, one persistent cooperative launch, one grid barrier per step.
+// Row R of every matrix belongs to warp R mod (4 gridDim.x) for all steps.
+// Every CTA holds x_k = A[k+1:, k] (the column the reflector of step k
+// maps onto a multiple of e_1) in shared memory and derives v, tau from it
+// itself.  Step k, per configuration:
+//   1. p_r = tau (B v)_r for the warp's rows of B = A[k+1:, k+1:]
+//      (written to pbuf[k & 1]);  grid barrier;
+//   2. every CTA reads all of p, forms w = p - (tau/2)(v^H p) v, applies
+//      B <- B - v w^H - w v^H to its own rows (writing the new A[R][k+2] to
+//      colbuf[k & 1] as well) and computes x_{k+1} = (new B)[1:, 0] from
+//      the column written one step earlier and v, w.
+// pbuf and colbuf alternate between steps, so that a buffer is rewritten
+// only after every CTA has passed the barrier that follows its last read.
+// e_k = sigma_k = ||x_k|| goes to e_all; the diagonal entries are final in
+// A once their step is done.  Dynamic shared memory: x for two steps of
+// every configuration, w, and tau and ||x_k||^2 per configuration.
+__global__ void __launch_bounds__(kTdThreads)
+    k_dort_tridiag(int C, int n, double2* __restrict__ Aall, double2* __restrict__ pbuf,
+                   double2* __restrict__ colbuf, double* __restrict__ e_all, unsigned* __restrict__ bar,
+                   int* __restrict__ err) {
+    extern __shared__ double2 td_sh[];
+    double2* xs = td_sh;                    // [2][C][n]
+    double2* w_sh = td_sh + 2 * (size_t)C * n;  // [n]
+    double* tau_sh = (double*)(w_sh + n);   // [C]
+    double* nrm_sh = tau_sh + C;            // [C] ||x_k||^2
+    __shared__ double red[kTdWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kTdWarps + warp, GW = gridDim.x * kTdWarps;
+    auto X = [&](int par, int c) { return xs + ((size_t)par * C + c) * n; };
+    // x_0 = A[1:, 0]; the column 1 below row 1 (needed by step 0) in X(1, c)
+    for (int c = 0; c < C; ++c) {
+        const double2* A = Aall + (long long)c * n * n;
+        double nrm2 = 0.0;
+        for (int r = threadIdx.x; r < n - 1; r += kTdThreads) {
+            const double2 a = A[(long long)(1 + r) * n];
+            X(0, c)[r] = a;
+            nrm2 += cabs2(a);
+        }
+        for (int r = threadIdx.x; r < n - 2; r += kTdThreads) X(1, c)[r] = A[(long long)(2 + r) * n + 1];
+        nrm2 = block_sum_td(nrm2, red);
+        if (threadIdx.x == 0) nrm_sh[c] = nrm2;
+    }
+    __syncthreads();
+    unsigned epoch = 0;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1, par = k & 1;
+        const int R0 = k + 1 + ((gw - (k + 1)) % GW + GW) % GW;  // first own row >= k+1
+        for (int c = 0; c < C; ++c) {
+            double2* x = X(par, c);
+            const double sigma = sqrt(nrm_sh[c]);
+            const double2 x0 = x[0];
+            const double ax0 = sqrt(cabs2(x0));
+            // v = x + e^{i arg x0} sigma e_1 maps x onto -e^{i arg x0} sigma e_1;
+            // ||v||^2 = 2 sigma (sigma + |x0|), tau = 2 / ||v||^2
+            const double tau = sigma > 0.0 ? 1.0 / (sigma * (sigma + ax0)) : 0.0;
+            __syncthreads();  // every thread has read x[0]
+            if (threadIdx.x == 0) {
+                if (sigma > 0.0) {
+                    const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+                    x[0] = cadd(x0, cscale(ph, sigma));  // x now holds v
+                }
+                tau_sh[c] = tau;
+                if (blockIdx.x == 0) e_all[(long long)c * n + k] = sigma;
+            }
+            __syncthreads();
+            const double2* A = Aall + (long long)c * n * n;
+            for (int R = R0; R < n; R += GW) {
+                const double2* row = A + (long long)R * n + (k + 1);
+                double2 s = make_double2(0.0, 0.0);
+                for (int j0 = lane; j0 < m; j0 += 32 * kTdBatch) {
+                    double2 a[kTdBatch];
+#pragma unroll
+                    for (int u = 0; u < kTdBatch; ++u) {
+                        const int j = j0 + 32 * u;
+                        a[u] = j < m ? row[j] : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTdBatch; ++u) {
+                        const int j = j0 + 32 * u;
+                        if (j < m) cfma(s, a[u], x[j]);
+                    }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+                    s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+                }
+                if (lane == 0) pbuf[((size_t)par * C + c) * n + (R - k - 1)] = cscale(s, tau);
+            }
+        }
+        grid_barrier(bar, ++epoch, err);
+        for (int c = 0; c < C; ++c) {
+            const double2* v = X(par, c);
+            const double tau = tau_sh[c];
+            const double2* p = pbuf + ((size_t)par * C + c) * n;
+            double vp_re = 0.0;  // Re(v^H p); v^H p = tau v^H B v is real
+            for (int r = threadIdx.x; r < m; r += kTdThreads) {
+                const double2 pr = p[r], vr = v[r];
+                w_sh[r] = pr;
+                vp_re += vr.x * pr.x + vr.y * pr.y;
+            }
+            vp_re = block_sum_td(vp_re, red);
+            const double K = 0.5 * tau * vp_re;
+            for (int r = threadIdx.x; r < m; r += kTdThreads) w_sh[r] = csub(w_sh[r], cscale(v[r], K));
+            __syncthreads();
+            double2* A = Aall + (long long)c * n * n;
+            double2* col_out = colbuf + ((size_t)par * C + c) * n;
+            for (int R = R0; R < n; R += GW) {
+                const int r = R - k - 1;
+                const double2 vr = v[r], wr = w_sh[r];
+                double2* row = A + (long long)R * n + (k + 1);
+                for (int j0 = lane; j0 < m; j0 += 32 * kTdBatch) {
+                    double2 a[kTdBatch];
+#pragma unroll
+                    for (int u = 0; u < kTdBatch; ++u) {
+                        const int j = j0 + 32 * u;
+                        a[u] = j < m ? row[j] : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTdBatch; ++u) {
+                        const int j = j0 + 32 * u;
+                        if (j < m) {
+                            const double2 b = rank2(a[u], vr, wr, w_sh[j], v[j]);
+                            row[j] = b;
+                            if (j == 1) col_out[R] = b;
+                        }
+                    }
+                }
+            }
+            // x_{k+1}[i] = new A[k+2+i][k+1], from the column written by the
+            // previous step (step 0: the copy taken before the first step)
+            double2* xn = X(par ^ 1, c);
+            const double2* col_in = colbuf + ((size_t)(par ^ 1) * C + c) * n;
+            const double2 w0 = w_sh[0], v0 = v[0];
+            double nrm2 = 0.0;  // ||x_{k+1}||^2 for the next step
+            for (int i = threadIdx.x; i < m - 1; i += kTdThreads) {
+                const double2 old = k == 0 ? xn[i] : col_in[k + 2 + i];
+                const double2 xi = rank2(old, v[i + 1], w_sh[i + 1], w0, v0);
+                xn[i] = xi;
+                nrm2 += cabs2(xi);
+            }
+            nrm2 = block_sum_td(nrm2, red);
+            if (threadIdx.x == 0) nrm_sh[c] = nrm2;
+            __syncthreads();
         }
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kHhRows + warp;
-    if (r >= m) return;
-    const double2* row = A + (long long)(k + 1 + r) * n + (k + 1);
-    double2 s = make_double2(0.0, 0.0);
-    for (int j = lane; j < m; j += 32) s = cadd(s, cmul(row[j], v_sh[j]));
-    for (int off = 16; off > 0; off >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
-    }
-    if (lane == 0) pall[(long long)c * n + r] = cscale(s, tau);
 }
 
-// Householder step k, part 2: w = p - (tau/2)(v^H p) v (every CTA), then
-// B <- B - v w^H - w v^H on the CTA's rows.  Dynamic shared memory: v and w.
-__global__ void __launch_bounds__(kHhThreads)
-    k_dort_hh_update(int n, int k, double2* __restrict__ Aall, const double2* __restrict__ vall,
-                     const double2* __restrict__ pall, const double* __restrict__ tau_all) {
-    extern __shared__ double2 vw_sh[];
-    __shared__ double red[kHhThreads / 32];
-    const int c = blockIdx.y, m = n - k - 1;
-    const double tau = tau_all[c];
-    if (tau == 0.0) return;  // column already reduced: H = I
-    double2* v_sh = vw_sh;
-    double2* w_sh = vw_sh + m;
-    double vp_re = 0.0;  // Re(v^H p); v^H p = tau v^H B v is real
-    for (int r = threadIdx.x; r < m; r += kHhThreads) {
-        const double2 v = vall[(long long)c * n + r], p = pall[(long long)c * n + r];
-        v_sh[r] = v;
-        w_sh[r] = p;
-        vp_re += v.x * p.x + v.y * p.y;
-    }
-    vp_re = block_sum_256(vp_re, red);
-    const double K = 0.5 * tau * vp_re;
-    for (int r = threadIdx.x; r < m; r += kHhThreads) w_sh[r] = csub(w_sh[r], cscale(v_sh[r], K));
-    __syncthreads();
-    double2* A = Aall + (long long)c * n * n;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kHhRows + warp;
-    if (r >= m) return;
-    const double2 vr = v_sh[r], wr = w_sh[r];
-    double2* row = A + (long long)(k + 1 + r) * n + (k + 1);
-    for (int j = lane; j < m; j += 32)
-        row[j] = csub(row[j], cadd(cmul(vr, cconj(w_sh[j])), cmul(wr, cconj(v_sh[j]))));
-}
+__device__ __forceinline__ int sign_bit(double x) { return (int)((unsigned)__double2hiint(x) >> 31); }
+__device__ __forceinline__ int biased_exponent(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
 
-// Sturm count: the number of eigenvalues of the symmetric tridiagonal
-// matrix (d, e) below x.
-__device__ int sturm_count(int n, const double* d, const double* e2, double x, double pivmin) {
-    int cnt = 0;
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++cnt;
+// Sturm count of the symmetric tridiagonal matrix (d, e) at x: the number
+// of sign changes of p_{-1} = 1, p_0 = d_0 - x,
+// p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, the leading principal minors
+// of the shifted matrix, which equals the number of eigenvalues below x.
+// No division: the pair (p_{i-1}, p_i) is rescaled by a power of two when
+// p_i leaves [2^-511, 2^512]; a zero p_i counts with the sign opposite to
+// p_{i-1} (it is replaced by -2^-300 p_{i-1}).
+__device__ int sturm_count(int n, const double* d, const double* e2, double x) {
+    double pm = 1.0, p = d[0] - x;
+    if (biased_exponent(p) == 0) p = -0x1p-300;
+    int cnt = sign_bit(p);
     for (int i = 1; i < n; ++i) {
-        q = (d[i] - x) - e2[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        if (q < 0.0) ++cnt;
+        double q = fma(d[i] - x, p, -e2[i - 1] * pm);
+        int ex = biased_exponent(q);
+        if (ex == 0) {  // zero (or below the normal range)
+            q = -0x1p-300 * p;
+            ex = biased_exponent(q);
+        }
+        cnt += sign_bit(q) ^ sign_bit(p);
+        if (ex > 1023 + 512 || ex < 1023 - 511) {
+            const double f = __hiloint2double((2046 - ex) << 20, 0);  // 2^-(ex - 1023)
+            q *= f;
+            p *= f;
+        }
+        pm = p;
+        p = q;
     }
     return cnt;
 }
 
-// Eigenvalue i (largest first) of configuration blockIdx.y by bisection.
-// The last two diagonal entries and the last off-diagonal one are read
-// from the reduced matrix; the others come from the Householder steps.
+constexpr int kBsWarps = 4;  // eigenvalues per CTA
+
+// Eigenvalue i (largest first) of configuration blockIdx.y, one warp per
+// eigenvalue: 32-point multisection of its bracket [lo, hi]
+// (count(lo) <= j < count(hi), j = n - 1 - i its ascending index), each
+// lane evaluating the Sturm count at one interior point, until the bracket
+// is a few ulps wide or 2^-60 of the norm bound wide.  The matrix is scaled
+// by a power of two so that its Gershgorin interval lies in [-1, 1].  The
+// diagonal and the last off-diagonal entry are read from the reduced
+// matrix; the other off-diagonal moduli come from the Householder steps.
 // Dynamic shared memory: d [n] and e^2 [n].
-__global__ void k_dort_bisect(int n, const double2* __restrict__ Aall, const double* __restrict__ d_all,
-                              const double* __restrict__ e_all, double* __restrict__ eig) {
+__global__ void __launch_bounds__(kBsWarps * 32)
+    k_dort_bisect(int n, const double2* __restrict__ Aall, const double* __restrict__ e_all,
+                  double* __restrict__ eig) {
     extern __shared__ double de_sh[];
     double* d = de_sh;
     double* e2 = de_sh + n;
-    __shared__ double lo_sh, hi_sh, pivmin_sh;
+    __shared__ double lo_w[kBsWarps], hi_w[kBsWarps];
+    __shared__ double lo_sh, hi_sh;
     const int c = blockIdx.y;
     const double2* A = Aall + (long long)c * n * n;
     const int nh = n > 2 ? n - 2 : 0;  // entries produced by the Householder steps
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        d[i] = i < nh ? d_all[(long long)c * n + i] : A[(long long)i * n + i].x;
-        if (i < n - 1) {
-            const double ei = i < nh ? e_all[(long long)c * n + i] : sqrt(cabs2(A[(long long)(i + 1) * n + i]));
-            e2[i] = ei * ei;
-        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double e_abs[2];
+    double lo = 1e308, hi = -1e308;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = A[(long long)i * n + i].x;
+    for (int i = threadIdx.x; i < n - 1; i += blockDim.x) {
+        const double ei = i < nh ? e_all[(long long)c * n + i] : sqrt(cabs2(A[(long long)(i + 1) * n + i]));
+        e2[i] = ei;  // |e_i| for now
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // Gershgorin interval and pivot floor
-        double lo = d[0], hi = d[0], emax2 = 1.0;
-        for (int i = 0; i < n; ++i) {
-            const double r = (i > 0 ? sqrt(e2[i - 1]) : 0.0) + (i < n - 1 ? sqrt(e2[i]) : 0.0);
-            lo = fmin(lo, d[i] - r);
-            hi = fmax(hi, d[i] + r);
-            if (i < n - 1) emax2 = fmax(emax2, e2[i]);
-        }
-        const double w = fmax(fabs(lo), fabs(hi));
-        lo_sh = lo - 4e-16 * w - 1e-300;
-        hi_sh = hi + 4e-16 * w + 1e-300;
-        pivmin_sh = 1e-290 * emax2;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // Gershgorin discs
+        e_abs[0] = i > 0 ? e2[i - 1] : 0.0;
+        e_abs[1] = i < n - 1 ? e2[i] : 0.0;
+        lo = fmin(lo, d[i] - e_abs[0] - e_abs[1]);
+        hi = fmax(hi, d[i] + e_abs[0] + e_abs[1]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (lane == 0) {
+        lo_w[warp] = lo;
+        hi_w[warp] = hi;
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBsWarps; ++w) {
+            lo = fmin(lo, lo_w[w]);
+            hi = fmax(hi, hi_w[w]);
+        }
+        lo_sh = lo;
+        hi_sh = hi;
+    }
+    __syncthreads();
+    const double bound = fmax(fabs(lo_sh), fabs(hi_sh));
+    const int i = blockIdx.x * kBsWarps + warp;
+    if (bound == 0.0) {  // zero matrix
+        if (i < n && lane == 0) eig[(long long)c * n + i] = 0.0;
+        return;
+    }
+    const int sc = ilogb(bound) + 1;  // 2^sc > bound
+    const double inv = ldexp(1.0, -sc);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        d[t] *= inv;
+        if (t < n - 1) e2[t] = (e2[t] * inv) * (e2[t] * inv);
+    }
+    __syncthreads();
     if (i >= n) return;
-    const int j = n - 1 - i;  // ascending index of the eigenvalue
-    double lo = lo_sh, hi = hi_sh;  // count(lo) <= j < count(hi)
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;  // interval at the last bit
-        if (sturm_count(n, d, e2, mid, pivmin_sh) <= j) lo = mid;
-        else hi = mid;
+    const int j = n - 1 - i;
+    lo = lo_sh * inv - 0x1p-50;
+    hi = hi_sh * inv + 0x1p-50;
+    for (int round = 0; round < 64; ++round) {
+        const double x = lo + (hi - lo) * ((double)(lane + 1) * (1.0 / 33.0));
+        const int cnt = sturm_count(n, d, e2, x);
+        const unsigned le = __ballot_sync(0xffffffffu, cnt <= j);
+        const int L = le ? 31 - __clz(le) : -1;  // highest lane with count <= j
+        const double xl = __shfl_sync(0xffffffffu, x, L < 0 ? 0 : L);
+        const double xh = __shfl_sync(0xffffffffu, x, L < 31 ? L + 1 : 31);
+        const double nlo = L >= 0 ? fmax(lo, xl) : lo;
+        const double nhi = L < 31 ? fmin(hi, xh) : hi;
+        if (nlo == lo && nhi == hi) break;  // the bracket cannot be split further
+        lo = nlo;
+        hi = nhi;
+        // converged: a few ulps of the eigenvalue, or 2^-60 of the scaled
+        // norm bound (below the tridiagonalisation's own error)
+        if (hi - lo <= fmax(0x1p-51 * fmax(fabs(lo), fabs(hi)), 0x1p-60)) break;
     }
-    eig[(long long)c * n + i] = 0.5 * (lo + hi);
+    if (lane == 0) eig[(long long)c * n + i] = ldexp(0.5 * (lo + hi), sc);
 }
 
 }  // namespace
 
 size_t dort_work_bytes(int C, int n) {
-    // T copy, v, p, tau, d, e
-    return (size_t)C * n * n * 16 + 2 * (size_t)C * n * 16 + (size_t)C * 8 + 2 * (size_t)C * n * 8;
+    // T copy, p and column buffers (two each), e, barrier counter and error flag
+    return (size_t)C * n * n * 16 + 4 * (size_t)C * n * 16 + (size_t)C * n * 8 + 16;
 }
 
-void launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, cudaStream_t s) {
+namespace {
+constexpr size_t kTdSmemMax = 220 * 1024;
+size_t tridiag_smem(int Cg, int n) { return (2 * (size_t)Cg * n + n) * 16 + (size_t)Cg * 16; }
+int tridiag_group(int C, int n) {
+    int g = (int)((kTdSmemMax / 16 - n) / (2 * (size_t)n + 1));
+    return std::max(1, std::min(C, g));
+}
+}  // namespace
+
+cudaError_t dort_set_smem_limits(int n) {
+    // the tridiagonalisation's shared memory: x of two steps per configuration, w, tau
+    return cudaFuncSetAttribute(k_dort_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTdSmemMax);
+}
+
+cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, int* err_host_flag,
+                        cudaStream_t s) {
     char* w = (char*)work;
     double2* A = (double2*)w;
     w += (size_t)C * n * n * 16;
-    double2* v = (double2*)w;
-    w += (size_t)C * n * 16;
-    double2* p = (double2*)w;
-    w += (size_t)C * n * 16;
-    double* tau = (double*)w;
-    w += (size_t)C * 8;
-    double* d = (double*)w;
-    w += (size_t)C * n * 8;
+    double2* pbuf = (double2*)w;  // [2][C][n]
+    w += 2 * (size_t)C * n * 16;
+    double2* colbuf = (double2*)w;  // [2][C][n]
+    w += 2 * (size_t)C * n * 16;
     double* e = (double*)w;
+    w += (size_t)C * n * 8;
+    unsigned* bar = (unsigned*)w;
+    int* err = (int*)(w + 4);
     const int tiles = (n + kGramTile - 1) / kGramTile;
     k_dort_gram<<<dim3(tiles, tiles, C), dim3(kGramTile, kGramTile), 0, s>>>(n, F, T);
-    cudaMemcpyAsync(A, T, (size_t)C * n * n * 16, cudaMemcpyDeviceToDevice, s);
-    long long launches = 1;
-    for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;
-        const dim3 grid((m + kHhRows - 1) / kHhRows, C);
-        k_dort_hh_mv<<<grid, kHhThreads, (size_t)m * 16, s>>>(n, k, A, v, p, tau, d, e);
-        k_dort_hh_update<<<grid, kHhThreads, (size_t)m * 32, s>>>(n, k, A, v, p, tau);
-        launches += 2;
+    cudaError_t ce = cudaMemcpyAsync(A, T, (size_t)C * n * n * 16, cudaMemcpyDeviceToDevice, s);
+    if (ce != cudaSuccess) return ce;
+    ce = cudaMemsetAsync(bar, 0, 8, s);
+    if (ce != cudaSuccess) return ce;
+    long long launches = 2;
+    if (n > 2) {
+        // persistent grid, every CTA co-resident (cooperative launch); the
+        // configurations in groups whose x buffers fit in shared memory
+        int dev = 0, sms = 0;
+        if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return ce;
+        if ((ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return ce;
+        const int G = tridiag_group(C, n);
+        for (int c0 = 0; c0 < C; c0 += G) {
+            int Cg = std::min(G, C - c0);
+            const size_t smem = tridiag_smem(Cg, n);
+            int per_sm = 0;
+            if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dort_tridiag, kTdThreads, smem)) !=
+                cudaSuccess)
+                return ce;
+            const int need = (n - 1 + kTdWarps - 1) / kTdWarps;
+            const int grid = std::max(1, std::min(need, per_sm * sms));
+            if (c0 > 0 && (ce = cudaMemsetAsync(bar, 0, 4, s)) != cudaSuccess) return ce;
+            double2* Ag = A + (size_t)c0 * n * n;
+            double* eg = e + (size_t)c0 * n;
+            void* args[] = {&Cg, (void*)&n, &Ag, &pbuf, &colbuf, &eg, &bar, &err};
+            ce = cudaLaunchCooperativeKernel((const void*)k_dort_tridiag, dim3(grid), dim3(kTdThreads), args, smem, s);
+            if (ce != cudaSuccess) return ce;
+            ++launches;
+        }
     }
-    k_dort_bisect<<<dim3((n + 31) / 32, C), 32, (size_t)n * 16, s>>>(n, A, d, e, eig);
-    g_msd_launches += launches + 1;
-}
-
-cudaError_t dort_set_smem_limits(int n) {
-    // dynamic shared memory above 48 KB needs an opt-in (n > 1536 for the update)
-    const int need = n * 32;
-    if (need <= 48 * 1024) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_dort_hh_update, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_dort_hh_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_dort_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    k_dort_bisect<<<dim3((n + kBsWarps - 1) / kBsWarps, C), kBsWarps * 32, (size_t)n * 16, s>>>(n, A, e, eig);
+    g_msd_launches += launches;
+    return cudaMemcpyAsync(err_host_flag, err, 4, cudaMemcpyDeviceToHost, s);
 }

@@ -187,7 +187,7 @@ struct msd_problem {
     std::vector<RowChunk> chunks_coarse;
     RowChunk* d_chunks_coarse = nullptr;
     int* d_cfg_chunk_off_coarse = nullptr;
-    int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags
+    int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags, [10] DORT barrier
     cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf xs, part, sbuf[24];
     DBuf gbuf[9];   // gradient work buffers
@@ -1630,7 +1630,7 @@ void dort_eigen(msd_problem* pb, int n, const double2* F, void* T_out, void* eig
     double* eig = (double*)pb->dortbuf[4].get((size_t)pb->C * n * 8);
     void* work = pb->dortbuf[5].get(dort_work_bytes(pb->C, n));
     CK(dort_set_smem_limits(n));
-    launch_dort(pb->C, n, F, T, work, eig, s);
+    CK(launch_dort(pb->C, n, F, T, work, eig, &pb->h_pinned[10], s));
     CK_LAUNCH();
     auto out = [&](void* dst, const void* src, size_t bytes) {
         if (dst)
@@ -1639,6 +1639,11 @@ void dort_eigen(msd_problem* pb, int n, const double2* F, void* T_out, void* eig
     };
     out(T_out, T, nn * 16);
     out(eig_out, eig, (size_t)pb->C * n * 8);
+}
+
+// After the stream reached dort_eigen's flag copy.
+void dort_check(msd_problem* pb) {
+    if (pb->h_pinned[10]) fail(MSD_ERR_CUDA, "msd_dort: a grid barrier of the tridiagonalisation timed out");
 }
 
 }  // namespace
@@ -1672,6 +1677,7 @@ msd_status msd_dort(msd_problem* pb, int n_alpha, const msd_opts* opts, void* F_
                                is_device_ptr(F_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         dort_eigen(pb, n, F, T_out, eig_out);
         CK(cudaStreamSynchronize(s));
+        dort_check(pb);
         return st;
     });
 }
@@ -1684,6 +1690,7 @@ msd_status msd_dort_eigen(msd_problem* pb, int n_alpha, const void* F, void* T_o
         const double2* d_F = (const double2*)stage_in(pb, pb->dortbuf[2], F, nn * 16);
         dort_eigen(pb, n_alpha, d_F, T_out, eig_out);
         CK(cudaStreamSynchronize(pb->stream));
+        dort_check(pb);
         return MSD_OK;
     });
 }

@@ -179,10 +179,12 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
 // Time reversal (section 7): T = conj(F)^T F for C far-field matrices
 // F [C][n][n] and the eigenvalues of every T, largest first (eig [C][n]).
 // work: dort_work_bytes(C, n) bytes.  dort_set_smem_limits(n) once before
-// the first launch with that n.
+// the first launch with that n.  *err_flag (host) receives, once the stream
+// reaches it, 1 if a grid-barrier wait of the tridiagonalisation expired.
 size_t dort_work_bytes(int C, int n);
 cudaError_t dort_set_smem_limits(int n);
-void launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, cudaStream_t s);
+cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, int* err_flag,
+                        cudaStream_t s);
 
 void launch_farfield(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
                      const double2* d_centre, const double* d_radius, const double2* J,
