@@ -27,6 +27,13 @@ Readings of the paper taken here:
     relres = ||P^-1 (b - A x)|| / ||P^-1 b||;
   * far field: the single-layer coefficient vector of section 4.4 (the a_L
     formula); a_M is not used;
+  * other integral equations (sections 3, 4.2, 5): a formulation is a
+    linear combination of I, L, M, N, D per boundary condition of the row
+    disk, a right-hand side -(w_U U + w_dU dU), and a representation
+    u = w_L L dens + w_M M dens for the fields; the diagonal of D is
+    -(i pi k^2 a_p / 2) J' H' and the double-layer far-field vector carries
+    -i e^{-i pi/4} sqrt(k a_p)/2, the signs the definitions of D and of the
+    double-layer potential give (both printed with the opposite sign);
   * time reversal (section 7): the mirror angles are alpha_j = 2 pi j /
     n_alpha from 0, the far field of incidence alpha_j is measured at
     alpha_i + pi (row i of F), and T = conj(F)^T F carries no quadrature
@@ -450,6 +457,171 @@ def dort_eigenvalues(T) -> np.ndarray:
 def rcs(F) -> np.ndarray:
     """Section 4.4: RCS = 10 log10(2 pi |a|^2) in dB."""
     return 10.0 * np.log10(2 * np.pi * np.abs(F) ** 2)
+
+
+# --------------------------------------------------------------------------
+# Other integral equations (section 3, "a few boundary integral equations";
+# section 4.2 blocks M and D; section 5 linear combinations)
+# --------------------------------------------------------------------------
+
+OPERATORS = ("I", "L", "M", "N", "D")
+
+
+def block_M(O, a, k, N, p, q) -> np.ndarray:
+    """Section 4.2, block M^pq of the trace of the double-layer potential:
+    -I/2 - (i pi k a_p / 2) J^p H'^p on the diagonal,
+    -(i k pi sqrt(a_p a_q) / 2) J^p (S^pq)^T J'^q off it."""
+    J, dJ, H, dH = bessel_diagonals(a, k, N)
+    if p == q:
+        return -0.5 * np.eye(2 * N + 1) - np.diag(0.5j * np.pi * k * a[p] * J[p] * dH[p])
+    S = separation_matrix(O[p], O[q], k, N)
+    return -0.5j * k * np.pi * np.sqrt(a[p] * a[q]) * (J[p][:, None] * S.T * dJ[q][None, :])
+
+
+def block_D(O, a, k, N, p, q) -> np.ndarray:
+    """Section 4.2, block D^pq of the normal-derivative trace of the
+    double-layer potential: -(i pi k^2 a_p / 2) J'^p H'^p on the diagonal,
+    -(i k^2 pi sqrt(a_p a_q) / 2) J'^p (S^pq)^T J'^q off it.  The diagonal
+    sign is the one the definition D lambda = -d_nx int d_ny G lambda (the
+    normal derivative of the double-layer potential of Prop. 4.3, continuous
+    across the circle) gives; the printed diagonal has the opposite sign,
+    while the printed off-diagonal blocks agree with the definition."""
+    J, dJ, H, dH = bessel_diagonals(a, k, N)
+    if p == q:
+        return np.diag(-0.5j * np.pi * k * k * a[p] * dJ[p] * dH[p])
+    S = separation_matrix(O[p], O[q], k, N)
+    return -0.5j * k * k * np.pi * np.sqrt(a[p] * a[q]) * (dJ[p][:, None] * S.T * dJ[q][None, :])
+
+
+def block_of(kind, O, a, k, N, p, q) -> np.ndarray:
+    """The block (p, q) of I, L, M, N or D (section 4.2)."""
+    if kind == "I":
+        return np.eye(2 * N + 1) if p == q else np.zeros((2 * N + 1, 2 * N + 1))
+    return {"L": block_L, "M": block_M, "N": block_N, "D": block_D}[kind](O, a, k, N, p, q)
+
+
+def assemble_formulation(O, a, bc, k, N, op_weights) -> np.ndarray:
+    """Section 5: the matrix of a linear combination of I, L, M, N and D
+    (the same block structure for every combination).  op_weights[c] maps
+    each operator name to its weight for the rows of disks with boundary
+    condition c (DIRICHLET or NEUMANN)."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    A = np.zeros((M * n, M * n), dtype=np.complex128)
+    for p in range(M):
+        w = op_weights[int(bc[p])]
+        for q in range(M):
+            B = np.zeros((n, n), dtype=np.complex128)
+            for kind in OPERATORS:
+                if w.get(kind, 0) != 0:
+                    B = B + w[kind] * block_of(kind, O, a, k, N, p, q)
+            A[p * n:(p + 1) * n, q * n:(q + 1) * n] = B
+    return A
+
+
+def rhs_formulation(O, a, bc, k, N, betas, rhs_weights) -> np.ndarray:
+    """Section 5: b = -(w_U U + w_dU dU) for plane waves (Prop. 4.1),
+    rhs_weights[c] = {"U": w_U, "dU": w_dU} for the rows of boundary
+    condition c.  [N_tot, R]."""
+    a = np.asarray(a, dtype=np.float64)
+    J, dJ, _, _ = bessel_diagonals(a, k, N)
+    cols = []
+    for beta in np.atleast_1d(betas):
+        d = planewave_coefficients(O, a, k, N, beta)
+        U, dU = d * J, k * d * dJ
+        b = np.zeros_like(U)
+        for p in range(len(a)):
+            w = rhs_weights[int(bc[p])]
+            b[p] = -(w.get("U", 0) * U[p] + w.get("dU", 0) * dU[p])
+        cols.append(b.reshape(-1))
+    return np.stack(cols, axis=1)
+
+
+def double_layer_potential(O, a, k, N, lam, points) -> np.ndarray:
+    """Prop. 4.3: (M lambda)(x) = -sum_p sum_m lambda^p_m (i pi k a_p / 2)
+    J'_m(k a_p) H_m(k r_p(x)) exp(i m theta_p(x)) / sqrt(2 pi a_p), for x
+    outside the disks."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    lam = np.asarray(lam)
+    squeeze = lam.ndim == 1
+    R = lam.reshape(M, n, -1)
+    pts = np.asarray(points, dtype=np.float64)
+    dJ = bessel_diagonals(a, k, N)[1]
+    m = modes(N)
+    u = np.zeros((len(pts), R.shape[2]), dtype=np.complex128)
+    for p in range(M):
+        d = pts - O[p][None, :]
+        r = np.hypot(d[:, 0], d[:, 1])
+        th = np.arctan2(d[:, 1], d[:, 0])
+        basis = special.hankel1(m[None, :], k * r[:, None]) * np.exp(1j * m[None, :] * th[:, None])
+        coef = -0.5j * np.pi * k * a[p] * dJ[p] / np.sqrt(2 * np.pi * a[p])
+        u += basis @ (coef[:, None] * R[p])
+    return u[:, 0] if squeeze else u
+
+
+def farfield_coefficients_M(O, a, k, N, theta) -> np.ndarray:
+    """Section 4.4, double-layer far-field vector a_M(theta):
+    -i e^{-i pi/4} sqrt(k a_p) / 2 exp(-i b_p k cos(theta - alpha_p))
+    J'_m(k a_p) exp(i m (theta - pi/2)).  The sign is the one the large-r
+    limit of the double-layer potential of Prop. 4.3 gives (the printed
+    vector has the opposite sign).  Returns [N_tot]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    dJ = bessel_diagonals(a, k, N)[1]
+    m = modes(N)[None, :]
+    bp = np.hypot(O[:, 0], O[:, 1])
+    alp = np.arctan2(O[:, 1], O[:, 0])
+    c = (-1j * np.exp(-1j * np.pi / 4) * np.sqrt(k * a) / 2)[:, None] \
+        * np.exp(-1j * bp * k * np.cos(theta - alp))[:, None] * dJ * np.exp(1j * m * (theta - np.pi / 2))
+    return c.reshape(-1)
+
+
+def farfield_formulation(O, a, k, N, dens, thetas, rep_weights) -> np.ndarray:
+    """Section 4.4 for the representation u = w_L L dens + w_M M dens:
+    a(theta) = w_L a_L(theta)^T dens + w_M a_M(theta)^T dens.  [T, R]."""
+    dens = np.asarray(dens)
+    if dens.ndim == 1:
+        dens = dens[:, None]
+    th = np.atleast_1d(thetas)
+    C = np.stack([rep_weights.get("L", 0) * farfield_coefficients(O, a, k, N, t)
+                  + rep_weights.get("M", 0) * farfield_coefficients_M(O, a, k, N, t) for t in th])
+    return C @ dens
+
+
+def potential_formulation(O, a, k, N, dens, points, rep_weights) -> np.ndarray:
+    """Prop. 4.3: u = w_L L dens + w_M M dens at points outside the disks."""
+    u = 0
+    if rep_weights.get("L", 0) != 0:
+        u = u + rep_weights["L"] * single_layer_potential(O, a, k, N, dens, points)
+    if rep_weights.get("M", 0) != 0:
+        u = u + rep_weights["M"] * double_layer_potential(O, a, k, N, dens, points)
+    return u
+
+
+def solve_formulation(O, a, bc, k, N, betas, op_weights, rhs_weights) -> np.ndarray:
+    """Section 5: LU solve of a formulation's system (no preconditioning
+    needed for the direct solve).  [N_tot, R]."""
+    A = assemble_formulation(O, a, bc, k, N, op_weights)
+    b = rhs_formulation(O, a, bc, k, N, betas, rhs_weights)
+    return np.linalg.solve(A, b)
+
+
+def preconditioned_formulation(O, a, bc, k, N, op_weights):
+    """P^-1 A of a formulation, P its diagonal blocks (diagonal matrices for
+    every combination of I, L, M, N, D)."""
+    A = assemble_formulation(O, a, bc, k, N, op_weights)
+    d = np.diag(A).copy()
+    M = len(np.asarray(a))
+    n = 2 * N + 1
+    for p in range(M):
+        blk = A[p * n:(p + 1) * n, p * n:(p + 1) * n]
+        assert np.count_nonzero(blk - np.diag(np.diag(blk))) == 0
+    return A / d[:, None], d
 
 
 # --------------------------------------------------------------------------
