@@ -406,6 +406,48 @@ def dort_timing():
     pb.close()
 
 
+def formulation_timing(reps: int = 5):
+    """Integral-equation formulations on the 400-disk workload: the
+    preconditioned product (CUDA events around msd_matvec, device buffers)
+    with the default rows and with the Brakhage-Werner rows (one
+    block-Toeplitz product over 2R columns), FP64 and FP32, R = 1 and 16;
+    then a mixed-precision solve to relres 1e-10 with each formulation."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cl = W.random_cluster_400()
+    pb = msd.Problem(cl)
+    rng = np.random.default_rng(0)
+    for kind in (None, "cfie", "bwie"):
+        pb.set_formulation(kind, k=cl.k) if kind else pb.set_formulation(None)
+        for prec in (msd.MSD_FP64, msd.MSD_FP32):
+            for R in (1, 16):
+                dt = torch.complex128 if prec == msd.MSD_FP64 else torch.complex64
+                x = torch.from_numpy(rng.standard_normal((cl.ntot, R)) + 1j * rng.standard_normal((cl.ntot, R))).to(
+                    device="cuda", dtype=dt)
+                y = torch.empty_like(x)
+                msd.msd_matvec(pb.handle, R, prec, x, y)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    msd.msd_matvec(pb.handle, R, prec, x, y)
+                e1.record()
+                torch.cuda.synchronize()
+                print(json.dumps({"workload": "random400 (M=400, N=20)", "formulation": kind or "default",
+                                  "precision": "fp64" if prec == msd.MSD_FP64 else "fp32", "R": R,
+                                  "product_ms": round(e0.elapsed_time(e1) / reps, 3)}), flush=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = pb.solve([cl.meta["beta"]], tol=1e-10, precision=msd.MSD_MIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "random400 (M=400, N=20)", "formulation": kind or "default",
+                          "mixed_solve_ms": round(e0.elapsed_time(e1), 1), "iters": int(res.iters[0]),
+                          "status": int(res.status)}), flush=True)
+    pb.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,11 +465,15 @@ def main():
                     help="print FP64 and mixed batched solve times (JSON lines) instead")
     ap.add_argument("--nearfield", action="store_true",
                     help="print the timing (JSON line) of the near field on a grid instead")
+    ap.add_argument("--formulations", action="store_true",
+                    help="print product and solve times (JSON lines) of the integral-equation formulations instead")
     ap.add_argument("--dort", action="store_true",
                     help="print the timing (JSON lines) of the time-reversal matrix and its eigenvalues instead")
     args = ap.parse_args()
     if args.dort:
         return dort_timing()
+    if args.formulations:
+        return formulation_timing()
     if args.nearfield:
         return nearfield_timing()
     if args.batched:

@@ -264,6 +264,40 @@ msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources,
 msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, int64_t P, const double* points,
                          void* u_out);
 
+/* Integral-equation formulation (sections 3, 4.2, 5): replaces the default
+ * rows (EFIE L rho = -U on sound-soft disks, (-I/2 + N) rho = -dU on
+ * sound-hard ones, u = L rho) by linear combinations of the identity and
+ * the four boundary integral operators of section 4.2,
+ *   rows of disks with boundary condition c:
+ *     (w_I I + w_L L + w_M M + w_N N + w_D D) dens = -(w_U U + w_dU dU),
+ *   fields (far field section 4.4, near field Prop. 4.3):
+ *     u = w_L' L dens + w_M' M dens,
+ * for every configuration of the problem.  Examples (Dirichlet rows):
+ * CFIE  w_L = alpha eta, w_I = (1 - alpha)/2, w_N = 1 - alpha,
+ *       w_U = alpha eta, w_dU = 1 - alpha, u = L dens;
+ * Brakhage-Werner  w_I = 1/2, w_L = -eta, w_M = -1, w_U = 1,
+ *       u = -(eta L + M) dens.
+ * The off-diagonal blocks of M, N, D use the same generators g^pq as L
+ * with J' in place of J on the source side (M, D) and/or the target side
+ * (N, D); the D diagonal is -(i pi k^2 a/2) J' H' (the normal derivative of
+ * the double-layer potential of Prop. 4.3; printed with the opposite sign)
+ * and the double-layer far field carries -i e^{-i pi/4} sqrt(k a)/2.
+ * Every solve, product, right-hand side, far field, near field and time-
+ * reversal call then uses the formulation, preconditioned by its own
+ * diagonal self blocks; products always use stored generators.
+ *   op_weights   double [2][5][2]: per boundary condition (MSD_DIRICHLET,
+ *                MSD_NEUMANN) the complex weights (re, im) of I, L, M, N, D;
+ *                NULL restores the default rows
+ *   rhs_weights  double [2][2][2]: per boundary condition the weights of U, dU
+ *   rep_weights  double [2][2]: the weights of L and M in the representation
+ * Returns MSD_ERR_NONFINITE when the self block of the combination vanishes
+ * for some mode (a resonance of that formulation at k a_p; the EFIE at a
+ * zero of J_m, for instance), and the formulation is left set.  The
+ * gradient (msd_grad_farfield_misfit) and msd_matvec_noalloc need the
+ * default rows (MSD_ERR_ARG otherwise).  Synchronises the stream. */
+msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const double* rhs_weights,
+                               const double* rep_weights);
+
 /* Time reversal, DORT (section 7, far-field mirror): for every
  * configuration the mirror emits the plane waves of incidence
  * alpha_j = 2 pi j / n_alpha (j = 0..n_alpha-1) and measures the far field

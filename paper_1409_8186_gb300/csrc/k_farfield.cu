@@ -2,6 +2,9 @@
 //   a_L(theta) = sum_p sum_m c^p_m(theta) rho^p_m,
 //   c^p_m(theta) = i e^{-i pi/4} sqrt(a_p) / (2 sqrt k) e^{-i k theta_hat . O_p}
 //                  J_m(k a_p) e^{i m (theta - pi/2)},
+// or, with J_m replaced by the row factor w_L J_m - k w_M J'_m, of the
+// representation u = w_L L + w_M M (the double-layer vector a_M is
+// -k J'_m / J_m times the single-layer one);
 // (b_p cos(theta - alpha_p) = theta_hat . O_p).  One CTA per (configuration,
 // sample angle, group of 8 columns); threads stride over the disks, the
 // e^{i m (theta - pi/2)} factors come from one sincos and a complex
@@ -42,7 +45,7 @@ __global__ void k_farfield(const MsdConfig* __restrict__ cfgs, const double2* __
         const long long row0 = c.row_off + (long long)p * c.n;
         double2 e = eN;
         for (int mi = 0; mi < c.n; ++mi) {
-            const double2 f = cscale(cmul(ph, e), J[row0 + mi].x);
+            const double2 f = cmul(cmul(ph, e), J[row0 + mi]);
             const double2* rr = rho + (row0 + mi) * R;
 #pragma unroll
             for (int j = 0; j < kCols; ++j)

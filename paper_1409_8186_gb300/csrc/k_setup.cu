@@ -296,8 +296,10 @@ __global__ void __launch_bounds__(kGenThreads)
 
 // ---------------------------------------------------------------- near field (Prop. 4.3)
 
-// W[row][r] = c^p_m rho^p_m[r] with c^p_m = (i pi a_p / 2) J_m(k a_p) / sqrt(2 pi a_p):
-// the weight of H_m(k r_p) e^{i m theta_p} in the single-layer potential.
+// W[row][r] = c^p_m rho^p_m[r] with c^p_m = (i pi a_p / 2) f^p_m / sqrt(2 pi a_p):
+// the weight of H_m(k r_p) e^{i m theta_p} in the potential, f = J_m(k a_p)
+// for the single-layer potential, w_L J_m - k w_M J'_m for u = w_L L + w_M M
+// (the double-layer term of Prop. 4.3 is -(i pi k a_p / 2) J'_m).
 __global__ void k_nf_weights(const MsdConfig* __restrict__ cfg, int ci, const double* __restrict__ radius,
                              const double2* __restrict__ J, const double2* __restrict__ rho, int R,
                              double2* __restrict__ W) {
@@ -441,8 +443,9 @@ void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, i
 __global__ void k_weighted_norms(const MsdConfig* __restrict__ cfg, const RowChunk* __restrict__ chunks, int R,
                                  const double* __restrict__ radius, const int8_t* __restrict__ bc,
                                  const double2* __restrict__ J, const double2* __restrict__ H,
-                                 const double2* __restrict__ dH, const double2* __restrict__ u,
-                                 const double2* __restrict__ v, double2* __restrict__ part) {
+                                 const double2* __restrict__ dH, const double2* __restrict__ diag,
+                                 const double2* __restrict__ u, const double2* __restrict__ v,
+                                 double2* __restrict__ part) {
     __shared__ double su[64], sv[64];
     for (int t = threadIdx.x; t < R; t += blockDim.x) su[t] = sv[t] = 0.0;
     __syncthreads();
@@ -454,10 +457,15 @@ __global__ void k_weighted_norms(const MsdConfig* __restrict__ cfg, const RowChu
         const int r = (int)(t % R);
         const int p = (int)((row - c.row_off) / c.n);
         const double a = radius[c.disk_off + p];
-        const double2 jj = J[row];
-        const double2 hh = bc[c.disk_off + p] ? dH[row] : H[row];
-        const double sc = bc[c.disk_off + p] ? 0.5 * M_PI * c.k * a : 0.5 * M_PI * a;
-        const double w2 = sc * sc * cabs2(jj) * cabs2(hh);
+        double w2;
+        if (diag) {
+            w2 = cabs2(diag[row]);
+        } else {
+            const double2 jj = J[row];
+            const double2 hh = bc[c.disk_off + p] ? dH[row] : H[row];
+            const double sc = bc[c.disk_off + p] ? 0.5 * M_PI * c.k * a : 0.5 * M_PI * a;
+            w2 = sc * sc * cabs2(jj) * cabs2(hh);
+        }
         atomicAdd(&su[r], w2 * cabs2(u[row * R + r]));
         atomicAdd(&sv[r], w2 * cabs2(v[row * R + r]));
     }
@@ -468,8 +476,9 @@ __global__ void k_weighted_norms(const MsdConfig* __restrict__ cfg, const RowChu
 
 void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int nchunk, int R,
                            const double* d_radius, const int8_t* d_bc, const double2* J, const double2* H,
-                           const double2* dH, const double2* u, const double2* v, double2* part, cudaStream_t s) {
-    k_weighted_norms<<<nchunk, 256, 0, s>>>(d_cfg, d_chunks, R, d_radius, d_bc, J, H, dH, u, v, part);
+                           const double2* dH, const double2* diag, const double2* u, const double2* v,
+                           double2* part, cudaStream_t s) {
+    k_weighted_norms<<<nchunk, 256, 0, s>>>(d_cfg, d_chunks, R, d_radius, d_bc, J, H, dH, diag, u, v, part);
     g_msd_launches += 1;
 }
 

@@ -193,6 +193,15 @@ struct msd_problem {
     DBuf gbuf[9];   // gradient work buffers
     DBuf nfbuf[4];  // near-field buffers: rho, points, weights, output stage
     DBuf dortbuf[6];  // time reversal: rho, angles, F, T, eigenvalues, eigen work
+    // integral-equation formulation (msd_set_formulation); form == false: the
+    // default rows (L on sound-soft disks, -I/2 + N on sound-hard ones, u = L rho)
+    bool form = false;
+    MsdFormulation fw{};
+    DBuf fbuf;  // the per-row factors below, in one allocation
+    double2 *d_fl1_64 = nullptr, *d_fl2_64 = nullptr, *d_frs = nullptr, *d_fff = nullptr, *d_fdiag = nullptr;
+    float2 *d_fl1_32 = nullptr, *d_fl2_32 = nullptr;
+    double* d_frf2_64 = nullptr;
+    float* d_frf2_32 = nullptr;
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
     double offdiag_L = 0, offdiag_n2 = 0;
@@ -232,6 +241,37 @@ void check_flags(msd_problem* pb, const char* where) {
     check_tc(where);
     if (f & 1) fail(MSD_ERR_NONFINITE, std::string(where) + ": non-finite Bessel factor (k a_p at a zero of J_m for a Neumann disk?)");
     if (f & 2) fail(MSD_ERR_RANGE, std::string(where) + ": a Hankel generator exceeds the complex64 range; use MSD_FP64");
+}
+
+// Right-hand-side scale and field factor of the current formulation.
+const double2* rhs_scale_of(const msd_problem* pb) { return pb->form ? pb->d_frs : pb->d_rhs_scale; }
+const double2* field_factor_of(const msd_problem* pb) { return pb->form ? pb->d_fff : pb->d_J; }
+
+// Per-row factors of the formulation pb->fw (after the Bessel diagonals).
+void form_rows(msd_problem* pb) {
+    const size_t n = (size_t)pb->Ntot;
+    char* b = (char*)pb->fbuf.get(n * (5 * 16 + 2 * 8 + 8 + 4));
+    pb->d_fl1_64 = (double2*)b;
+    pb->d_fl2_64 = pb->d_fl1_64 + n;
+    pb->d_frs = pb->d_fl2_64 + n;
+    pb->d_fff = pb->d_frs + n;
+    pb->d_fdiag = pb->d_fff + n;
+    pb->d_fl1_32 = (float2*)(pb->d_fdiag + n);
+    pb->d_fl2_32 = pb->d_fl1_32 + n;
+    pb->d_frf2_64 = (double*)(pb->d_fl2_32 + n);
+    pb->d_frf2_32 = (float*)(pb->d_frf2_64 + n);
+    CK(cudaMemsetAsync(pb->d_flags, 0, sizeof(int), pb->stream));
+    launch_form_rows(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_radius, pb->d_bc, pb->d_J, pb->d_dJ, pb->d_H,
+                     pb->d_dH, pb->fw, pb->d_fl1_64, pb->d_fl2_64, pb->d_fl1_32, pb->d_fl2_32, pb->d_frf2_64,
+                     pb->d_frf2_32, pb->d_frs, pb->d_fff, pb->d_fdiag, pb->d_flags, pb->stream);
+    CK_LAUNCH();
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, pb->d_flags, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
+    CK(cudaStreamSynchronize(pb->stream));
+    if (f & 1)
+        fail(MSD_ERR_NONFINITE,
+             "msd_set_formulation: the self block of the combination vanishes for some mode (a resonance of this "
+             "formulation at k a_p)");
 }
 
 // K2 over the whole problem: the stored generator array(s).
@@ -658,7 +698,31 @@ void matvec_recompute_dev(msd_problem* pb, int R, bool fp64, const void* x, void
 }
 
 // y = P^-1 A x on the problem's stream (device pointers).
+// The product of a formulation (msd_set_formulation): one block-Toeplitz
+// product over 2R columns (sqrt(a) J x | sqrt(a) J' x) with the stored
+// generators, then y = x + l1 z1 + l2 z2.
+void matvec_form_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
+    if (matvec_smem_bytes(matvec_default_choice(2 * R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
+        fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
+    ensure_generators(pb, fp64);
+    MatvecPlan& plan = get_plan(pb, 2 * R, fp64);
+    const size_t elem = fp64 ? 16 : 8;
+    void* xs = pb->xs.get((size_t)pb->Ntot * 2 * R * elem);
+    void* part = pb->part.get((size_t)plan.nsplit * pb->Ntot * 2 * R * elem);
+    launch_form_scale(fp64, pb->Ntot, R, fp64 ? (const void*)pb->d_rf64 : (const void*)pb->d_rf32,
+                      fp64 ? (const void*)pb->d_frf2_64 : (const void*)pb->d_frf2_32, x, xs, pb->stream);
+    launch_bt_only(plan.ch, fp64, pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax,
+                   fp64 ? (const void*)pb->d_G64 : (const void*)pb->d_G32, xs, part, pb->Ntot, 2 * R, pb->stream);
+    launch_form_finalize(fp64, pb->Ntot, R, plan.nsplit, fp64 ? (const void*)pb->d_fl1_64 : (const void*)pb->d_fl1_32,
+                         fp64 ? (const void*)pb->d_fl2_64 : (const void*)pb->d_fl2_32, x, part, y, pb->stream);
+    CK_LAUNCH();
+}
+
 void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
+    if (pb->form) {
+        matvec_form_dev(pb, R, fp64, x, y);
+        return;
+    }
     if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     if (pb->gen_mode == MSD_GEN_RECOMPUTE) {
@@ -731,6 +795,7 @@ void ensure_adjoint(msd_problem* pb, bool fp64) {
 //   adjoint: y = x + r .* T^H(conj(l) .* x)       ((P^-1 A)^H x)
 //   raw forward: y = T(r .* x)    raw adjoint: y = T^H(conj(l) .* x)
 void product_dev(msd_problem* pb, int R, bool fp64, bool adjoint, bool raw, const void* x, void* y) {
+    if (pb->form) fail(MSD_ERR_ARG, "adjoint and raw products need the default formulation");
     if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     if (adjoint) ensure_adjoint(pb, fp64);
@@ -997,14 +1062,15 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
         CK(cudaMemcpyAsync(cx.b, b_dev, nv * 16, cudaMemcpyDeviceToDevice, s));
     } else {
         CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
-        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, rhs_scale_of(pb),
                              pb->Nmax, R, d_betas, cx.b, s);
         CK_LAUNCH();
     }
     if (adjoint) {
+        if (pb->form) fail(MSD_ERR_ARG, "adjoint solves need the default formulation");
         ensure_adjoint(pb, true);
         if (mixed) ensure_adjoint(pb, false);
-    } else if (pb->gen_mode != MSD_GEN_RECOMPUTE) {
+    } else if (pb->gen_mode != MSD_GEN_RECOMPUTE || pb->form) {
         ensure_generators(pb, true);
         if (mixed) ensure_generators(pb, false);
     }
@@ -1086,6 +1152,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     if (!adjoint && R <= 64) {
         const int nch = (int)pb->chunks.size();
         launch_weighted_norms(pb->d_cfg, pb->d_chunks, nch, R, pb->d_radius, pb->d_bc, pb->d_J, pb->d_H, pb->d_dH,
+                              pb->form ? pb->d_fdiag : nullptr,
                               cx.r, cx.b, cx.part, s);
         CK_LAUNCH();
         std::vector<double2> wp((size_t)nch * R);
@@ -1283,6 +1350,7 @@ void msd_destroy(msd_problem* pb) {
     for (auto& b : pb->gbuf) b.release();
     for (auto& b : pb->nfbuf) b.release();
     for (auto& b : pb->dortbuf) b.release();
+    pb->fbuf.release();
     delete pb;
 }
 
@@ -1326,7 +1394,7 @@ msd_status msd_rhs_planewave(msd_problem* pb, int R, const double* betas_host, v
         double* d_betas = (double*)pb->sbuf[21].get((size_t)pb->C * R * 8);
         CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, pb->stream));
         OutStage o(pb, pb->sbuf[20], out, (size_t)pb->Ntot * R * 16);
-        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale,
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, rhs_scale_of(pb),
                              pb->Nmax, R, d_betas, (double2*)o.dev, pb->stream);
         CK_LAUNCH();
         o.finish();
@@ -1374,6 +1442,7 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
         if (pb->d_G64 || pb->d_G32) launch_full_generators(pb, pb->d_G64, pb->d_G32);
         CK_LAUNCH();
         check_flags(pb, "msd_update_geometry");
+        if (pb->form) form_rows(pb);
         pb->geom_version += 1;  // adjoint operator data is rebuilt on next use
         return MSD_OK;
     });
@@ -1484,6 +1553,7 @@ msd_status msd_grad_farfield_misfit(msd_problem* pb, int R, const double* betas_
     return guarded([&]() -> msd_status {
         if (!pb || R <= 0 || T <= 0 || !betas_host || !thetas_host || !F_target)
             fail(MSD_ERR_ARG, "msd_grad_farfield_misfit: bad argument");
+        if (pb->form) fail(MSD_ERR_ARG, "msd_grad_farfield_misfit: needs the default formulation");
         cudaStream_t s = pb->stream;
         const long long nv = pb->Ntot * R;
         const size_t nF = (size_t)pb->C * T * R;
@@ -1564,7 +1634,7 @@ msd_status msd_farfield(msd_problem* pb, const void* rho, int R, int T, const do
         CK(cudaMemcpyAsync(d_th, thetas_host, (size_t)T * 8, cudaMemcpyHostToDevice, pb->stream));
         const double2* d_rho = (const double2*)stage_in(pb, pb->sbuf[22], rho, (size_t)pb->Ntot * R * 16);
         OutStage o(pb, pb->sbuf[23], F_out, (size_t)pb->C * T * R * 16);
-        launch_farfield(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_radius, pb->d_J, R, T, d_th, d_rho,
+        launch_farfield(pb->d_cfg, pb->C, pb->cfg.data(), pb->d_centre, pb->d_radius, field_factor_of(pb), R, T, d_th, d_rho,
                         nullptr, (double2*)o.dev, pb->stream);
         CK_LAUNCH();
         o.finish();
@@ -1578,7 +1648,7 @@ msd_status msd_rhs_pointsource(msd_problem* pb, int R, const double* sources_hos
         double2* d_src = (double2*)pb->sbuf[21].get((size_t)pb->C * R * 16);
         CK(cudaMemcpyAsync(d_src, sources_host, (size_t)pb->C * R * 16, cudaMemcpyHostToDevice, pb->stream));
         OutStage o(pb, pb->sbuf[20], out, (size_t)pb->Ntot * R * 16);
-        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale, R,
+        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, rhs_scale_of(pb), R,
                                d_src, (double2*)o.dev, pb->stream);
         CK_LAUNCH();
         o.finish();
@@ -1593,10 +1663,36 @@ msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources_
         double2* d_src = (double2*)pb->nfbuf[1].get((size_t)pb->C * R * 16);
         CK(cudaMemcpyAsync(d_src, sources_host, (size_t)pb->C * R * 16, cudaMemcpyHostToDevice, pb->stream));
         double2* b = (double2*)pb->nfbuf[2].get((size_t)pb->Ntot * R * 16);
-        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_rhs_scale, R,
+        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, rhs_scale_of(pb), R,
                                d_src, b, pb->stream);
         CK_LAUNCH();
         return solve_impl(pb, R, nullptr, opts, rho_out, stats_host, b);
+    });
+}
+
+msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const double* rhs_weights,
+                               const double* rep_weights) {
+    return guarded([&]() -> msd_status {
+        if (!pb) fail(MSD_ERR_ARG, "msd_set_formulation: bad handle");
+        if (!op_weights) {
+            pb->form = false;
+            return MSD_OK;
+        }
+        if (!rhs_weights || !rep_weights) fail(MSD_ERR_ARG, "msd_set_formulation: bad argument");
+        MsdFormulation w{};
+        for (int c = 0; c < 2; ++c) {
+            for (int o = 0; o < 5; ++o)
+                w.op[c][o] = make_double2(op_weights[(c * 5 + o) * 2], op_weights[(c * 5 + o) * 2 + 1]);
+            for (int o = 0; o < 2; ++o)
+                w.rhs[c][o] = make_double2(rhs_weights[(c * 2 + o) * 2], rhs_weights[(c * 2 + o) * 2 + 1]);
+        }
+        for (int o = 0; o < 2; ++o) w.rep[o] = make_double2(rep_weights[2 * o], rep_weights[2 * o + 1]);
+        for (const double2* v = &w.op[0][0]; v < &w.op[0][0] + 10; ++v)
+            if (!std::isfinite(v->x) || !std::isfinite(v->y)) fail(MSD_ERR_ARG, "msd_set_formulation: weight");
+        pb->fw = w;
+        pb->form = true;
+        form_rows(pb);
+        return MSD_OK;
     });
 }
 
@@ -1609,7 +1705,7 @@ msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, in
         const double2* d_pts = (const double2*)stage_in(pb, pb->nfbuf[1], points, (size_t)P * 16);
         double2* W = (double2*)pb->nfbuf[2].get((size_t)pb->Ntot * R * 16);
         OutStage o(pb, pb->nfbuf[3], u_out, (size_t)P * R * 16);
-        launch_nearfield(pb->d_cfg, config, pb->cfg[config], pb->d_centre, pb->d_radius, pb->d_J, d_rho, R, W,
+        launch_nearfield(pb->d_cfg, config, pb->cfg[config], pb->d_centre, pb->d_radius, field_factor_of(pb), d_rho, R, W,
                          d_pts, P, (double2*)o.dev, pb->stream);
         CK_LAUNCH();
         o.finish();
@@ -1669,7 +1765,7 @@ msd_status msd_dort(msd_problem* pb, int n_alpha, const msd_opts* opts, void* F_
         double* d_th = (double*)pb->dortbuf[1].get((size_t)n * 8);
         CK(cudaMemcpyAsync(d_th, thetas.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
         double2* F = (double2*)pb->dortbuf[2].get(nn * 16);
-        launch_farfield(pb->d_cfg, C, pb->cfg.data(), pb->d_centre, pb->d_radius, pb->d_J, n, n, d_th, rho, nullptr,
+        launch_farfield(pb->d_cfg, C, pb->cfg.data(), pb->d_centre, pb->d_radius, field_factor_of(pb), n, n, d_th, rho, nullptr,
                         F, s);
         CK_LAUNCH();
         if (F_out)
@@ -1761,6 +1857,7 @@ extern "C" msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, 
         if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev))
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must be device memory");
         if (x_dev == y_dev) fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must not overlap");
+        if (pb->form) fail(MSD_ERR_ARG, "msd_matvec_noalloc: needs the default formulation");
         const bool fp64 = precision == MSD_FP64;
         if ((fp64 && !pb->d_G64) || (!fp64 && !pb->d_G32))
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: the generators of this precision are not built yet "

@@ -142,12 +142,41 @@ void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, i
 
 // ||P u||^2 and ||P v||^2 per (row chunk, column) with the preconditioner's
 // diagonal P (unpreconditioned residual norms); R <= 64.
+// diag (may be NULL): the self-block diagonal P of a formulation; NULL takes
+// the default rows' P from J, H, H'.
 void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int nchunk, int R,
                            const double* d_radius, const int8_t* d_bc, const double2* J, const double2* H,
-                           const double2* dH, const double2* u, const double2* v, double2* part, cudaStream_t s);
+                           const double2* dH, const double2* diag, const double2* u, const double2* v,
+                           double2* part, cudaStream_t s);
+
+// Integral-equation formulation (sections 3, 4.2, 5): per boundary
+// condition c (0 Dirichlet, 1 Neumann) the weights of I, L, M, N, D in the
+// rows of its disks and of U, dU in their right-hand side, and the weights
+// of the single- and double-layer potentials in the field representation.
+struct MsdFormulation {
+    double2 op[2][5];
+    double2 rhs[2][2];
+    double2 rep[2];
+};
+// Per-row factors: l1, l2 (FP64, FP32) of the combined product, rf2 =
+// sqrt(a) J', the right-hand-side scale -(w_U J + k w_dU J')/P, the field
+// factor w_L' J - k w_M' J' and the self-block diagonal P.  d_flags bit 0 is
+// set when a factor is not finite (P = 0).
+void launch_form_rows(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg, const double* d_radius,
+                      const int8_t* d_bc, const double2* J, const double2* dJ, const double2* H, const double2* dH,
+                      const MsdFormulation& w, double2* l1_64, double2* l2_64, float2* l1_32, float2* l2_32,
+                      double* rf2_64, float* rf2_32, double2* rhs_scale, double2* ff, double2* diag, int* d_flags,
+                      cudaStream_t s);
+// xs [Ntot][2R] = (rf .* x | rf2 .* x);  y = x + l1 .* sum part[:, :, 0:R] + l2 .* sum part[:, :, R:2R]
+void launch_form_scale(bool fp64, long long Ntot, int R, const void* rf, const void* rf2, const void* x, void* xs,
+                       cudaStream_t s);
+void launch_form_finalize(bool fp64, long long Ntot, int R, int nsplit, const void* l1, const void* l2,
+                          const void* x, const void* part, void* y, cudaStream_t s);
 
 // Near field (Prop. 4.3): u(points)[r] of configuration ci for densities rho
 // [N_tot][R]; W is a work buffer of N_tot * R complex128.
+// J: the per-row field factor (the Bessel diagonal J for u = L rho, or a
+// formulation's w_L J - k w_M J').
 void launch_nearfield(const MsdConfig* d_cfg, int ci, const MsdConfig& h_cfg, const double2* d_centre,
                       const double* d_radius, const double2* J, const double2* rho, int R, double2* W,
                       const double2* d_pts, long long P, double2* out, cudaStream_t s);
@@ -186,6 +215,7 @@ cudaError_t dort_set_smem_limits(int n);
 cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, int* err_flag,
                         cudaStream_t s);
 
+// J: the per-row field factor, as for launch_nearfield.
 void launch_farfield(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,
                      const double2* d_centre, const double* d_radius, const double2* J,
                      int R, int T, const double* d_thetas, const double2* rho,

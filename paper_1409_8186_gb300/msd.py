@@ -20,6 +20,7 @@ _LIB_PATH = os.path.join(_HERE, "libmsd.so")
 MSD_OK = 0
 MSD_NOT_CONVERGED = 1
 MSD_STAGNATED = 3
+MSD_ERR_ARG, MSD_ERR_OVERLAP, MSD_ERR_CUDA, MSD_ERR_OOM, MSD_ERR_NONFINITE, MSD_ERR_RANGE = -1, -2, -3, -4, -5, -6
 MSD_DIRICHLET, MSD_NEUMANN = 0, 1
 MSD_FP64, MSD_MIXED, MSD_FP32 = 0, 1, 2
 MSD_GEN_AUTO, MSD_GEN_STREAMED, MSD_GEN_RECOMPUTE = 0, 1, 2
@@ -77,6 +78,7 @@ def _load():
         "msd_solve_pointsources": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P]),
         "msd_dort": (I, [P, I, ctypes.POINTER(msd_opts), P, P, P, P]),
         "msd_dort_eigen": (I, [P, I, P, P, P]),
+        "msd_set_formulation": (I, [P, P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
     }
@@ -93,7 +95,7 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
-            "msd_dort", "msd_dort_eigen", "msd_last_error")
+            "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_last_error")
 
 
 def library_path() -> str:
@@ -264,6 +266,64 @@ def msd_dort_eigen(h, n_alpha: int, F, T_out, eig_out) -> None:
     _check(_lib.msd_dort_eigen(h, n_alpha, _ptr(F), _ptr(T_out) if T_out is not None else None, _ptr(eig_out)))
 
 
+def msd_set_formulation(h, op_weights, rhs_weights, rep_weights) -> None:
+    """op_weights complex [2][5] (I, L, M, N, D per boundary condition),
+    rhs_weights complex [2][2] (U, dU), rep_weights complex [2] (L, M);
+    op_weights None restores the default rows."""
+    if op_weights is None:
+        _check(_lib.msd_set_formulation(h, None, None, None))
+        return
+    ow = np.ascontiguousarray(np.asarray(op_weights, np.complex128).reshape(2, 5)).view(np.float64)
+    rw = np.ascontiguousarray(np.asarray(rhs_weights, np.complex128).reshape(2, 2)).view(np.float64)
+    pw = np.ascontiguousarray(np.asarray(rep_weights, np.complex128).reshape(2)).view(np.float64)
+    _check(_lib.msd_set_formulation(h, _ptr(ow), _ptr(rw), _ptr(pw)))
+
+
+_OPS = ("I", "L", "M", "N", "D")
+
+
+def formulation(kind: str, alpha: float = 0.5, eta=None, k: float | None = None):
+    """Weights (op [2][5], rhs [2][2], rep [2]) of a standard formulation
+    (section 3).  Sound-soft rows: "efie" L = -U; "mfie" (I/2 + N) = -dU;
+    "cfie" alpha eta L + (1 - alpha)(I/2 + N) = -(alpha eta U + (1 - alpha) dU);
+    "bwie" (I/2 - eta L - M) = -U with u = -(eta L + M).  Sound-hard rows:
+    (-I/2 + N) = -dU for the single-layer representations, and the normal
+    trace (eta I/2 - eta N - D) = -dU of the Brakhage-Werner representation.
+    eta defaults to i k."""
+    if eta is None and kind in ("cfie", "bwie"):
+        if k is None:
+            raise ValueError("eta or k is needed")
+        eta = 1j * k
+    op = np.zeros((2, 5), np.complex128)
+    rhs = np.zeros((2, 2), np.complex128)
+    rep = np.zeros(2, np.complex128)
+
+    def put(c, **w):
+        for name, v in w.items():
+            op[c, _OPS.index(name)] = v
+    if kind == "bwie":
+        put(MSD_DIRICHLET, I=0.5, L=-eta, M=-1.0)
+        put(MSD_NEUMANN, I=0.5 * eta, N=-eta, D=-1.0)
+        rhs[:, :] = [[1, 0], [0, 1]]
+        rep[:] = [-eta, -1.0]
+        return op, rhs, rep
+    put(MSD_NEUMANN, I=-0.5, N=1.0)
+    rhs[MSD_NEUMANN] = [0, 1]
+    rep[:] = [1.0, 0.0]
+    if kind == "efie":
+        put(MSD_DIRICHLET, L=1.0)
+        rhs[MSD_DIRICHLET] = [1, 0]
+    elif kind == "mfie":
+        put(MSD_DIRICHLET, I=0.5, N=1.0)
+        rhs[MSD_DIRICHLET] = [0, 1]
+    elif kind == "cfie":
+        put(MSD_DIRICHLET, L=alpha * eta, I=0.5 * (1 - alpha), N=1 - alpha)
+        rhs[MSD_DIRICHLET] = [alpha * eta, 1 - alpha]
+    else:
+        raise ValueError(kind)
+    return op, rhs, rep
+
+
 def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
 
@@ -430,6 +490,19 @@ class Problem:
         eig = torch.empty((self.C, n_alpha), dtype=torch.float64, device="cuda")
         st = msd_dort(self.handle, n_alpha, o, F, T, eig)
         return eig, F, T, st
+
+    def set_formulation(self, kind=None, **kw):
+        """Use a standard formulation ("efie", "mfie", "cfie", "bwie"; see
+        formulation()), explicit weights (op=, rhs=, rep=), or the default
+        rows (kind None)."""
+        if kind is None and "op" not in kw:
+            msd_set_formulation(self.handle, None, None, None)
+            return
+        if kind is None:
+            op, rhs, rep = kw["op"], kw["rhs"], kw["rep"]
+        else:
+            op, rhs, rep = formulation(kind, **kw)
+        msd_set_formulation(self.handle, op, rhs, rep)
 
     def dort_eigen(self, F, want_T=False):
         """T = conj(F)^T F and its eigenvalues (largest first) for caller
