@@ -34,6 +34,11 @@ Readings of the paper taken here:
     -(i pi k^2 a_p / 2) J' H' and the double-layer far-field vector carries
     -i e^{-i pi/4} sqrt(k a_p)/2, the signs the definitions of D and of the
     double-layer potential give (both printed with the opposite sign);
+  * penetrable obstacles (section 7, Example II): one interior wavenumber
+    k- per configuration and mu per disk; the (2, 2) block of the
+    transmission system is -mu (I/2 + N-), the sign the interior normal
+    trace of L- rho- (Prop. 3.2) and the transmission condition
+    d_n u+ - mu d_n u- = -d_n u_inc give (printed without the minus);
   * time reversal (section 7): the mirror angles are alpha_j = 2 pi j /
     n_alpha from 0, the far field of incidence alpha_j is measured at
     alpha_i + pi (row i of F), and T = conj(F)^T F carries no quadrature
@@ -622,6 +627,110 @@ def preconditioned_formulation(O, a, bc, k, N, op_weights):
         blk = A[p * n:(p + 1) * n, p * n:(p + 1) * n]
         assert np.count_nonzero(blk - np.diag(np.diag(blk))) == 0
     return A / d[:, None], d
+
+
+# --------------------------------------------------------------------------
+# Penetrable obstacles (section 7, Example II: the transmission problem)
+# --------------------------------------------------------------------------
+
+def assemble_penetrable(O, a, k_plus, k_minus, mu, N) -> np.ndarray:
+    """Section 7, transmission system for u+ = L+ rho+ outside and
+    u- = L- rho- inside the disks (single layers at k+ and k-):
+        [ L+           -L-            ] [rho+]   [ -U  ]
+        [ -I/2 + N+    -mu (I/2 + N-) ] [rho-] = [ -dU ],
+    rows: the traces u+ - u- = -u_inc and mu-weighted normal traces
+    d_n u+ - mu d_n u- = -d_n u_inc on every circle (mu per disk, its row);
+    the interior normal trace of L- rho- is (I/2 + N-) rho- (Prop. 3.2), hence
+    the minus sign in the (2, 2) block.  [2 N_tot, 2 N_tot]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    mu = np.broadcast_to(np.asarray(mu, dtype=np.complex128), (M,))
+    Nt = M * n
+    A = np.zeros((2 * Nt, 2 * Nt), dtype=np.complex128)
+    for p in range(M):
+        rs = slice(p * n, (p + 1) * n)
+        rn = slice(Nt + p * n, Nt + (p + 1) * n)
+        for q in range(M):
+            cp = slice(q * n, (q + 1) * n)
+            cm = slice(Nt + q * n, Nt + (q + 1) * n)
+            A[rs, cp] = block_L(O, a, k_plus, N, p, q)
+            A[rs, cm] = -block_L(O, a, k_minus, N, p, q)
+            Bp = block_N(O, a, k_plus, N, p, q)
+            Bm = block_N(O, a, k_minus, N, p, q)
+            if p == q:
+                Bp = Bp - 0.5 * np.eye(n)
+                Bm = Bm + 0.5 * np.eye(n)
+            A[rn, cp] = Bp
+            A[rn, cm] = -mu[p] * Bm
+    return A
+
+
+def rhs_penetrable(O, a, k_plus, N, betas) -> np.ndarray:
+    """Section 7: [-U; -dU] of the plane waves at k+ (Prop. 4.1).
+    [2 N_tot, R]."""
+    a = np.asarray(a, dtype=np.float64)
+    J, dJ, _, _ = bessel_diagonals(a, k_plus, N)
+    cols = []
+    for beta in np.atleast_1d(betas):
+        d = planewave_coefficients(O, a, k_plus, N, beta)
+        cols.append(np.concatenate([-(d * J).reshape(-1), -(k_plus * d * dJ).reshape(-1)]))
+    return np.stack(cols, axis=1)
+
+
+def solve_penetrable(O, a, k_plus, k_minus, mu, N, betas):
+    """LU solve of the transmission system; returns (rho+, rho-), each
+    [N_tot, R]."""
+    A = assemble_penetrable(O, a, k_plus, k_minus, mu, N)
+    x = np.linalg.solve(A, rhs_penetrable(O, a, k_plus, N, betas))
+    Nt = A.shape[0] // 2
+    return x[:Nt], x[Nt:]
+
+
+def preconditioned_penetrable(O, a, k_plus, k_minus, mu, N):
+    """B^-1 A with B the 2 x 2 self blocks of every (disk, mode): the
+    trace and normal rows of a mode couple its rho+ and rho- entries
+    only, so B is a 2 x 2 matrix per mode.  Returns (B^-1 A, B [N_tot, 2, 2])."""
+    A = assemble_penetrable(O, a, k_plus, k_minus, mu, N)
+    Nt = A.shape[0] // 2
+    i = np.arange(Nt)
+    B = np.stack([np.stack([A[i, i], A[i, Nt + i]], -1), np.stack([A[Nt + i, i], A[Nt + i, Nt + i]], -1)], -2)
+    Binv = np.linalg.inv(B)
+    P = np.zeros_like(A)
+    P[i, i], P[i, Nt + i] = Binv[:, 0, 0], Binv[:, 0, 1]
+    P[Nt + i, i], P[Nt + i, Nt + i] = Binv[:, 1, 0], Binv[:, 1, 1]
+    return P @ A, B
+
+
+def single_layer_potential_inside(O, a, k, N, rho, points, p) -> np.ndarray:
+    """Prop. 4.3 for points x inside disk p: the self term takes the
+    interior expansion (i pi a_p/2) H_m(k a_p) J_m(k r_p) exp(i m theta_p)
+    / sqrt(2 pi a_p) (Graf's theorem with the roles of x and y exchanged),
+    the other disks their exterior expansion."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    M = len(a)
+    n = 2 * N + 1
+    rho = np.asarray(rho)
+    squeeze = rho.ndim == 1
+    R = rho.reshape(M, n, -1)
+    pts = np.asarray(points, dtype=np.float64)
+    J, _, H, _ = bessel_diagonals(a, k, N)
+    m = modes(N)
+    u = np.zeros((len(pts), R.shape[2]), dtype=np.complex128)
+    for q in range(M):
+        d = pts - O[q][None, :]
+        r = np.hypot(d[:, 0], d[:, 1])
+        th = np.arctan2(d[:, 1], d[:, 0])
+        if q == p:
+            basis = special.jv(m[None, :], k * r[:, None]) * np.exp(1j * m[None, :] * th[:, None])
+            coef = 0.5j * np.pi * a[q] * H[q] / np.sqrt(2 * np.pi * a[q])
+        else:
+            basis = special.hankel1(m[None, :], k * r[:, None]) * np.exp(1j * m[None, :] * th[:, None])
+            coef = 0.5j * np.pi * a[q] * J[q] / np.sqrt(2 * np.pi * a[q])
+        u += basis @ (coef[:, None] * R[q])
+    return u[:, 0] if squeeze else u
 
 
 # --------------------------------------------------------------------------
