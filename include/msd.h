@@ -264,6 +264,37 @@ msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources,
 msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, int64_t P, const double* points,
                          void* u_out);
 
+/* Penetrable obstacles (section 7, Example II, the transmission problem):
+ * the wavenumber is k+ (the problem's k) outside the disks and k- inside,
+ * and u+ = L+ rho+ outside, u- = L- rho- inside (single layers at k+ and
+ * k-).  The unknowns (rho+, rho-) solve
+ *   L+ rho+ - L- rho- = -U,
+ *   (-I/2 + N+) rho+ - mu (I/2 + N-) rho- = -dU,
+ * i.e. u+ + u_inc = u- and d_n(u+ + u_inc) = mu d_n u- on every circle
+ * (mu per disk: the section 7 contrast of the normal derivatives).  The
+ * (2, 2) block carries the minus sign of the interior jump relation of
+ * Prop. 3.2 (printed without it).  Every row is preconditioned by the
+ * 2 x 2 self block of its mode, and a product runs the block-Toeplitz
+ * kernel once with the generators at k+ and once at k-.
+ * msd_set_penetrable:
+ *   k_minus  host [C] interior wavenumbers (> 0), NULL switches the mode off
+ *   mu       host [disk_off[C]] contrasts (> 0), NULL for all 1
+ *   needs the default formulation; MSD_ERR_NONFINITE when a 2 x 2 self
+ *   block is singular.  Keeps internal problems for the interior
+ *   wavenumber and the solver layout until switched off or destroyed.
+ * msd_penetrable_matvec: (y+, y-) = B^-1 A (x+, x-), B the 2 x 2 self
+ *   blocks; x+-, y+- device complex128 [N_tot][R]; MSD_FP64 only.
+ * msd_solve_penetrable: plane waves (Prop. 4.1, at k+) betas_host [C][R];
+ *   rho_plus, rho_minus host or device complex128 [N_tot][R]; options and
+ *   statistics as msd_solve_planewaves (true_relres not computed, -1).
+ *   The exterior scattered field of the solution is msd_farfield /
+ *   msd_nearfield of rho_plus. */
+msd_status msd_set_penetrable(msd_problem* pb, const double* k_minus, const double* mu);
+msd_status msd_penetrable_matvec(msd_problem* pb, int R, int precision, const void* xp, const void* xm, void* yp,
+                                 void* ym);
+msd_status msd_solve_penetrable(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts,
+                                void* rho_plus, void* rho_minus, msd_stats* stats_host);
+
 /* Integral-equation formulation (sections 3, 4.2, 5): replaces the default
  * rows (EFIE L rho = -U on sound-soft disks, (-I/2 + N) rho = -dU on
  * sound-hard ones, u = L rho) by linear combinations of the identity and

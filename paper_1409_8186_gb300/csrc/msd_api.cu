@@ -202,6 +202,19 @@ struct msd_problem {
     float2 *d_fl1_32 = nullptr, *d_fl2_32 = nullptr;
     double* d_frf2_64 = nullptr;
     float* d_frf2_32 = nullptr;
+    // penetrable obstacles (msd_set_penetrable): the same geometry at the
+    // interior wavenumber k- (its Bessel diagonals and generators), and the
+    // problem whose 2 M disk slots per configuration give the Krylov solver
+    // the row layout of (rho+, rho-); pen_parent is set on the latter
+    msd_problem* pen_minus = nullptr;
+    msd_problem* pen_shadow = nullptr;
+    msd_problem* pen_parent = nullptr;
+    DBuf penbuf;     // A64 [Ntot][4], A32 [Ntot][4], S64 [2][Ntot], mu [Mtot]
+    DBuf penio[4];   // transmission-layout vectors and right-hand sides
+    double2* d_penA64 = nullptr;
+    float2* d_penA32 = nullptr;
+    double2* d_penS = nullptr;
+    double* d_pen_mu = nullptr;
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
     double offdiag_L = 0, offdiag_n2 = 0;
@@ -272,6 +285,26 @@ void form_rows(msd_problem* pb) {
         fail(MSD_ERR_NONFINITE,
              "msd_set_formulation: the self block of the combination vanishes for some mode (a resonance of this "
              "formulation at k a_p)");
+}
+
+// Per-row transmission factors from the Bessel diagonals at k+ and k-.
+void pen_rows(msd_problem* pb) {
+    CK(cudaMemsetAsync(pb->d_flags, 0, sizeof(int), pb->stream));
+    msd_problem* pm = pb->pen_minus;
+    launch_pen_rows(pb->d_cfg, pm->d_cfg, pb->Mtot, pb->Ntot, pb->d_disk_cfg, pb->d_radius, pb->d_pen_mu, pb->d_J,
+                    pb->d_dJ, pb->d_H, pb->d_dH, pm->d_J, pm->d_dJ, pm->d_H, pm->d_dH, pb->d_penA64, pb->d_penA32,
+                    pb->d_penS, pb->d_flags, pb->stream);
+    CK_LAUNCH();
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, pb->d_flags, sizeof(int), cudaMemcpyDeviceToHost, pb->stream));
+    CK(cudaStreamSynchronize(pb->stream));
+    if (f & 1) fail(MSD_ERR_NONFINITE, "msd_set_penetrable: a 2 x 2 self block of the transmission system is singular");
+}
+
+void pen_release(msd_problem* pb) {
+    if (pb->pen_minus) msd_destroy(pb->pen_minus);
+    if (pb->pen_shadow) msd_destroy(pb->pen_shadow);
+    pb->pen_minus = pb->pen_shadow = nullptr;
 }
 
 // K2 over the whole problem: the stored generator array(s).
@@ -718,7 +751,41 @@ void matvec_form_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) 
     CK_LAUNCH();
 }
 
+// The transmission product (penetrable obstacles) of the parent problem pb
+// on vectors in the transmission layout: one block-Toeplitz product with
+// the generators at k+ (pb) and one at k- (pb->pen_minus), then
+// y = x + A [z+; z-].
+void pen_matvec(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
+    msd_problem* pm = pb->pen_minus;
+    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
+        fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
+    ensure_generators(pb, fp64);
+    ensure_generators(pm, fp64);
+    MatvecPlan& pp = get_plan(pb, R, fp64);
+    MatvecPlan& pq = get_plan(pm, R, fp64);
+    const size_t elem = fp64 ? 16 : 8;
+    const size_t nv = (size_t)pb->Ntot * R;
+    void* xsp = pb->xs.get(nv * elem);
+    void* xsm = pm->xs.get(nv * elem);
+    void* partp = pb->part.get((size_t)pp.nsplit * nv * elem);
+    void* partm = pm->part.get((size_t)pq.nsplit * nv * elem);
+    launch_pen_scale(fp64, pb->d_cfg, pb->C, pb->Ntot, R, fp64 ? (const void*)pb->d_rf64 : (const void*)pb->d_rf32,
+                     fp64 ? (const void*)pm->d_rf64 : (const void*)pm->d_rf32, x, xsp, xsm, pb->stream);
+    launch_bt_only(pp.ch, fp64, pb->d_cfg, pp.d_work, (int)pp.work.size(), pb->Nmax,
+                   fp64 ? (const void*)pb->d_G64 : (const void*)pb->d_G32, xsp, partp, pb->Ntot, R, pb->stream);
+    launch_bt_only(pq.ch, fp64, pm->d_cfg, pq.d_work, (int)pq.work.size(), pm->Nmax,
+                   fp64 ? (const void*)pm->d_G64 : (const void*)pm->d_G32, xsm, partm, pm->Ntot, R, pb->stream);
+    launch_pen_finalize(fp64, pb->d_cfg, pb->C, pb->Ntot, R,
+                        fp64 ? (const void*)pb->d_penA64 : (const void*)pb->d_penA32, x, partp, pp.nsplit, partm,
+                        pq.nsplit, y, pb->stream);
+    CK_LAUNCH();
+}
+
 void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
+    if (pb->pen_parent) {
+        pen_matvec(pb->pen_parent, R, fp64, x, y);
+        return;
+    }
     if (pb->form) {
         matvec_form_dev(pb, R, fp64, x, y);
         return;
@@ -1070,7 +1137,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
         if (pb->form) fail(MSD_ERR_ARG, "adjoint solves need the default formulation");
         ensure_adjoint(pb, true);
         if (mixed) ensure_adjoint(pb, false);
-    } else if (pb->gen_mode != MSD_GEN_RECOMPUTE || pb->form) {
+    } else if ((pb->gen_mode != MSD_GEN_RECOMPUTE || pb->form) && !pb->pen_parent) {
         ensure_generators(pb, true);
         if (mixed) ensure_generators(pb, false);
     }
@@ -1149,7 +1216,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     // unpreconditioned relative residual ||P r'|| / ||P b'|| from the final
     // FP64 residual r' of the preconditioned system
     std::vector<double> true_relres(S, -1.0);
-    if (!adjoint && R <= 64) {
+    if (!adjoint && R <= 64 && !pb->pen_parent) {
         const int nch = (int)pb->chunks.size();
         launch_weighted_norms(pb->d_cfg, pb->d_chunks, nch, R, pb->d_radius, pb->d_bc, pb->d_J, pb->d_H, pb->d_dH,
                               pb->form ? pb->d_fdiag : nullptr,
@@ -1351,6 +1418,10 @@ void msd_destroy(msd_problem* pb) {
     for (auto& b : pb->nfbuf) b.release();
     for (auto& b : pb->dortbuf) b.release();
     pb->fbuf.release();
+    if (pb->pen_minus) msd_destroy(pb->pen_minus);
+    if (pb->pen_shadow) msd_destroy(pb->pen_shadow);
+    pb->penbuf.release();
+    for (auto& b : pb->penio) b.release();
     delete pb;
 }
 
@@ -1443,6 +1514,11 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
         CK_LAUNCH();
         check_flags(pb, "msd_update_geometry");
         if (pb->form) form_rows(pb);
+        if (pb->pen_minus) {
+            const msd_status st = msd_update_geometry(pb->pen_minus, centres, radii, nullptr);
+            if (st != MSD_OK) fail(st, std::string("msd_update_geometry (interior wavenumber): ") + msd_last_error());
+            pen_rows(pb);
+        }
         pb->geom_version += 1;  // adjoint operator data is rebuilt on next use
         return MSD_OK;
     });
@@ -1670,6 +1746,124 @@ msd_status msd_solve_pointsources(msd_problem* pb, int R, const double* sources_
     });
 }
 
+msd_status msd_set_penetrable(msd_problem* pb, const double* k_minus, const double* mu) {
+    return guarded([&]() -> msd_status {
+        if (!pb || pb->pen_parent) fail(MSD_ERR_ARG, "msd_set_penetrable: bad handle");
+        if (!k_minus) {
+            pen_release(pb);
+            return MSD_OK;
+        }
+        if (pb->form) fail(MSD_ERR_ARG, "msd_set_penetrable: needs the default formulation");
+        const int C = pb->C, Mtot = pb->Mtot;
+        for (int c = 0; c < C; ++c)
+            if (!(k_minus[c] > 0) || !std::isfinite(k_minus[c])) fail(MSD_ERR_ARG, "msd_set_penetrable: k- must be positive");
+        std::vector<double> muv(Mtot, 1.0);
+        if (mu)
+            for (int d = 0; d < Mtot; ++d) {
+                if (!(mu[d] > 0) || !std::isfinite(mu[d])) fail(MSD_ERR_ARG, "msd_set_penetrable: mu must be positive");
+                muv[d] = mu[d];
+            }
+        std::vector<double> cen(2 * (size_t)Mtot), rad(Mtot);
+        CK(cudaMemcpyAsync(cen.data(), pb->d_centre, cen.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+        CK(cudaMemcpyAsync(rad.data(), pb->d_radius, rad.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+        CK(cudaStreamSynchronize(pb->stream));
+        std::vector<int> doff(C + 1), Nv(C), sdoff(C + 1);
+        std::vector<double> kp(C);
+        for (int c = 0; c < C; ++c) {
+            doff[c] = pb->cfg[c].disk_off;
+            Nv[c] = pb->cfg[c].N;
+            kp[c] = pb->cfg[c].k;
+        }
+        doff[C] = Mtot;
+        pen_release(pb);
+        std::vector<int8_t> bc0(2 * (size_t)Mtot, (int8_t)MSD_DIRICHLET);
+        msd_problem* pm = nullptr;
+        msd_status st = msd_create(C, doff.data(), cen.data(), rad.data(), bc0.data(), k_minus, Nv.data(), pb->stream, &pm);
+        if (st != MSD_OK) fail(st, std::string("msd_set_penetrable (interior wavenumber): ") + msd_last_error());
+        pb->pen_minus = pm;
+        // Krylov layout: 2 M disk slots per configuration, placed apart on a
+        // line (their geometry is never used)
+        std::vector<double> scen, srad;
+        sdoff[0] = 0;
+        for (int c = 0; c < C; ++c) {
+            const int M = doff[c + 1] - doff[c];
+            double amax = 0;
+            for (int d = doff[c]; d < doff[c + 1]; ++d) amax = std::max(amax, rad[d]);
+            for (int j = 0; j < 2 * M; ++j) {
+                scen.push_back(j * (2.0 * amax + 1.0));
+                scen.push_back(0.0);
+                srad.push_back(rad[doff[c] + (j % M)]);
+            }
+            sdoff[c + 1] = sdoff[c] + 2 * M;
+        }
+        msd_problem* sh = nullptr;
+        st = msd_create(C, sdoff.data(), scen.data(), srad.data(), bc0.data(), kp.data(), Nv.data(), pb->stream, &sh);
+        if (st != MSD_OK) fail(st, std::string("msd_set_penetrable (solver layout): ") + msd_last_error());
+        sh->pen_parent = pb;
+        pb->pen_shadow = sh;
+        const size_t n = (size_t)pb->Ntot;
+        char* b = (char*)pb->penbuf.get(n * 4 * 16 + n * 4 * 8 + 2 * n * 16 + (size_t)Mtot * 8);
+        pb->d_penA64 = (double2*)b;
+        pb->d_penA32 = (float2*)(pb->d_penA64 + 4 * n);
+        pb->d_penS = (double2*)(pb->d_penA32 + 4 * n);
+        pb->d_pen_mu = (double*)(pb->d_penS + 2 * n);
+        CK(cudaMemcpyAsync(pb->d_pen_mu, muv.data(), (size_t)Mtot * 8, cudaMemcpyHostToDevice, pb->stream));
+        pen_rows(pb);
+        return MSD_OK;
+    });
+}
+
+msd_status msd_penetrable_matvec(msd_problem* pb, int R, int precision, const void* xp, const void* xm, void* yp,
+                                 void* ym) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !pb->pen_shadow || R <= 0 || !xp || !xm || !yp || !ym)
+            fail(MSD_ERR_ARG, "msd_penetrable_matvec: bad argument (msd_set_penetrable first)");
+        if (precision != MSD_FP64)
+            fail(MSD_ERR_ARG, "msd_penetrable_matvec: MSD_FP64 only (FP32 products run inside mixed-precision solves)");
+        for (const void* p : {xp, xm, (const void*)yp, (const void*)ym})
+            if (!is_device_ptr(p)) fail(MSD_ERR_ARG, "msd_penetrable_matvec: device memory expected");
+        const size_t nv = (size_t)pb->Ntot * R;
+        double2* X = (double2*)pb->penio[0].get(2 * nv * 16);
+        double2* Y = (double2*)pb->penio[1].get(2 * nv * 16);
+        launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, true, X, (double2*)xp, (double2*)xm, pb->stream);
+        pen_matvec(pb, R, true, X, Y);
+        launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, false, Y, (double2*)yp, (double2*)ym, pb->stream);
+        CK_LAUNCH();
+        CK(cudaStreamSynchronize(pb->stream));
+        return MSD_OK;
+    });
+}
+
+msd_status msd_solve_penetrable(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts,
+                                void* rho_plus, void* rho_minus, msd_stats* stats_host) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !pb->pen_shadow || R <= 0 || !betas_host || !rho_plus || !rho_minus)
+            fail(MSD_ERR_ARG, "msd_solve_penetrable: bad argument (msd_set_penetrable first)");
+        cudaStream_t s = pb->stream;
+        const size_t nv = (size_t)pb->Ntot * R;
+        double* d_betas = (double*)pb->penio[3].get((size_t)pb->C * R * 8);
+        CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
+        double2* bp = (double2*)pb->penio[0].get(2 * nv * 16);
+        double2* bm = bp + nv;
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS, pb->Nmax, R,
+                             d_betas, bp, s);
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS + pb->Ntot,
+                             pb->Nmax, R, d_betas, bm, s);
+        double2* b = (double2*)pb->penio[1].get(2 * nv * 16);
+        launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, true, b, bp, bm, s);
+        CK_LAUNCH();
+        double2* x = (double2*)pb->penio[2].get(2 * nv * 16);
+        const msd_status st = solve_impl(pb->pen_shadow, R, nullptr, opts, x, stats_host, b);
+        OutStage op(pb, pb->nfbuf[0], rho_plus, nv * 16), om(pb, pb->nfbuf[3], rho_minus, nv * 16);
+        launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, false, x, (double2*)op.dev, (double2*)om.dev, s);
+        CK_LAUNCH();
+        op.finish();
+        om.finish();
+        CK(cudaStreamSynchronize(s));
+        return st;
+    });
+}
+
 msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const double* rhs_weights,
                                const double* rep_weights) {
     return guarded([&]() -> msd_status {
@@ -1679,6 +1873,7 @@ msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const 
             return MSD_OK;
         }
         if (!rhs_weights || !rep_weights) fail(MSD_ERR_ARG, "msd_set_formulation: bad argument");
+        if (pb->pen_minus) fail(MSD_ERR_ARG, "msd_set_formulation: not with penetrable obstacles");
         MsdFormulation w{};
         for (int c = 0; c < 2; ++c) {
             for (int o = 0; o < 5; ++o)

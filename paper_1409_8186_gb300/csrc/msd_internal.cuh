@@ -149,6 +149,26 @@ void launch_weighted_norms(const MsdConfig* d_cfg, const RowChunk* d_chunks, int
                            const double2* dH, const double2* diag, const double2* u, const double2* v,
                            double2* part, cudaStream_t s);
 
+// Penetrable obstacles (section 7): per parent row the 2 x 2 factor A =
+// B^-1 C of the combined product (A64, A32 [Ntot][4]: A11, A12, A21, A22) and
+// the right-hand-side scales S64 [2][Ntot] (B^-1 [-J+; -k+ J+']), from the
+// Bessel diagonals at k+ (p) and k- (m) and mu per disk; flags bit 0 when a
+// factor is not finite.
+void launch_pen_rows(const MsdConfig* cfg_p, const MsdConfig* cfg_m, int Mtot, long long Ntot, const int* disk_cfg,
+                     const double* radius, const double* mu, const double2* Jp, const double2* dJp,
+                     const double2* Hp, const double2* dHp, const double2* Jm, const double2* dJm,
+                     const double2* Hm, const double2* dHm, double2* A64, float2* A32, double2* S64, int* flags,
+                     cudaStream_t s);
+// xs+- = sqrt(a) J+- rho+- (parent layout) from x in the transmission layout
+void launch_pen_scale(bool fp64, const MsdConfig* cfg, int C, long long Ntot, int R, const void* rfp,
+                      const void* rfm, const void* x, void* xsp, void* xsm, cudaStream_t s);
+// y = x + A [z+; z-] in the transmission layout
+void launch_pen_finalize(bool fp64, const MsdConfig* cfg, int C, long long Ntot, int R, const void* A, const void* x,
+                         const void* partp, int nsp, const void* partm, int nsm, void* y, cudaStream_t s);
+// transmission layout <-> (rho+, rho-) in the parent layout (FP64)
+void launch_pen_layout(const MsdConfig* cfg, int C, long long Ntot, int R, bool to_pen, double2* pen, double2* xp,
+                       double2* xm, cudaStream_t s);
+
 // Integral-equation formulation (sections 3, 4.2, 5): per boundary
 // condition c (0 Dirichlet, 1 Neumann) the weights of I, L, M, N, D in the
 // rows of its disks and of U, dU in their right-hand side, and the weights

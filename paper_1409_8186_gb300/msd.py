@@ -79,6 +79,9 @@ def _load():
         "msd_dort": (I, [P, I, ctypes.POINTER(msd_opts), P, P, P, P]),
         "msd_dort_eigen": (I, [P, I, P, P, P]),
         "msd_set_formulation": (I, [P, P, P, P]),
+        "msd_set_penetrable": (I, [P, P, P]),
+        "msd_penetrable_matvec": (I, [P, I, I, P, P, P, P]),
+        "msd_solve_penetrable": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
     }
@@ -95,7 +98,8 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
-            "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_last_error")
+            "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_penetrable",
+            "msd_penetrable_matvec", "msd_solve_penetrable", "msd_last_error")
 
 
 def library_path() -> str:
@@ -277,6 +281,26 @@ def msd_set_formulation(h, op_weights, rhs_weights, rep_weights) -> None:
     rw = np.ascontiguousarray(np.asarray(rhs_weights, np.complex128).reshape(2, 2)).view(np.float64)
     pw = np.ascontiguousarray(np.asarray(rep_weights, np.complex128).reshape(2)).view(np.float64)
     _check(_lib.msd_set_formulation(h, _ptr(ow), _ptr(rw), _ptr(pw)))
+
+
+def msd_set_penetrable(h, k_minus, mu=None) -> None:
+    if k_minus is None:
+        _check(_lib.msd_set_penetrable(h, None, None))
+        return
+    km = np.ascontiguousarray(np.atleast_1d(k_minus), dtype=np.float64)
+    m = None if mu is None else np.ascontiguousarray(mu, dtype=np.float64)
+    _check(_lib.msd_set_penetrable(h, _ptr(km), _ptr(m) if m is not None else None))
+
+
+def msd_penetrable_matvec(h, R: int, precision: int, xp, xm, yp, ym) -> None:
+    _check(_lib.msd_penetrable_matvec(h, R, precision, _ptr(xp), _ptr(xm), _ptr(yp), _ptr(ym)))
+
+
+def msd_solve_penetrable(h, R: int, betas, opts: msd_opts | None, rho_plus, rho_minus, stats_out=None) -> int:
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    return _check(_lib.msd_solve_penetrable(h, R, _ptr(b), ctypes.byref(opts) if opts else None, _ptr(rho_plus),
+                                            _ptr(rho_minus), ctypes.addressof(stats_out) if stats_out is not None
+                                            else None), allow_positive=True)
 
 
 _OPS = ("I", "L", "M", "N", "D")
@@ -503,6 +527,37 @@ class Problem:
         else:
             op, rhs, rep = formulation(kind, **kw)
         msd_set_formulation(self.handle, op, rhs, rep)
+
+    def set_penetrable(self, k_minus, mu=None):
+        """Penetrable obstacles (section 7): interior wavenumber(s) k_minus
+        (scalar or [C]) and per-disk contrasts mu (None: 1); k_minus None
+        switches back to sound-soft/sound-hard disks."""
+        if k_minus is not None:
+            k_minus = np.broadcast_to(np.asarray(k_minus, np.float64), (self.C,))
+        msd_set_penetrable(self.handle, k_minus, mu)
+
+    def penetrable_matvec(self, xp, xm):
+        """(y+, y-) = B^-1 A (x+, x-) of the transmission system (FP64)."""
+        R = xp.shape[1] if xp.dim() == 2 else 1
+        yp, ym = xp.new_empty(xp.shape), xm.new_empty(xm.shape)
+        msd_penetrable_matvec(self.handle, R, MSD_FP64, xp, xm, yp, ym)
+        return yp, ym
+
+    def solve_penetrable(self, betas, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64):
+        """Returns (rho_plus, rho_minus, SolveResult); the exterior field is
+        farfield / nearfield of rho_plus."""
+        import torch
+        b = self._betas(betas)
+        R = b.shape[1]
+        o = msd_opts(tol, restart, maxit, 0, 0.0, precision, MSD_GEN_AUTO)
+        rp = torch.empty((self.ntot, R), dtype=torch.complex128, device="cuda")
+        rm = torch.empty_like(rp)
+        stats = (msd_stats * (self.C * R))()
+        st = msd_solve_penetrable(self.handle, R, b, o, rp, rm, stats)
+        res = SolveResult(rp, st, np.array([s.flag for s in stats]), np.array([s.iters for s in stats]),
+                          np.array([s.refine_steps for s in stats]), np.array([s.relres for s in stats]),
+                          np.array([s.true_relres for s in stats]), float(stats[0].solve_ms) if len(stats) else 0.0)
+        return rp, rm, res
 
     def dort_eigen(self, F, want_T=False):
         """T = conj(F)^T F and its eigenvalues (largest first) for caller
