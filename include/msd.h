@@ -288,12 +288,17 @@ msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, in
  *   rho_plus, rho_minus host or device complex128 [N_tot][R]; options and
  *   statistics as msd_solve_planewaves (true_relres not computed, -1).
  *   The exterior scattered field of the solution is msd_farfield /
- *   msd_nearfield of rho_plus. */
+ *   msd_nearfield of rho_plus.
+ * msd_solve_penetrable_pointsources: the same with the point-source
+ *   incident waves (i/4) H_0(k+ |x - s|) of section 4.3, sources [C][R][2]
+ *   host (outside every disk). */
 msd_status msd_set_penetrable(msd_problem* pb, const double* k_minus, const double* mu);
 msd_status msd_penetrable_matvec(msd_problem* pb, int R, int precision, const void* xp, const void* xm, void* yp,
                                  void* ym);
 msd_status msd_solve_penetrable(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts,
                                 void* rho_plus, void* rho_minus, msd_stats* stats_host);
+msd_status msd_solve_penetrable_pointsources(msd_problem* pb, int R, const double* sources, const msd_opts* opts,
+                                             void* rho_plus, void* rho_minus, msd_stats* stats_host);
 
 /* Integral-equation formulation (sections 3, 4.2, 5): replaces the default
  * rows (EFIE L rho = -U on sound-soft disks, (-I/2 + N) rho = -dU on

@@ -679,6 +679,18 @@ def rhs_penetrable(O, a, k_plus, N, betas) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
+def rhs_penetrable_pointsource(O, a, k_plus, N, sources) -> np.ndarray:
+    """Section 7 with the point-source incident wave of section 4.3:
+    [-U; -dU] with U = d' J, dU = k+ d' J' at k+.  [2 N_tot, R]."""
+    a = np.asarray(a, dtype=np.float64)
+    J, dJ, _, _ = bessel_diagonals(a, k_plus, N)
+    cols = []
+    for s in np.atleast_2d(np.asarray(sources, dtype=np.float64)):
+        d = pointsource_coefficients(O, a, k_plus, N, s)
+        cols.append(np.concatenate([-(d * J).reshape(-1), -(k_plus * d * dJ).reshape(-1)]))
+    return np.stack(cols, axis=1)
+
+
 def solve_penetrable(O, a, k_plus, k_minus, mu, N, betas):
     """LU solve of the transmission system; returns (rho+, rho-), each
     [N_tot, R]."""

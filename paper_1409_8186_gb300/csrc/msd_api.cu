@@ -1834,33 +1834,66 @@ msd_status msd_penetrable_matvec(msd_problem* pb, int R, int precision, const vo
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+// Transmission solve for plane waves (betas_host [C][R]) or point sources
+// (sources_host [C][R][2]).
+msd_status solve_penetrable_impl(msd_problem* pb, int R, const double* betas_host, const double* sources_host,
+                                 const msd_opts* opts, void* rho_plus, void* rho_minus, msd_stats* stats_host) {
+    if (!pb || !pb->pen_shadow || R <= 0 || (!betas_host && !sources_host) || !rho_plus || !rho_minus)
+        fail(MSD_ERR_ARG, "msd_solve_penetrable: bad argument (msd_set_penetrable first)");
+    cudaStream_t s = pb->stream;
+    const size_t nv = (size_t)pb->Ntot * R;
+    double2* bp = (double2*)pb->penio[0].get(2 * nv * 16);
+    double2* bm = bp + nv;
+    if (betas_host) {
+        double* d_betas = (double*)pb->penio[3].get((size_t)pb->C * R * 8);
+        CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS, pb->Nmax,
+                             R, d_betas, bp, s);
+        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS + pb->Ntot,
+                             pb->Nmax, R, d_betas, bm, s);
+    } else {
+        double2* d_src = (double2*)pb->penio[3].get((size_t)pb->C * R * 16);
+        CK(cudaMemcpyAsync(d_src, sources_host, (size_t)pb->C * R * 16, cudaMemcpyHostToDevice, s));
+        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS, R, d_src,
+                               bp, s);
+        launch_rhs_pointsource(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius,
+                               pb->d_penS + pb->Ntot, R, d_src, bm, s);
+    }
+    double2* b = (double2*)pb->penio[1].get(2 * nv * 16);
+    launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, true, b, bp, bm, s);
+    CK_LAUNCH();
+    double2* x = (double2*)pb->penio[2].get(2 * nv * 16);
+    const msd_status st = solve_impl(pb->pen_shadow, R, nullptr, opts, x, stats_host, b);
+    OutStage op(pb, pb->nfbuf[0], rho_plus, nv * 16), om(pb, pb->nfbuf[3], rho_minus, nv * 16);
+    launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, false, x, (double2*)op.dev, (double2*)om.dev, s);
+    CK_LAUNCH();
+    op.finish();
+    om.finish();
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
 msd_status msd_solve_penetrable(msd_problem* pb, int R, const double* betas_host, const msd_opts* opts,
                                 void* rho_plus, void* rho_minus, msd_stats* stats_host) {
     return guarded([&]() -> msd_status {
-        if (!pb || !pb->pen_shadow || R <= 0 || !betas_host || !rho_plus || !rho_minus)
-            fail(MSD_ERR_ARG, "msd_solve_penetrable: bad argument (msd_set_penetrable first)");
-        cudaStream_t s = pb->stream;
-        const size_t nv = (size_t)pb->Ntot * R;
-        double* d_betas = (double*)pb->penio[3].get((size_t)pb->C * R * 8);
-        CK(cudaMemcpyAsync(d_betas, betas_host, (size_t)pb->C * R * 8, cudaMemcpyHostToDevice, s));
-        double2* bp = (double2*)pb->penio[0].get(2 * nv * 16);
-        double2* bm = bp + nv;
-        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS, pb->Nmax, R,
-                             d_betas, bp, s);
-        launch_rhs_planewave(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_centre, pb->d_radius, pb->d_penS + pb->Ntot,
-                             pb->Nmax, R, d_betas, bm, s);
-        double2* b = (double2*)pb->penio[1].get(2 * nv * 16);
-        launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, true, b, bp, bm, s);
-        CK_LAUNCH();
-        double2* x = (double2*)pb->penio[2].get(2 * nv * 16);
-        const msd_status st = solve_impl(pb->pen_shadow, R, nullptr, opts, x, stats_host, b);
-        OutStage op(pb, pb->nfbuf[0], rho_plus, nv * 16), om(pb, pb->nfbuf[3], rho_minus, nv * 16);
-        launch_pen_layout(pb->d_cfg, pb->C, pb->Ntot, R, false, x, (double2*)op.dev, (double2*)om.dev, s);
-        CK_LAUNCH();
-        op.finish();
-        om.finish();
-        CK(cudaStreamSynchronize(s));
-        return st;
+        if (!betas_host) fail(MSD_ERR_ARG, "msd_solve_penetrable: betas_host is NULL");
+        return solve_penetrable_impl(pb, R, betas_host, nullptr, opts, rho_plus, rho_minus, stats_host);
+    });
+}
+
+msd_status msd_solve_penetrable_pointsources(msd_problem* pb, int R, const double* sources, const msd_opts* opts,
+                                             void* rho_plus, void* rho_minus, msd_stats* stats_host) {
+    return guarded([&]() -> msd_status {
+        if (!sources) fail(MSD_ERR_ARG, "msd_solve_penetrable_pointsources: sources is NULL");
+        return solve_penetrable_impl(pb, R, nullptr, sources, opts, rho_plus, rho_minus, stats_host);
     });
 }
 

@@ -82,6 +82,7 @@ def _load():
         "msd_set_penetrable": (I, [P, P, P]),
         "msd_penetrable_matvec": (I, [P, I, I, P, P, P, P]),
         "msd_solve_penetrable": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
+        "msd_solve_penetrable_pointsources": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_last_error": (ctypes.c_char_p, []),
     }
@@ -99,7 +100,8 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
             "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_penetrable",
-            "msd_penetrable_matvec", "msd_solve_penetrable", "msd_last_error")
+            "msd_penetrable_matvec", "msd_solve_penetrable", "msd_solve_penetrable_pointsources",
+            "msd_last_error")
 
 
 def library_path() -> str:
@@ -301,6 +303,15 @@ def msd_solve_penetrable(h, R: int, betas, opts: msd_opts | None, rho_plus, rho_
     return _check(_lib.msd_solve_penetrable(h, R, _ptr(b), ctypes.byref(opts) if opts else None, _ptr(rho_plus),
                                             _ptr(rho_minus), ctypes.addressof(stats_out) if stats_out is not None
                                             else None), allow_positive=True)
+
+
+def msd_solve_penetrable_pointsources(h, R: int, sources, opts: msd_opts | None, rho_plus, rho_minus,
+                                      stats_out=None) -> int:
+    src = np.ascontiguousarray(sources, dtype=np.float64)
+    return _check(_lib.msd_solve_penetrable_pointsources(h, R, _ptr(src), ctypes.byref(opts) if opts else None,
+                                                         _ptr(rho_plus), _ptr(rho_minus),
+                                                         ctypes.addressof(stats_out) if stats_out is not None
+                                                         else None), allow_positive=True)
 
 
 _OPS = ("I", "L", "M", "N", "D")
@@ -543,17 +554,24 @@ class Problem:
         msd_penetrable_matvec(self.handle, R, MSD_FP64, xp, xm, yp, ym)
         return yp, ym
 
-    def solve_penetrable(self, betas, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64):
-        """Returns (rho_plus, rho_minus, SolveResult); the exterior field is
+    def solve_penetrable(self, betas=None, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64, sources=None):
+        """Plane waves (betas) or point sources ([R, 2] or [C, R, 2]).
+        Returns (rho_plus, rho_minus, SolveResult); the exterior field is
         farfield / nearfield of rho_plus."""
         import torch
-        b = self._betas(betas)
+        if sources is not None:
+            b = self._sources(sources)
+        else:
+            b = self._betas(betas)
         R = b.shape[1]
         o = msd_opts(tol, restart, maxit, 0, 0.0, precision, MSD_GEN_AUTO)
         rp = torch.empty((self.ntot, R), dtype=torch.complex128, device="cuda")
         rm = torch.empty_like(rp)
         stats = (msd_stats * (self.C * R))()
-        st = msd_solve_penetrable(self.handle, R, b, o, rp, rm, stats)
+        if sources is not None:
+            st = msd_solve_penetrable_pointsources(self.handle, R, b, o, rp, rm, stats)
+        else:
+            st = msd_solve_penetrable(self.handle, R, b, o, rp, rm, stats)
         res = SolveResult(rp, st, np.array([s.flag for s in stats]), np.array([s.iters for s in stats]),
                           np.array([s.refine_steps for s in stats]), np.array([s.relres for s in stats]),
                           np.array([s.true_relres for s in stats]), float(stats[0].solve_ms) if len(stats) else 0.0)

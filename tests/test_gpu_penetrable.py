@@ -125,3 +125,20 @@ def test_mode_switches(msd):
     with pytest.raises(msd.MsdError):
         pb.set_penetrable(2.0)
     pb.close()
+
+
+def test_point_source_solve(msd):
+    cl = W.small_mixed(seed=5, M=3, N=14, k=1.6)
+    km, mu = 2.4, np.array([1.0, 1.5, 0.7])
+    src = np.array([[9.0, -7.5], [-6.0, 8.0]])
+    A = O_.assemble_penetrable(cl.centres, cl.radii, cl.k, km, mu, cl.N)
+    ref = np.linalg.solve(A, O_.rhs_penetrable_pointsource(cl.centres, cl.radii, cl.k, cl.N, src))
+    P, _ = O_.preconditioned_penetrable(cl.centres, cl.radii, cl.k, km, mu, cl.N)
+    tol = 10 * np.linalg.cond(P) * 1e-12
+    pb = msd.Problem(cl)
+    pb.set_penetrable(km, mu)
+    rp, rm, res = pb.solve_penetrable(sources=src, tol=1e-12)
+    assert res.status == msd.MSD_OK
+    got = np.concatenate([rp.cpu().numpy(), rm.cpu().numpy()])
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    pb.close()

@@ -136,3 +136,26 @@ def test_energy_balance_lossless():
     lhs = np.sum(np.abs(F[:T]) ** 2) * 2 * np.pi / T
     rhs = -2 * np.sqrt(2 * np.pi / cl.k) * np.real(np.exp(1j * np.pi / 4) * F[T])
     assert abs(lhs - rhs) <= 1e-10 * lhs
+
+
+def test_point_source_transmission_conditions():
+    """A point source outside a 3-disk cluster: the solution's exterior total
+    field (with u_inc = (i/4) H_0(k+|x - s|)) and interior field satisfy the
+    projected transmission conditions on every circle."""
+    cl = W.small_mixed(seed=5, M=3, N=14, k=1.6)
+    km, mu = 2.4, np.array([1.0, 1.5, 0.7])
+    src = np.array([9.0, -7.5])
+    A = O_.assemble_penetrable(cl.centres, cl.radii, cl.k, km, mu, cl.N)
+    x = np.linalg.solve(A, O_.rhs_penetrable_pointsource(cl.centres, cl.radii, cl.k, cl.N, [src]))[:, 0]
+    Nt = cl.ntot
+    t = 2 * np.pi * np.arange(256) / 256
+    for p in range(cl.M):
+        nrm = np.stack([np.cos(t), np.sin(t)], axis=1)
+        xo = cl.centres[p][None, :] + cl.radii[p] * (1 + 1e-13) * nrm
+        xi = cl.centres[p][None, :] + cl.radii[p] * (1 - 1e-13) * nrm
+        d = xo - src[None, :]
+        r = np.hypot(d[:, 0], d[:, 1])
+        ui = 0.25j * special.hankel1(0, cl.k * r)
+        up = O_.single_layer_potential(cl.centres, cl.radii, cl.k, cl.N, x[:Nt], xo) + ui
+        um = O_.single_layer_potential_inside(cl.centres, cl.radii, km, cl.N, x[Nt:], xi, p)
+        assert np.abs(project(up - um, cl.radii[p], cl.N, t)).max() <= 1e-11 * np.abs(up).max()
