@@ -7,7 +7,7 @@
 // diagonal onto a multiple of e_1 with H = I - tau v v^H and applies
 // H B H = B - v w^H - w v^H to the trailing block B, p = tau B v,
 // w = p - (tau/2)(v^H p) v), all steps in one persistent cooperative launch
-// with grid barriers between the two phases of a step.  A diagonal unitary
+// with one grid barrier per step (between p and its use).  A diagonal unitary
 // similarity makes the off-diagonal entries real and non-negative (their
 // moduli), and the eigenvalues of that real symmetric tridiagonal matrix
 // are bracketed by Sturm counts (the number of sign changes of the leading
