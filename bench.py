@@ -448,6 +448,47 @@ def formulation_timing(reps: int = 5):
     pb.close()
 
 
+def penetrable_timing(reps: int = 5):
+    """Penetrable obstacles on the geometry of the paper's example (400 unit
+    disks on a square lattice of spacing 3 without its middle row and column,
+    k+ = 1, k- = 2, N = 10, a point source at the origin): the transmission
+    product (two block-Toeplitz launches, CUDA events around the C-ABI call
+    with device buffers) and the FP64 and mixed solves to relres 1e-10."""
+    import numpy as np
+    import torch
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cl = W.penetrable_lattice()
+    pb = msd.Problem(cl)
+    pb.set_penetrable(2.0)
+    rng = np.random.default_rng(0)
+    xp = torch.from_numpy(rng.standard_normal((cl.ntot, 1)) + 1j * rng.standard_normal((cl.ntot, 1))).cuda()
+    xm = torch.from_numpy(rng.standard_normal((cl.ntot, 1)) + 1j * rng.standard_normal((cl.ntot, 1))).cuda()
+    pb.penetrable_matvec(xp, xm)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        pb.penetrable_matvec(xp, xm)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": f"penetrable lattice (M={cl.M}, N={cl.N}, k+=1, k-=2)", "unknowns": 2 * int(pb.ntot),
+                      "what": "FP64 transmission product, R=1", "product_ms": round(e0.elapsed_time(e1) / reps, 3)}),
+          flush=True)
+    th = W.angles(360)
+    for prec, name in ((msd.MSD_FP64, "fp64"), (msd.MSD_MIXED, "mixed")):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rp, _, res = pb.solve_penetrable(sources=[[0.0, 0.0]], tol=1e-10, precision=prec)
+        F = pb.farfield(rp, th)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": f"penetrable lattice (M={cl.M}, N={cl.N}, k+=1, k-=2), point source at 0",
+                          "precision": name, "solve_and_farfield_ms": round(e0.elapsed_time(e1), 1),
+                          "iters": int(res.iters[0]), "relres": float(res.relres[0]), "status": int(res.status),
+                          "rcs_db_at_0": float(10 * np.log10(2 * np.pi * abs(F[0, 0, 0].item()) ** 2))}), flush=True)
+    pb.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,6 +506,8 @@ def main():
                     help="print FP64 and mixed batched solve times (JSON lines) instead")
     ap.add_argument("--nearfield", action="store_true",
                     help="print the timing (JSON line) of the near field on a grid instead")
+    ap.add_argument("--penetrable", action="store_true",
+                    help="print product and solve times (JSON lines) of the penetrable example instead")
     ap.add_argument("--formulations", action="store_true",
                     help="print product and solve times (JSON lines) of the integral-equation formulations instead")
     ap.add_argument("--dort", action="store_true",
@@ -474,6 +517,8 @@ def main():
         return dort_timing()
     if args.formulations:
         return formulation_timing()
+    if args.penetrable:
+        return penetrable_timing()
     if args.nearfield:
         return nearfield_timing()
     if args.batched:

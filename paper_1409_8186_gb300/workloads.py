@@ -180,6 +180,17 @@ def dort_three_disks(bc: int = DIRICHLET) -> Cluster:
     return Cluster(O, a, np.full(3, bc, np.int8), 2.0 * np.pi, 4, "dort3")
 
 
+def penetrable_lattice(half: int = 10, spacing: float = 3.0) -> Cluster:
+    """The penetrable example's geometry (section 7, Example II): unit disks
+    on the (2 half + 1)^2 square lattice of the given spacing centred on the
+    origin, without its middle row and column (400 disks for half = 10),
+    exterior k = 1, N = 10 (the interior wavenumber 2 is set separately)."""
+    idx = [i for i in range(-half, half + 1) if i != 0]
+    O = np.array([[i * spacing, j * spacing] for j in idx for i in idx], dtype=np.float64)
+    M = len(O)
+    return Cluster(O, np.ones(M), np.zeros(M, np.int8), 1.0, 10, f"penetrable_lattice{M}")
+
+
 def small_mixed(seed: int = 11, M: int = 6, N: int = 10, k: float = 2.3,
                 half_side: float = 8.0) -> Cluster:
     """Small mixed Dirichlet/Neumann cluster for unit tests."""
