@@ -478,7 +478,7 @@ def penetrable_timing(reps: int = 5):
     for prec, name in ((msd.MSD_FP64, "fp64"), (msd.MSD_MIXED, "mixed")):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        rp, _, res = pb.solve_penetrable(sources=[[0.0, 0.0]], tol=1e-10, precision=prec)
+        rp, _, res = pb.solve_penetrable(sources=[[0.0, 0.0]], tol=1e-10, precision=prec, maxit=8000)
         F = pb.farfield(rp, th)
         e1.record()
         torch.cuda.synchronize()
