@@ -5,6 +5,11 @@
  * for M disks (paper: mu-diff, arXiv 1409.8186, section 5, eq. for
  * L rho = -U and its sound-hard counterpart) on one GPU, with the
  * block-Toeplitz matrix-vector product of section 5 as the hot path.
+ * Around it: plane-wave and point-source right-hand sides (Prop. 4.1,
+ * section 4.3), the far field (section 4.4) and near field (Prop. 4.3), the
+ * adjoint gradient of a far-field misfit, other integral equations as
+ * combinations of I, L, M, N, D (sections 3 and 4.2), penetrable obstacles
+ * and the time-reversal matrix (section 7).
  *
  * Notation (section 4.1): disk p has centre O_p, radius a_p and a boundary
  * condition flag; every disk of a configuration carries the Fourier modes
