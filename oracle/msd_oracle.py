@@ -453,6 +453,23 @@ def time_reversal_matrix(F) -> np.ndarray:
     return F.conj().T @ F
 
 
+def dort_eigenvectors(T):
+    """Section 7: eigenvalues (largest first) and eigenvectors (columns) of
+    the Hermitian T (LAPACK)."""
+    lam, V = np.linalg.eigh(T)
+    return lam[::-1], V[:, ::-1]
+
+
+def herglotz_wave(k, alphas, g, points) -> np.ndarray:
+    """Section 7: the discrete Herglotz wave of parameter g emitted by the
+    mirror, u_I(x) = sum_j h_alpha g_j exp(i k (x1 cos alpha_j + x2 sin alpha_j)),
+    h_alpha = 2 pi / n_alpha.  points [P, 2] -> [P]."""
+    alphas = np.asarray(alphas, dtype=np.float64)
+    pts = np.asarray(points, dtype=np.float64)
+    E = np.exp(1j * k * (np.outer(pts[:, 0], np.cos(alphas)) + np.outer(pts[:, 1], np.sin(alphas))))
+    return (2 * np.pi / len(alphas)) * (E @ np.asarray(g))
+
+
 def dort_eigenvalues(T) -> np.ndarray:
     """Section 7: the eigenvalues of T (LAPACK Hermitian solver), largest
     first."""

@@ -15,8 +15,10 @@ quantities they do not use.
   (n_alpha = 512), with a gap of more than 500 to the rest.
 * T is Hermitian positive semi-definite and its eigenvalues are the squared
   singular values of F.
+* The Herglotz waves of the three significant eigenvectors of the example
+  focus each on one obstacle (selective focusing).
 * Planted mistakes (far field measured in the emitting direction, T without
-  the conjugate) fail these pins.
+  the conjugate, the conjugate Herglotz parameter) fail these pins.
 """
 import numpy as np
 from scipy import special
@@ -95,3 +97,31 @@ def test_three_small_disks_significant_eigenvalues():
         assert len(ex) == count
         assert np.abs(lam[:count] / ex - 1).max() < 0.05, (bc, lam[:count] / ex)
         assert lam[count] < lam[count - 1] / 500, (bc, lam[count] / lam[count - 1])
+
+
+def test_eigenvectors_focus_on_each_obstacle():
+    """Section 7: the Herglotz wave of each of the three significant
+    eigenvectors (three small sound-soft disks, 512 angles) peaks on one
+    obstacle, a different one for each, largest eigenvalue on the largest
+    disk, and stays below 30 % of its peak on the other two.  Planted
+    mistake: the conjugate parameter focuses at -O_p, on no obstacle."""
+    cl = W.dort_three_disks(0)
+    n = 512
+    alphas, F = O_.dort_far_field_matrix(cl.centres, cl.radii, cl.bc, cl.k, cl.N, n)
+    lam, V = O_.dort_eigenvectors(O_.time_reversal_matrix(F))
+    assert np.allclose(lam, O_.dort_eigenvalues(O_.time_reversal_matrix(F)), rtol=0, atol=1e-9 * lam[0])
+    g = np.linspace(-25, 25, 201)
+    X, Y = np.meshgrid(g, g)
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    wavelength = 2 * np.pi / cl.k
+    for e in range(3):
+        u = np.abs(O_.herglotz_wave(cl.k, alphas, V[:, e], pts))
+        peak = pts[u.argmax()]
+        d = np.hypot(cl.centres[:, 0] - peak[0], cl.centres[:, 1] - peak[1])
+        assert d.argmin() == e and d.min() <= 0.1 * wavelength, (e, peak)
+        at = np.abs(O_.herglotz_wave(cl.k, alphas, V[:, e], cl.centres))
+        others = np.delete(at, e)
+        assert others.max() < 0.3 * u.max(), (e, at / u.max())
+        u_bad = np.abs(O_.herglotz_wave(cl.k, alphas, V[:, e].conj(), pts))
+        bad = pts[u_bad.argmax()]
+        assert np.hypot(cl.centres[:, 0] - bad[0], cl.centres[:, 1] - bad[1]).min() > 5 * wavelength
