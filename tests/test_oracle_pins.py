@@ -251,12 +251,102 @@ def test_translation_and_rotation_covariance():
     assert np.abs(F_r - F).max() <= 1e-11 * np.abs(F).max()
 
 
-def test_truncation_rule_example():
-    """Eq. (Np) evaluated for k a = 6 pi * 0.15 (Example I's largest disk)."""
-    N = O_.truncation_order(6 * np.pi * 0.15, 1e-10)
-    assert N == int(np.floor(6 * np.pi * 0.15 + (np.log(2 * np.sqrt(2) * np.pi * 6 * np.pi * 0.15 / 1e-10)
-                                                  / (2 * np.sqrt(2))) ** (2 / 3) * (6 * np.pi * 0.15) ** (1 / 3) + 1))
-    assert 8 <= N <= 14
+def _single_disk_farfield(ka, N, bc):
+    """Far field of the oracle's solve for one unit disk at the origin,
+    truncated at N, at 16 equally spaced angles (offset 0.1)."""
+    Oc, a = np.zeros((1, 2)), np.array([1.0])
+    rho, _ = O_.solve(Oc, a, np.array([bc], np.int8), ka, N, [0.3], method="lu")
+    return O_.farfield(Oc, a, ka, N, rho, W.angles(16) + 0.1)[:, 0]
+
+
+def _truncation_rule_misses(rule, stop_at_first=False):
+    """Eq. (Np) is the truncation a solve to relative accuracy eps needs.
+    For one disk the truncated system is diagonal, so its solution is the
+    Mie series cut at N; the largest far-field error over the sampled angles,
+    relative to the largest far field, against the series cut 30 modes later
+    must be at most 5 eps at N = N_p (the rule is sufficient) and at least
+    eps/5 at N_p - 3 (the rule is not padded).  Returns the (bc, eps, ka)
+    cases that break either bound."""
+    misses = []
+    for bc in (0, 1):
+        for eps in (1e-6, 1e-8, 1e-10):
+            for ka in (1.0, 2.0, 5.0, 10.0, 20.0, 40.0, 80.0, 160.0):
+                N = rule(ka, eps)
+                ref = _single_disk_farfield(ka, N + 30, bc)
+                err = lambda n: np.abs(_single_disk_farfield(ka, n, bc) - ref).max() / np.abs(ref).max()
+                if not (err(N) <= 5 * eps and err(max(N - 3, 0)) >= eps / 5):
+                    misses.append((bc, eps, ka))
+                    if stop_at_first:
+                        return misses
+    return misses
+
+
+def test_truncation_rule_gives_the_requested_accuracy():
+    """Eq. (Np) (section 5) over k a in [1, 160] and eps in [1e-10, 1e-6],
+    sound-soft and sound-hard: accurate to a few eps, and three modes fewer
+    are not."""
+    assert _truncation_rule_misses(O_.truncation_order) == []
+
+
+_S2 = 2 * np.sqrt(2)
+
+
+@pytest.mark.parametrize("bad", [
+    # exponent 1/2 instead of 2/3 on the logarithmic term
+    lambda ka, e: int(np.floor(ka + (np.log(_S2 * np.pi * ka / e) / _S2) ** 0.5 * ka ** (1 / 3) + 1)),
+    # (k a)^(1/2) instead of (k a)^(1/3)
+    lambda ka, e: int(np.floor(ka + (np.log(_S2 * np.pi * ka / e) / _S2) ** (2 / 3) * ka ** 0.5 + 1)),
+    # sqrt 2 instead of 2 sqrt 2
+    lambda ka, e: int(np.floor(ka + (np.log(np.sqrt(2) * np.pi * ka / e) / np.sqrt(2)) ** (2 / 3)
+                               * ka ** (1 / 3) + 1)),
+    # the "+1" dropped
+    lambda ka, e: int(np.floor(ka + (np.log(_S2 * np.pi * ka / e) / _S2) ** (2 / 3) * ka ** (1 / 3))),
+    # decimal instead of natural logarithm
+    lambda ka, e: int(np.floor(ka + (np.log10(_S2 * np.pi * ka / e) / _S2) ** (2 / 3) * ka ** (1 / 3) + 1)),
+])
+def test_planted_truncation_rule_mistakes_are_caught(monkeypatch, bad):
+    monkeypatch.setattr(O_, "truncation_order", bad)
+    assert _truncation_rule_misses(O_.truncation_order, stop_at_first=True) != []
+
+
+def _rcs_pins_hold(cl, betas):
+    """Section 4.4 RCS(theta) = 10 log10(2 pi |a(theta)|^2) is the 2-D
+    scattering width in dB.  (i) Its integral over the circle is the total
+    scattering width, which the optical theorem fixes from the forward far
+    field, -2 sqrt(2 pi / k) Re(e^{i pi/4} F(beta)) (lossless obstacles).
+    (ii) The backscatter width of one disk tends to pi a as k a grows
+    (geometrical optics), sound-soft and sound-hard alike."""
+    ok = True
+    T = 720
+    for beta in betas:
+        rho = solve_lu(cl, [beta])
+        F = O_.farfield(cl.centres, cl.radii, cl.k, cl.N, rho, np.concatenate([W.angles(T), [beta]]))[:, 0]
+        width = np.sum(10.0 ** (O_.rcs(F[:T]) / 10.0)) / T       # (1 / 2 pi) * integral of 2 pi |F|^2
+        ext = -2 * np.sqrt(2 * np.pi / cl.k) * np.real(np.exp(1j * np.pi / 4) * F[T])
+        ok &= abs(width - ext) <= 1e-10 * ext
+    for bc in (0, 1):
+        ka = 100.0
+        N = O_.truncation_order(ka, 1e-10)
+        one = W.Cluster(np.zeros((1, 2)), np.array([1.0]), np.array([bc], np.int8), ka, N)
+        rho = solve_lu(one, [0.3])
+        Fb = O_.farfield(one.centres, one.radii, ka, N, rho, np.array([0.3 + np.pi]))[:, 0]
+        ok &= abs(10.0 ** (O_.rcs(Fb)[0] / 10.0) / np.pi - 1.0) <= 1e-3
+    return bool(ok)
+
+
+def test_rcs_total_width_and_backscatter_limit():
+    assert _rcs_pins_hold(W.four_disks(), [0.0, 0.4])
+    assert _rcs_pins_hold(W.small_mixed(seed=5, M=4, N=10, k=1.7), [1.1])
+
+
+@pytest.mark.parametrize("bad", [
+    lambda F: 20.0 * np.log10(2 * np.pi * np.abs(F) ** 2),    # amplitude decibels
+    lambda F: 10.0 * np.log10(np.abs(F) ** 2),                # 2 pi dropped
+    lambda F: 10.0 * np.log10(2 * np.pi * np.abs(F)),         # |F| instead of |F|^2
+])
+def test_planted_rcs_mistakes_are_caught(monkeypatch, bad):
+    monkeypatch.setattr(O_, "rcs", bad)
+    assert not _rcs_pins_hold(W.four_disks(), [0.0])
 
 
 def test_preconditioned_rows_match_dense():
