@@ -419,7 +419,7 @@ def formulation_timing(reps: int = 5):
     pb = msd.Problem(cl)
     rng = np.random.default_rng(0)
     for kind in (None, "cfie", "bwie"):
-        pb.set_formulation(kind, k=cl.k) if kind else pb.set_formulation(None)
+        pb.set_formulation(kind) if kind else pb.set_formulation(None)
         for prec in (msd.MSD_FP64, msd.MSD_FP32):
             for R in (1, 16):
                 dt = torch.complex128 if prec == msd.MSD_FP64 else torch.complex64

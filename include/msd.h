@@ -53,6 +53,15 @@ typedef enum {
     MSD_OK = 0,              /* converged / completed                               */
     MSD_NOT_CONVERGED = 1,   /* iteration limit reached before the tolerance        */
     MSD_STAGNATED = 3,       /* refinement stopped reducing the FP64 residual        */
+    /* Matlab's gmres FLAG 2 (section 6.2: the preconditioner is ill-conditioned)
+     * has no positive code here.  The single-scattering preconditioner is the
+     * block diagonal of self blocks (section 5), which are diagonal in the
+     * Fourier modes, so it is singular exactly when one mode's self block
+     * vanishes (a sound-hard disk with k a_p at a zero of J_m; a resonance of a
+     * formulation's combination).  The library finds that when it forms the
+     * per-row factors -- msd_create, msd_update_geometry, msd_set_formulation,
+     * msd_set_formulation_kind, msd_set_penetrable -- and returns
+     * MSD_ERR_NONFINITE there, before any solve; a solve never returns 2. */
     MSD_ERR_ARG = -1,        /* invalid argument (sizes, null pointers, N range)     */
     MSD_ERR_OVERLAP = -2,    /* two disks of one configuration intersect             */
     MSD_ERR_CUDA = -3,       /* a CUDA runtime call failed                            */
@@ -142,7 +151,8 @@ msd_status msd_rhs_planewave(msd_problem* pb, int R, const double* betas_host, v
  * (Dirichlet) or J'_m/(sqrt(a_p) J_m H'_m) (Neumann).
  *   precision  MSD_FP64: x, y complex128; MSD_FP32: complex64 with FP32
  *              accumulation (the inner product of MSD_MIXED solves)
- *   x, y       device, [N_tot][R]; x and y must not overlap
+ *   x, y       device, [N_tot][R]; byte ranges that overlap in any way are
+ *              rejected with MSD_ERR_ARG
  * Asynchronous on the problem's stream. */
 msd_status msd_matvec(msd_problem* pb, int R, int precision, const void* x_dev, void* y_dev);
 
@@ -155,7 +165,10 @@ msd_status msd_matvec(msd_problem* pb, int R, int precision, const void* x_dev, 
  *   pb         a problem whose generators of this precision already exist
  *              (after one msd_matvec or msd_solve_planewaves call with that
  *              precision; otherwise MSD_ERR_ARG)
- *   x, y       device, [N_tot][R], as for msd_matvec
+ *   x, y       device, [N_tot][R], as for msd_matvec; byte ranges that
+ *              overlap in any way are rejected with MSD_ERR_ARG
+ * The tile shape is the cost model's choice for (R, precision), not the
+ * autotuned one (tuning would need timing buffers and a synchronisation).
  * The call allocates nothing: its work list, scaled input and per-split
  * partial sums live in one 32 MiB device array that the library declares
  * at file scope (every GPU that loads the library holds it until the
@@ -338,6 +351,32 @@ msd_status msd_solve_penetrable_pointsources(msd_problem* pb, int R, const doubl
  * default rows (MSD_ERR_ARG otherwise).  Synchronises the stream. */
 msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const double* rhs_weights,
                                const double* rep_weights);
+
+/* The named formulations of section 3, with their weights formed by the
+ * library (for every configuration of the problem):
+ *   MSD_FORM_EFIE  sound-soft rows L rho = -U
+ *   MSD_FORM_MFIE  sound-soft rows (I/2 + N) rho = -dU
+ *   MSD_FORM_CFIE  sound-soft rows [alpha eta L + (1 - alpha)(I/2 + N)] rho
+ *                  = -(alpha eta U + (1 - alpha) dU)   (section 5 CFIE system)
+ *   (these three: sound-hard rows (-I/2 + N) rho = -dU, field u = L rho)
+ *   MSD_FORM_BWIE  Brakhage-Werner, u = -(eta L + M) psi: sound-soft rows
+ *                  (I/2 - eta L - M) psi = -U, sound-hard rows the normal
+ *                  trace (eta I/2 - eta N - D) psi = -dU
+ * msd_set_formulation_kind:
+ *   alpha  CFIE weight, 0 <= alpha <= 1 (ignored by the other kinds)
+ *   eta    NULL: eta = i k of each configuration; else host double[2]
+ *          (re, im) for every configuration.  CFIE and Brakhage-Werner need
+ *          Im(eta) != 0 (section 3), else MSD_ERR_ARG.
+ *   Otherwise as msd_set_formulation (MSD_ERR_NONFINITE at a resonance of
+ *   the combination; synchronises the stream).
+ * msd_formulation_weights: the same weights in the layout of
+ *   msd_set_formulation, for inspection or editing; needs no problem and no
+ *   GPU.  eta NULL means i k (k > 0 then needed for CFIE and BWIE).  Any
+ *   output may be NULL. */
+enum { MSD_FORM_EFIE = 0, MSD_FORM_MFIE = 1, MSD_FORM_CFIE = 2, MSD_FORM_BWIE = 3 };
+msd_status msd_set_formulation_kind(msd_problem* pb, int kind, double alpha, const double* eta);
+msd_status msd_formulation_weights(int kind, double alpha, const double* eta, double k, double* op_weights,
+                                   double* rhs_weights, double* rep_weights);
 
 /* Time reversal, DORT (section 7, far-field mirror): for every
  * configuration the mirror emits the plane waves of incidence

@@ -522,6 +522,35 @@ def block_of(kind, O, a, k, N, p, q) -> np.ndarray:
     return {"L": block_L, "M": block_M, "N": block_N, "D": block_D}[kind](O, a, k, N, p, q)
 
 
+def standard_formulation(kind, alpha=0.5, eta=None, k=None):
+    """Section 3 (and the section 5 CFIE system): the weights of the named
+    integral equations, as (op_weights, rhs_weights, rep_weights) for
+    assemble_formulation / rhs_formulation / farfield_formulation.
+    Sound-soft rows:
+      "efie"  L rho = -U;
+      "mfie"  (I/2 + N) rho = -dU;
+      "cfie"  [alpha eta L + (1 - alpha)(I/2 + N)] rho = -(alpha eta U + (1 - alpha) dU);
+      "bwie"  (I/2 - eta L - M) psi = -U with u = -(eta L + M) psi.
+    Sound-hard rows: (-I/2 + N) rho = -dU for the three single-layer
+    representations (u = L rho); for Brakhage-Werner the normal trace of its
+    representation, (eta I/2 - eta N - D) psi = -dU.  eta defaults to i k
+    (the paper leaves eta free with Im(eta) != 0)."""
+    if eta is None and kind in ("cfie", "bwie"):
+        eta = 1j * k
+    if kind == "bwie":
+        return ({DIRICHLET: {"I": 0.5, "L": -eta, "M": -1.0}, NEUMANN: {"I": 0.5 * eta, "N": -eta, "D": -1.0}},
+                {DIRICHLET: {"U": 1.0}, NEUMANN: {"dU": 1.0}}, {"L": -eta, "M": -1.0})
+    hard_rows, hard_rhs = {"I": -0.5, "N": 1.0}, {"dU": 1.0}
+    soft = {"efie": ({"L": 1.0}, {"U": 1.0}),
+            "mfie": ({"I": 0.5, "N": 1.0}, {"dU": 1.0}),
+            "cfie": ({"L": alpha * eta, "I": 0.5 * (1 - alpha), "N": 1 - alpha},
+                     {"U": alpha * eta, "dU": 1 - alpha}) if kind == "cfie" else None}
+    if kind not in soft:
+        raise ValueError(kind)
+    rows, rhs = soft[kind]
+    return {DIRICHLET: rows, NEUMANN: hard_rows}, {DIRICHLET: rhs, NEUMANN: hard_rhs}, {"L": 1.0, "M": 0.0}
+
+
 def assemble_formulation(O, a, bc, k, N, op_weights) -> np.ndarray:
     """Section 5: the matrix of a linear combination of I, L, M, N and D
     (the same block structure for every combination).  op_weights[c] maps

@@ -41,8 +41,18 @@ __global__ void k_form_rows(const MsdConfig* __restrict__ cfg, int Mtot, const i
     const MsdConfig c = cfg[disk_cfg[d]];
     const double a = radius[d], k = c.k, sa = sqrt(a);
     const int cls = bc[d] == MSD_NEUMANN ? 1 : 0;
+    double2 std_op[5], std_rhs[2], std_rep[2];
     const double2* op = w.op[cls];  // I, L, M, N, D
-    const double2 wU = w.rhs[cls][0], wdU = w.rhs[cls][1];
+    const double2* rhs = w.rhs[cls];
+    const double2* rep = w.rep;
+    if (w.kind >= 0) {  // named formulation; eta = i k of this configuration unless given
+        msd_standard_weights(w.kind, w.alpha, w.eta_ik ? make_double2(0.0, k) : w.eta, cls, std_op, std_rhs,
+                             std_rep);
+        op = std_op;
+        rhs = std_rhs;
+        rep = std_rep;
+    }
+    const double2 wU = rhs[0], wdU = rhs[1];
     const long long row0 = c.row_off + (long long)(d - c.disk_off) * c.n;
     const double hpa = 0.5 * M_PI * a, hpka = 0.5 * M_PI * k * a, hpk2a = 0.5 * M_PI * k * k * a;
     int bad = 0;
@@ -76,7 +86,7 @@ __global__ void k_form_rows(const MsdConfig* __restrict__ cfg, int Mtot, const i
         rf2_64[row] = sa * dJm;
         rf2_32[row] = (float)(sa * dJm);
         rhs_scale[row] = rs;
-        ff[row] = cadd(cmulr(w.rep[0], Jm), cmulr(w.rep[1], -k * dJm));
+        ff[row] = cadd(cmulr(rep[0], Jm), cmulr(rep[1], -k * dJm));
         diag[row] = P;
     }
     if (bad) atomicOr(flags, 1);

@@ -73,6 +73,12 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// True when the byte ranges [x, x + bytes) and [y, y + bytes) intersect.
+bool ranges_overlap(const void* x, const void* y, size_t bytes) {
+    const uintptr_t a = (uintptr_t)x, b = (uintptr_t)y;
+    return a < b + bytes && b < a + bytes;
+}
+
 // Growable device buffer owned by the library.
 struct DBuf {
     void* p = nullptr;
@@ -1478,7 +1484,8 @@ msd_status msd_matvec(msd_problem* pb, int R, int precision, const void* x_dev, 
         if (!pb || R <= 0 || !x_dev || !y_dev) fail(MSD_ERR_ARG, "msd_matvec: bad argument");
         if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_matvec: precision");
         if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev)) fail(MSD_ERR_ARG, "msd_matvec: x and y must be device memory");
-        if (x_dev == y_dev) fail(MSD_ERR_ARG, "msd_matvec: x and y must not overlap");
+        if (ranges_overlap(x_dev, y_dev, (size_t)pb->Ntot * R * (precision == MSD_FP64 ? 16 : 8)))
+            fail(MSD_ERR_ARG, "msd_matvec: x and y must not overlap");
         matvec_dev(pb, R, precision == MSD_FP64, x_dev, y_dev);
         return MSD_OK;
     });
@@ -1924,6 +1931,70 @@ msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const 
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+// Arguments of a named formulation: CFIE needs 0 <= alpha <= 1, CFIE and
+// Brakhage-Werner a coupling eta with a non-zero imaginary part (section 3).
+void check_kind(const char* where, int kind, double alpha, const double* eta) {
+    if (kind != MSD_FORM_EFIE && kind != MSD_FORM_MFIE && kind != MSD_FORM_CFIE && kind != MSD_FORM_BWIE)
+        fail(MSD_ERR_ARG, std::string(where) + ": unknown formulation kind");
+    if (kind == MSD_FORM_CFIE && !(alpha >= 0.0 && alpha <= 1.0))
+        fail(MSD_ERR_ARG, std::string(where) + ": CFIE needs 0 <= alpha <= 1");
+    if ((kind == MSD_FORM_CFIE || kind == MSD_FORM_BWIE) && eta &&
+        (!std::isfinite(eta[0]) || !std::isfinite(eta[1]) || eta[1] == 0.0))
+        fail(MSD_ERR_ARG, std::string(where) + ": eta needs a finite, non-zero imaginary part");
+}
+
+}  // namespace
+
+extern "C" {
+
+msd_status msd_set_formulation_kind(msd_problem* pb, int kind, double alpha, const double* eta) {
+    return guarded([&]() -> msd_status {
+        if (!pb) fail(MSD_ERR_ARG, "msd_set_formulation_kind: bad handle");
+        check_kind("msd_set_formulation_kind", kind, alpha, eta);
+        if (pb->pen_minus) fail(MSD_ERR_ARG, "msd_set_formulation_kind: not with penetrable obstacles");
+        MsdFormulation w{};
+        w.kind = kind;
+        w.alpha = alpha;
+        w.eta_ik = eta ? 0 : 1;
+        w.eta = eta ? make_double2(eta[0], eta[1]) : make_double2(0.0, 0.0);
+        pb->fw = w;
+        pb->form = true;
+        form_rows(pb);
+        return MSD_OK;
+    });
+}
+
+msd_status msd_formulation_weights(int kind, double alpha, const double* eta, double k, double* op_weights,
+                                   double* rhs_weights, double* rep_weights) {
+    return guarded([&]() -> msd_status {
+        check_kind("msd_formulation_weights", kind, alpha, eta);
+        if (!eta && (kind == MSD_FORM_CFIE || kind == MSD_FORM_BWIE) && !(k > 0.0 && std::isfinite(k)))
+            fail(MSD_ERR_ARG, "msd_formulation_weights: eta = i k needs k > 0");
+        const double2 e = eta ? make_double2(eta[0], eta[1]) : make_double2(0.0, k);
+        for (int c = 0; c < 2; ++c) {
+            double2 op[5], rhs[2], rep[2];
+            msd_standard_weights(kind, alpha, e, c, op, rhs, rep);
+            for (int o = 0; o < 5 && op_weights; ++o) {
+                op_weights[(c * 5 + o) * 2] = op[o].x;
+                op_weights[(c * 5 + o) * 2 + 1] = op[o].y;
+            }
+            for (int o = 0; o < 2 && rhs_weights; ++o) {
+                rhs_weights[(c * 2 + o) * 2] = rhs[o].x;
+                rhs_weights[(c * 2 + o) * 2 + 1] = rhs[o].y;
+            }
+            for (int o = 0; o < 2 && rep_weights && c == 0; ++o) {
+                rep_weights[2 * o] = rep[o].x;
+                rep_weights[2 * o + 1] = rep[o].y;
+            }
+        }
+        return MSD_OK;
+    });
+}
+
 msd_status msd_nearfield(msd_problem* pb, int config, const void* rho, int R, int64_t P, const double* points,
                          void* u_out) {
     return guarded([&]() -> msd_status {
@@ -2084,7 +2155,8 @@ extern "C" msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, 
         if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_matvec_noalloc: precision");
         if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev))
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must be device memory");
-        if (x_dev == y_dev) fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must not overlap");
+        if (ranges_overlap(x_dev, y_dev, (size_t)pb->Ntot * R * (precision == MSD_FP64 ? 16 : 8)))
+            fail(MSD_ERR_ARG, "msd_matvec_noalloc: x and y must not overlap");
         if (pb->form) fail(MSD_ERR_ARG, "msd_matvec_noalloc: needs the default formulation");
         const bool fp64 = precision == MSD_FP64;
         if ((fp64 && !pb->d_G64) || (!fp64 && !pb->d_G32))

@@ -177,7 +177,69 @@ struct MsdFormulation {
     double2 op[2][5];
     double2 rhs[2][2];
     double2 rep[2];
+    // kind >= 0 (MSD_FORM_*): the weights above are ignored and each row
+    // takes those of the named formulation (msd_standard_weights) with
+    // alpha, and eta or, when eta_ik is set, i k of the row's configuration.
+    int kind = -1;
+    int eta_ik = 0;
+    double alpha = 0.0;
+    double2 eta = {0.0, 0.0};
 };
+
+// Weights of a named formulation (section 3 integral equations; the
+// Brakhage-Werner sound-hard rows are the normal trace of its
+// representation) for the rows of boundary condition cls: op[5] = weights
+// of I, L, M, N, D, rhs[2] = weights of U, dU, rep[2] = weights of L, M in
+// the field representation.  Returns false for an unknown kind.
+__host__ __device__ inline bool msd_standard_weights(int kind, double alpha, double2 eta, int cls, double2 op[5],
+                                                     double2 rhs[2], double2 rep[2]) {
+    const double2 z = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
+    for (int o = 0; o < 5; ++o) op[o] = z;
+    rhs[0] = rhs[1] = z;
+    rep[0] = one;
+    rep[1] = z;
+    if (kind == MSD_FORM_BWIE) {
+        // u = -(eta L + M) psi: trace (I/2 - eta L - M) psi = -U on sound-soft
+        // rows, normal trace (eta I/2 - eta N - D) psi = -dU on sound-hard rows
+        rep[0] = make_double2(-eta.x, -eta.y);
+        rep[1] = make_double2(-1.0, 0.0);
+        if (cls == MSD_DIRICHLET) {
+            op[0] = make_double2(0.5, 0.0);
+            op[1] = make_double2(-eta.x, -eta.y);
+            op[2] = make_double2(-1.0, 0.0);
+            rhs[0] = one;
+        } else {
+            op[0] = make_double2(0.5 * eta.x, 0.5 * eta.y);
+            op[3] = make_double2(-eta.x, -eta.y);
+            op[4] = make_double2(-1.0, 0.0);
+            rhs[1] = one;
+        }
+        return true;
+    }
+    if (kind != MSD_FORM_EFIE && kind != MSD_FORM_MFIE && kind != MSD_FORM_CFIE) return false;
+    if (cls == MSD_NEUMANN) {  // single-layer representations: (-I/2 + N) rho = -dU
+        op[0] = make_double2(-0.5, 0.0);
+        op[3] = one;
+        rhs[1] = one;
+        return true;
+    }
+    if (kind == MSD_FORM_EFIE) {  // L rho = -U
+        op[1] = one;
+        rhs[0] = one;
+    } else if (kind == MSD_FORM_MFIE) {  // (I/2 + N) rho = -dU
+        op[0] = make_double2(0.5, 0.0);
+        op[3] = one;
+        rhs[1] = one;
+    } else {  // CFIE: alpha eta L + (1 - alpha)(I/2 + N) = -(alpha eta U + (1 - alpha) dU)
+        const double2 ae = make_double2(alpha * eta.x, alpha * eta.y);
+        op[0] = make_double2(0.5 * (1.0 - alpha), 0.0);
+        op[1] = ae;
+        op[3] = make_double2(1.0 - alpha, 0.0);
+        rhs[0] = ae;
+        rhs[1] = make_double2(1.0 - alpha, 0.0);
+    }
+    return true;
+}
 // Per-row factors: l1, l2 (FP64, FP32) of the combined product, rf2 =
 // sqrt(a) J', the right-hand-side scale -(w_U J + k w_dU J')/P, the field
 // factor w_L' J - k w_M' J' and the self-block diagonal P.  d_flags bit 0 is

@@ -24,6 +24,8 @@ MSD_ERR_ARG, MSD_ERR_OVERLAP, MSD_ERR_CUDA, MSD_ERR_OOM, MSD_ERR_NONFINITE, MSD_
 MSD_DIRICHLET, MSD_NEUMANN = 0, 1
 MSD_FP64, MSD_MIXED, MSD_FP32 = 0, 1, 2
 MSD_GEN_AUTO, MSD_GEN_STREAMED, MSD_GEN_RECOMPUTE = 0, 1, 2
+MSD_FORM_EFIE, MSD_FORM_MFIE, MSD_FORM_CFIE, MSD_FORM_BWIE = 0, 1, 2, 3
+FORMULATION_KINDS = {"efie": MSD_FORM_EFIE, "mfie": MSD_FORM_MFIE, "cfie": MSD_FORM_CFIE, "bwie": MSD_FORM_BWIE}
 MSD_MAX_N = 63
 MSD_MAX_DORT = 2048
 
@@ -79,6 +81,8 @@ def _load():
         "msd_dort": (I, [P, I, ctypes.POINTER(msd_opts), P, P, P, P]),
         "msd_dort_eigen": (I, [P, I, P, P, P]),
         "msd_set_formulation": (I, [P, P, P, P]),
+        "msd_set_formulation_kind": (I, [P, I, D, P]),
+        "msd_formulation_weights": (I, [I, D, P, D, P, P, P]),
         "msd_set_penetrable": (I, [P, P, P]),
         "msd_penetrable_matvec": (I, [P, I, I, P, P, P, P]),
         "msd_solve_penetrable": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
@@ -99,7 +103,8 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_farfield", "msd_update_geometry", "msd_matvec_timing", "msd_kernel_launches",
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
-            "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_penetrable",
+            "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_formulation_kind",
+            "msd_formulation_weights", "msd_set_penetrable",
             "msd_penetrable_matvec", "msd_solve_penetrable", "msd_solve_penetrable_pointsources",
             "msd_last_error")
 
@@ -314,49 +319,45 @@ def msd_solve_penetrable_pointsources(h, R: int, sources, opts: msd_opts | None,
                                                          else None), allow_positive=True)
 
 
-_OPS = ("I", "L", "M", "N", "D")
+def _eta_arg(eta):
+    if eta is None:
+        return None
+    e = complex(eta)
+    return np.array([e.real, e.imag], np.float64)
+
+
+def _kind(kind) -> int:
+    if kind not in FORMULATION_KINDS:
+        raise ValueError(f"unknown formulation {kind!r}; one of {sorted(FORMULATION_KINDS)}")
+    return FORMULATION_KINDS[kind]
+
+
+def msd_set_formulation_kind(h, kind: str, alpha: float = 0.5, eta=None) -> None:
+    """kind "efie", "mfie", "cfie" or "bwie"; eta None means i k of each
+    configuration (include/msd.h)."""
+    e = _eta_arg(eta)
+    _check(_lib.msd_set_formulation_kind(h, _kind(kind), float(alpha), _ptr(e) if e is not None else None))
+
+
+def msd_formulation_weights(kind: str, alpha: float = 0.5, eta=None, k: float = 0.0):
+    """The library's weights of a named formulation: (op [2][5], rhs [2][2],
+    rep [2]) complex, the layout of msd_set_formulation."""
+    e = _eta_arg(eta)
+    op = np.zeros((2, 5), np.complex128)
+    rhs = np.zeros((2, 2), np.complex128)
+    rep = np.zeros(2, np.complex128)
+    _check(_lib.msd_formulation_weights(_kind(kind), float(alpha), _ptr(e) if e is not None else None,
+                                        float(k), _ptr(op), _ptr(rhs), _ptr(rep)))
+    return op, rhs, rep
 
 
 def formulation(kind: str, alpha: float = 0.5, eta=None, k: float | None = None):
     """Weights (op [2][5], rhs [2][2], rep [2]) of a standard formulation
-    (section 3).  Sound-soft rows: "efie" L = -U; "mfie" (I/2 + N) = -dU;
-    "cfie" alpha eta L + (1 - alpha)(I/2 + N) = -(alpha eta U + (1 - alpha) dU);
-    "bwie" (I/2 - eta L - M) = -U with u = -(eta L + M).  Sound-hard rows:
-    (-I/2 + N) = -dU for the single-layer representations, and the normal
-    trace (eta I/2 - eta N - D) = -dU of the Brakhage-Werner representation.
-    eta defaults to i k."""
-    if eta is None and kind in ("cfie", "bwie"):
-        if k is None:
-            raise ValueError("eta or k is needed")
-        eta = 1j * k
-    op = np.zeros((2, 5), np.complex128)
-    rhs = np.zeros((2, 2), np.complex128)
-    rep = np.zeros(2, np.complex128)
-
-    def put(c, **w):
-        for name, v in w.items():
-            op[c, _OPS.index(name)] = v
-    if kind == "bwie":
-        put(MSD_DIRICHLET, I=0.5, L=-eta, M=-1.0)
-        put(MSD_NEUMANN, I=0.5 * eta, N=-eta, D=-1.0)
-        rhs[:, :] = [[1, 0], [0, 1]]
-        rep[:] = [-eta, -1.0]
-        return op, rhs, rep
-    put(MSD_NEUMANN, I=-0.5, N=1.0)
-    rhs[MSD_NEUMANN] = [0, 1]
-    rep[:] = [1.0, 0.0]
-    if kind == "efie":
-        put(MSD_DIRICHLET, L=1.0)
-        rhs[MSD_DIRICHLET] = [1, 0]
-    elif kind == "mfie":
-        put(MSD_DIRICHLET, I=0.5, N=1.0)
-        rhs[MSD_DIRICHLET] = [0, 1]
-    elif kind == "cfie":
-        put(MSD_DIRICHLET, L=alpha * eta, I=0.5 * (1 - alpha), N=1 - alpha)
-        rhs[MSD_DIRICHLET] = [alpha * eta, 1 - alpha]
-    else:
-        raise ValueError(kind)
-    return op, rhs, rep
+    (section 3), formed by the library (msd_formulation_weights); eta
+    defaults to i k."""
+    if eta is None and kind in ("cfie", "bwie") and k is None:
+        raise ValueError("eta or k is needed")
+    return msd_formulation_weights(kind, alpha, eta, 0.0 if k is None else k)
 
 
 def msd_kernel_launches() -> int:
@@ -532,12 +533,11 @@ class Problem:
         rows (kind None)."""
         if kind is None and "op" not in kw:
             msd_set_formulation(self.handle, None, None, None)
-            return
-        if kind is None:
-            op, rhs, rep = kw["op"], kw["rhs"], kw["rep"]
+        elif kind is None:
+            msd_set_formulation(self.handle, kw["op"], kw["rhs"], kw["rep"])
         else:
-            op, rhs, rep = formulation(kind, **kw)
-        msd_set_formulation(self.handle, op, rhs, rep)
+            kw.pop("k", None)      # eta = i k of each configuration is the library's default
+            msd_set_formulation_kind(self.handle, kind, **kw)
 
     def set_penetrable(self, k_minus, mu=None):
         """Penetrable obstacles (section 7): interior wavenumber(s) k_minus

@@ -30,10 +30,17 @@ def msd():
 
 
 def as_dicts(op, rhs, rep):
-    """The binding's weight arrays as the oracle's dictionaries."""
+    """Weight arrays (layout of msd_set_formulation) as the oracle's dictionaries."""
     ow = {c: {OPS[o]: op[c, o] for o in range(5) if op[c, o] != 0} for c in (0, 1)}
     rw = {c: {"U": rhs[c, 0], "dU": rhs[c, 1]} for c in (0, 1)}
     return ow, rw, {"L": rep[0], "M": rep[1]}
+
+
+def as_arrays(ow, rw, pw):
+    """The oracle's weight dictionaries in the layout of msd_set_formulation."""
+    op = np.array([[ow[c].get(o, 0) for o in OPS] for c in (0, 1)], np.complex128)
+    rhs = np.array([[rw[c].get("U", 0), rw[c].get("dU", 0)] for c in (0, 1)], np.complex128)
+    return op, rhs, np.array([pw["L"], pw["M"]], np.complex128)
 
 
 KINDS = ["efie", "mfie", "cfie", "bwie"]
@@ -49,11 +56,10 @@ def clusters():
 def test_products_match_oracle(msd, kind):
     rng = np.random.default_rng(5)
     for cl in clusters():
-        op, rhs, rep = msd.formulation(kind, k=cl.k)
-        ow, _, _ = as_dicts(op, rhs, rep)
+        ow, _, _ = O_.standard_formulation(kind, k=cl.k)
         Ap, _ = O_.preconditioned_formulation(cl.centres, cl.radii, cl.bc, cl.k, cl.N, ow)
         pb = msd.Problem(cl)
-        pb.set_formulation(kind, k=cl.k)
+        pb.set_formulation(kind)               # by name: the library forms the weights (eta = i k)
         for R in (1, 3, 16):
             x = rng.standard_normal((cl.ntot, R)) + 1j * rng.standard_normal((cl.ntot, R))
             ref = Ap @ x
@@ -85,12 +91,11 @@ def test_efie_weights_reproduce_default_rows(msd):
 @pytest.mark.parametrize("kind", KINDS)
 def test_rhs_solve_and_fields(msd, kind):
     cl = W.small_mixed(seed=3, M=6, N=14, k=2.0)
-    op, rhs, rep = msd.formulation(kind, k=cl.k)
-    ow, rw, pw = as_dicts(op, rhs, rep)
+    ow, rw, pw = O_.standard_formulation(kind, k=cl.k)
     betas = [0.3, 2.0]
     th = W.angles(48)
     pb = msd.Problem(cl)
-    pb.set_formulation(kind, k=cl.k)
+    pb.set_formulation(kind)
     _, d = O_.preconditioned_formulation(cl.centres, cl.radii, cl.bc, cl.k, cl.N, ow)
     b_ref = O_.rhs_formulation(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas, rw) / d[:, None]
     b = pb.rhs(betas).cpu().numpy()
@@ -134,7 +139,7 @@ def test_dirichlet_resonance(msd):
     th = W.angles(24)
     ref = mie_far(k, a, 0.9, th)
     for kind in ("efie", "cfie", "bwie"):
-        pb.set_formulation(kind, k=k)
+        pb.set_formulation(kind)
         res = pb.solve([0.9], tol=1e-13)
         assert res.status == msd.MSD_OK
         F = pb.farfield(res.rho, th).cpu().numpy()[0, :, 0]
@@ -146,7 +151,7 @@ def test_vanishing_self_block_is_an_error(msd):
     """All weights of the sound-soft rows zero: the self block is 0 and the
     call fails with MSD_ERR_NONFINITE."""
     pb = msd.Problem(W.small_mixed(seed=3, M=6, N=10, k=2.0))
-    op, rhs, rep = msd.formulation("efie")
+    op, rhs, rep = as_arrays(*O_.standard_formulation("efie"))
     op[msd.MSD_DIRICHLET, :] = 0
     with pytest.raises(msd.MsdError) as e:
         pb.set_formulation(op=op, rhs=rhs, rep=rep)
@@ -158,7 +163,7 @@ def test_time_reversal_is_formulation_independent(msd):
     cl = W.small_mixed(seed=3, M=6, N=14, k=2.0)
     pb = msd.Problem(cl)
     e0, _, _, _ = pb.dort(32, want_F=False, want_T=False)
-    pb.set_formulation("bwie", k=cl.k)
+    pb.set_formulation("bwie")
     e1, _, _, _ = pb.dort(32, want_F=False, want_T=False)
     e0, e1 = e0.cpu().numpy(), e1.cpu().numpy()
     assert np.abs(e1 - e0).max() <= 1e-9 * e0.max()
@@ -168,11 +173,43 @@ def test_time_reversal_is_formulation_independent(msd):
 def test_default_rows_required(msd):
     cl = W.small_mixed(seed=3, M=6, N=10, k=2.0)
     pb = msd.Problem(cl)
-    pb.set_formulation("cfie", k=cl.k)
+    pb.set_formulation("cfie")
     with pytest.raises(msd.MsdError):
         pb.grad_farfield_misfit([0.1], W.angles(8), np.zeros((1, 8, 1), np.complex128))
     x = torch.zeros((cl.ntot, 1), dtype=torch.complex128, device="cuda")
     with pytest.raises(msd.MsdError):
         msd.msd_matvec_noalloc(pb.handle, 1, msd.MSD_FP64, x, torch.empty_like(x))
     pb.set_formulation(None)
+    pb.close()
+
+
+def test_named_formulation_per_configuration_eta(msd):
+    """Two configurations with different k set to CFIE and Brakhage-Werner by
+    name through the C ABI (msd_set_formulation_kind, eta = i k of each
+    configuration; then an explicit eta): products and far fields of solves
+    against the oracle's statement of the same formulations."""
+    cls = [W.small_mixed(seed=3, M=6, N=12, k=2.0), W.small_mixed(seed=4, M=5, N=12, k=3.1)]
+    pb = msd.Problem(cls)
+    betas = [0.3, 2.0]
+    th = W.angles(40)
+    rng = np.random.default_rng(2)
+    for kind, alpha, eta in (("cfie", 0.3, None), ("bwie", 0.5, None), ("cfie", 0.6, 0.5 + 1.7j)):
+        msd.msd_set_formulation_kind(pb.handle, kind, alpha, eta)
+        x = rng.standard_normal((pb.ntot, 2)) + 1j * rng.standard_normal((pb.ntot, 2))
+        y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP64).cpu().numpy()
+        res = pb.solve(betas, tol=1e-12)
+        assert res.status == msd.MSD_OK, kind
+        F = pb.farfield(res.rho, th).cpu().numpy()
+        for c, cl in enumerate(cls):
+            ow, rw, pw = O_.standard_formulation(kind, alpha=alpha, eta=eta, k=cl.k)
+            Ap, _ = O_.preconditioned_formulation(cl.centres, cl.radii, cl.bc, cl.k, cl.N, ow)
+            r0 = pb.row_offset(c)
+            ref = Ap @ x[r0:r0 + cl.ntot]
+            assert np.abs(y[r0:r0 + cl.ntot] - ref).max() <= 1e-11 * np.abs(ref).max(), (kind, c)
+            dens = O_.solve_formulation(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas, ow, rw)
+            F_ref = O_.farfield_formulation(cl.centres, cl.radii, cl.k, cl.N, dens, th, pw)
+            assert np.abs(F[c] - F_ref).max() <= 1e-10 * np.abs(F_ref).max(), (kind, c)
+    with pytest.raises(msd.MsdError) as e:
+        msd.msd_set_formulation_kind(pb.handle, "cfie", 0.5, 1.0)       # Im(eta) = 0
+    assert e.value.status == msd.MSD_ERR_ARG
     pb.close()

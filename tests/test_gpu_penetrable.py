@@ -118,10 +118,10 @@ def test_mode_switches(msd):
     rho0 = pb.solve([0.3], tol=1e-12).rho.cpu().numpy()
     pb.set_penetrable(2.0)
     with pytest.raises(msd.MsdError):
-        pb.set_formulation("cfie", k=cl.k)
+        pb.set_formulation("cfie")
     pb.set_penetrable(None)
     assert np.abs(pb.solve([0.3], tol=1e-12).rho.cpu().numpy() - rho0).max() <= 1e-12 * np.abs(rho0).max()
-    pb.set_formulation("cfie", k=cl.k)
+    pb.set_formulation("cfie")
     with pytest.raises(msd.MsdError):
         pb.set_penetrable(2.0)
     pb.close()
