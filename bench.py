@@ -34,6 +34,8 @@ TF32_OVER_BF16 = 1.1 / 2.25                    # nominal dense TF32 / bf16 tenso
 # product kernel (window length 7) on this workload, from an ncu capture
 # (216.42 MB read + 5.75 MB written); the algorithmic stream is 207.7 MB
 K3_FP64_DRAM_BYTES_PER_LAUNCH = 222170624
+K3_FP64_TRAFFIC_SOURCE = ("copied from an ncu capture of the same kernel on this workload "
+                          "(profiles/k_bt_matvec_random400.md), not measured in this run")
 WORKLOAD = ("random400_k2pi: M=400 sound-soft disks, a~U[0.5,1.5], centres U[-50,50]^2 gap 0.2, "
             "k=2pi, N=20 (16400 unknowns), 1 plane wave, GMRES (restart length sized to HBM) to relres 1e-10, "
             "far field T=360")
@@ -87,22 +89,55 @@ def stop_clock_sampler(p):
             "samples": len(sm)}
 
 
-def oracle_matvec_sample(cl, targets, seconds=10.0):
-    """Times the oracle's preconditioned block rows on a sample of target
-    disks; returns seconds per full product (scaled to all M rows)."""
-    import numpy as np
+# The CPU baseline (the oracle, as it stands) is timed on one fixed sample
+# of the 400-disk product: CPU_SAMPLE_ROWS target block rows, evenly spaced,
+# applied to one seeded vector, split over a spawn process pool with one
+# worker per host core (each worker single-threaded).  The reference arm
+# runs one pass of this sample per step; the cpu_baseline of the main line
+# repeats the same pass for about ten seconds.
+CPU_SAMPLE_ROWS = 64
+
+
+def _oracle_rows(payload):
+    """Worker: the oracle's preconditioned block rows `rows` applied to x."""
     import oracle.msd_oracle as O_
-    x = (np.random.default_rng(0).standard_normal((cl.ntot, 1)) + 0j)
-    t0 = time.perf_counter()
-    done = 0
-    while True:
-        for p in targets:
-            O_.preconditioned_rows(cl.centres, cl.radii, cl.bc, cl.k, cl.N, x, [p])
-            done += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    return dt / done * cl.M, done
+    centres, radii, bc, k, N, x, rows = payload
+    return O_.preconditioned_rows(centres, radii, bc, k, N, x, rows)
+
+
+class OracleSample:
+    def __init__(self, cl):
+        import multiprocessing as mp
+        import numpy as np
+        self.cl = cl
+        self.cores = os.cpu_count() or 1
+        self.rows = [int(r) for r in np.linspace(0, cl.M - 1, CPU_SAMPLE_ROWS).round()]
+        self.x = np.random.default_rng(0).standard_normal((cl.ntot, 1)) + 0j
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.cores)   # spawned: safe after CUDA is initialised
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+        self.chunks = [self.rows[i::self.cores] for i in range(self.cores) if self.rows[i::self.cores]]
+        self.pass_once()   # imports the oracle in every worker (untimed)
+        self.bytes_per_pass = algorithmic_bytes_fp64(cl) * len(self.rows) / cl.M
+        self.description = (f"{len(self.rows)} evenly spaced target block rows of the 400-disk FP64 product "
+                            f"(oracle preconditioned_rows, NumPy/SciPy) per pass, split over {self.cores} "
+                            "single-threaded spawn workers")
+
+    def pass_once(self) -> float:
+        cl = self.cl
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_rows, [(cl.centres, cl.radii, cl.bc, cl.k, cl.N, self.x, ch) for ch in self.chunks])
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def algorithmic_bytes_fp64(cl, R=1):
@@ -116,22 +151,21 @@ def run_reference(args):
         return
     from paper_1409_8186_gb300 import workloads as W
     cl = W.random_cluster_400()
-    sample = list(range(0, cl.M, max(1, cl.M // 8)))[:8]
+    smp = OracleSample(cl)
     for _ in range(max(0, args.warmup)):
-        oracle_matvec_sample(cl, sample[:1], seconds=0.0)
-    times = []
-    for _ in range(args.steps):
-        t, _ = oracle_matvec_sample(cl, sample, seconds=2.0)
-        times.append(t)
-    t = statistics.median(times)
-    gbs = algorithmic_bytes_fp64(cl) / t / 1e9
+        smp.pass_once()
+    times = [smp.pass_once() for _ in range(args.steps)]
+    smp.close()
+    t = sum(times) / len(times)
+    gbs = smp.bytes_per_pass / t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "what": "oracle block-row products (FP64 NumPy/SciPy), one full "
-                       "product per step extrapolated from 8 sampled target disks"},
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "8 of 400 target block rows per step, scaled by 400/8"},
+            "config": {"workload": WORKLOAD, "what": "the CPU oracle's FP64 block-row products; one step = one "
+                       "pass over the fixed row sample (value = algorithmic bytes of the sampled rows / wall time)"},
+            "ms_per_full_product_extrapolated": t * 1e3 * cl.M / len(smp.rows),
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": smp.cores, "kind": "oracle",
+                             "sample": smp.description},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -635,6 +669,7 @@ def main():
     achieved_tf = r64["kernel_flops"] / kern_s / 1e12 if kern_s > 0 else 0.0
     kern_gbs = r64["kernel_bytes"] / kern_s / 1e9 if kern_s > 0 else 0.0
     mix_kern_s = rmx["kernel_ms"] * 1e-3
+    mix_tf = rmx["kernel_flops"] / mix_kern_s / 1e12 if mix_kern_s > 0 else None
 
     # the other steps of the path, each timed alone after the timed region
     # (CUDA events around 10 calls; update_geometry includes its host-side
@@ -656,12 +691,16 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        sample = list(range(0, cl.M, cl.M // 8))[:8]
-        t_cpu, done = oracle_matvec_sample(cl, sample, seconds=12.0)
-        cpu_gbs = algorithmic_bytes_fp64(cl) / t_cpu / 1e9
-        cpu = {"value": cpu_gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"{done} target block rows of the 400-disk product (FP64 NumPy/SciPy), "
-                         "scaled to one full product", "ms_per_matvec": t_cpu * 1e3}
+        smp = OracleSample(cl)
+        t_cpu, passes = 0.0, 0
+        while t_cpu < 10.0:
+            t_cpu += smp.pass_once()
+            passes += 1
+        smp.close()
+        cpu_gbs = smp.bytes_per_pass * passes / t_cpu / 1e9
+        cpu = {"value": cpu_gbs, "unit": "GB/s", "cores": smp.cores, "kind": "oracle",
+               "sample": smp.description + f"; {passes} passes",
+               "ms_per_full_product_extrapolated": t_cpu / passes * 1e3 * cl.M / len(smp.rows)}
 
     ms_step = total_ms / args.steps
     line = {
@@ -686,8 +725,14 @@ def main():
                         "TFLOP_s": rmx["kernel_flops"] / mix_kern_s / 1e12 if mix_kern_s > 0 else None},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": K3_FP64_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_source": K3_FP64_TRAFFIC_SOURCE,
                      "kernel": "k_bt_matvec<double2,1,1> (FP64 block-Toeplitz product)",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
+        "roofline_mixed": {"bound": "alu", "achieved": mix_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": mix_tf / FP32_PEAK_TFLOPS if mix_tf else None, "traffic": None,
+                           "kernel": "FP32 block-Toeplitz product inside the mixed-precision solve "
+                                     "(autotuned CUDA-core shape)",
+                           "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_bytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s / args.steps * 1e3},

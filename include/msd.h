@@ -454,6 +454,19 @@ msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes
 msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double* tuned_ms);
 msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT);
 
+/* Test hook for the error path of the bounded device waits (no GPU fault
+ * is involved).  While on != 0 (process-wide; off by default), every launch
+ * of a kernel with such a wait -- the tensor-core product's pipeline and the
+ * time-reversal grid barrier -- waits once, with a limit of about 10 us,
+ * for a condition that nothing fulfils: the kernel records the expiry, lets
+ * its own MMAs finish (the tensor-core kernel waits for them as usual),
+ * frees its TMEM, writes no result and returns.  The call that synchronises
+ * on that work then returns MSD_ERR_CUDA (solves and msd_matvec_timing for
+ * products, msd_dort / msd_dort_eigen for the barrier); an msd_matvec alone
+ * is asynchronous and leaves the report to the next such call.  With the
+ * hook off again the next call works normally. */
+void msd_test_expire_waits(int on);
+
 /* Total number of CUDA kernels launched by this library in this process. */
 int64_t msd_kernel_launches(void);
 

@@ -66,16 +66,23 @@ __device__ double block_sum_td(double v, double* red) {
 // The wait is bounded (~1 s of SM clock); on expiry *err is set, and once
 // it is set no CTA waits again (the results are then invalid and the host
 // reports the error).
-__device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned epoch, int* err) {
+// expire_test (msd_test_expire_waits): the first barrier waits for one CTA
+// more than the grid has, with a limit of kTestWaitCycles, so that the
+// expiry path runs without any fault.
+constexpr long long kTestWaitCycles = 20000;
+
+__device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned epoch, int* err, int expire_test) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(counter, 1u);
-        const unsigned target = gridDim.x * epoch;
+        const bool test = expire_test && epoch == 1;
+        const unsigned target = gridDim.x * epoch + (test ? 1u : 0u);
+        const long long limit = test ? kTestWaitCycles : kBarrierCycles;
         if (!*(volatile int*)err) {
             const long long t0 = clock64();
             while (*(volatile unsigned*)counter < target) {
-                if (clock64() - t0 > kBarrierCycles) {
+                if (clock64() - t0 > limit) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -122,7 +129,7 @@ constexpr int kTdBatch = 8;  // row entries per lane whose loads are issued toge
 __global__ void __launch_bounds__(kTdThreads)
     k_dort_tridiag(int C, int n, double2* __restrict__ Aall, double2* __restrict__ pbuf,
                    double2* __restrict__ colbuf, double* __restrict__ e_all, unsigned* __restrict__ bar,
-                   int* __restrict__ err) {
+                   int* __restrict__ err, int expire_test) {
     extern __shared__ double2 td_sh[];
     double2* xs = td_sh;                    // [2][C][n]
     double2* w_sh = td_sh + 2 * (size_t)C * n;  // [n]
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(kTdThreads)
                 if (lane == 0) pbuf[((size_t)par * C + c) * n + (R - k - 1)] = cscale(s, tau);
             }
         }
-        grid_barrier(bar, ++epoch, err);
+        grid_barrier(bar, ++epoch, err, expire_test);
         for (int c = 0; c < C; ++c) {
             const double2* v = X(par, c);
             const double tau = tau_sh[c];
@@ -435,7 +442,8 @@ cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, 
             if (c0 > 0 && (ce = cudaMemsetAsync(bar, 0, 4, s)) != cudaSuccess) return ce;
             double2* Ag = A + (size_t)c0 * n * n;
             double* eg = e + (size_t)c0 * n;
-            void* args[] = {&Cg, (void*)&n, &Ag, &pbuf, &colbuf, &eg, &bar, &err};
+            int expire_test = g_msd_expire_waits.load();
+            void* args[] = {&Cg, (void*)&n, &Ag, &pbuf, &colbuf, &eg, &bar, &err, &expire_test};
             ce = cudaLaunchCooperativeKernel((const void*)k_dort_tridiag, dim3(grid), dim3(kTdThreads), args, smem, s);
             if (ce != cudaSuccess) return ce;
             ++launches;

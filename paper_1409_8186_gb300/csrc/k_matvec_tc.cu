@@ -43,6 +43,7 @@ constexpr int kLbo = 128;
 constexpr int kSbo = 512;
 constexpr int kABytes = kTcM * kKc * 4;  // one A array of a stage (8 KB)
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr long long kTestWaitCycles = 20000;     // msd_test_expire_waits
 
 template <int RC>
 struct TcLayout {
@@ -100,6 +101,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
+// Test hook (msd_test_expire_waits): a wait on a flag that nothing sets,
+// with a short limit, so that the expiry path runs without any fault.
+__device__ __forceinline__ bool wait_unset_flag(const volatile int* flag) {
+    const long long t0 = clock64();
+    while (!*flag)
+        if (clock64() - t0 > kTestWaitCycles) return false;
+    return true;
+}
+
 template <int NC>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
 
@@ -123,7 +133,8 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
 template <int RC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_bt_tc(const MsdConfig* __restrict__ cfgs, const MatvecWork* __restrict__ works, const float2* __restrict__ G,
-            const float2* __restrict__ xs, float2* __restrict__ part, long long Ntot, int R, int rtiles) {
+            const float2* __restrict__ xs, float2* __restrict__ part, long long Ntot, int R, int rtiles,
+            int expire_test) {
     typedef TcLayout<RC> Lay;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -131,6 +142,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ __align__(8) uint64_t accbar[2];  // the MMAs of a source into accumulator 0 / 1 are done
     __shared__ int abort_sh;                      // a pipeline wait ran out
+    __shared__ int never_sh;                      // stays 0 (test hook)
 
     const int wi = blockIdx.x / rtiles;
     const int rt = blockIdx.x - wi * rtiles;
@@ -150,6 +162,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (tid == 0) {
         abort_sh = 0;
+        never_sh = 0;
         for (int s = 0; s < kTcStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
         for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accbar[s])));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -230,6 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // the end; warp-collective TMEM loads only run for whole warps.
         bool mine = true;  // the MMAs that last read buffer b are done
         if (it >= kTcStages) mine = mbar_wait(smem_u32(&mbar[b]), (uint32_t)((it / kTcStages - 1) & 1));
+        if (expire_test && it == kTcStages) mine = wait_unset_flag(&never_sh) && mine;
         // the accumulator of this source last held source qi - 2: fold it first
         if (kc == 0 && qi >= 2 && !mma_warp) {
             bool acc_ready = mine && mbar_wait(smem_u32(&accbar[qi & 1]), (uint32_t)(((qi - 2) >> 1) & 1));
@@ -379,7 +393,8 @@ void launch_rc(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, cons
     }
     const int rtiles = R / RC;
     k_bt_tc<RC><<<(unsigned)(nwork * rtiles), kTcThreads, TcLayout<RC>::kSmem, s>>>(d_cfg, d_work, G, xs, part, Ntot,
-                                                                                    R, rtiles);
+                                                                                    R, rtiles,
+                                                                                    g_msd_expire_waits.load());
 }
 
 }  // namespace

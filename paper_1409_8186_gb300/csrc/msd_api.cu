@@ -21,6 +21,7 @@
 // ---------------------------------------------------------------- errors
 
 std::atomic<long long> g_msd_launches{0};
+std::atomic<int> g_msd_expire_waits{0};
 
 namespace {
 thread_local std::string g_err;
@@ -986,7 +987,10 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         if (j >= kLag) {
             const int slot = (j - kLag) % kRing;
             CK(cudaEventSynchronize(pb->ring_ev[slot]));
-            if (pb->h_pinned[2 + 2 * slot + 1]) fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+            if (pb->h_pinned[2 + 2 * slot + 1]) {
+                check_tc("GMRES");
+                fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+            }
             if (!pb->h_pinned[2 + 2 * slot]) break;
         }
         V* vj = Vb + (long long)j * vstride;
@@ -1021,7 +1025,10 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
     CK(cudaStreamSynchronize(s));
     if (j > 0) {
         const int slot = (j - 1) % kRing;
-        if (pb->h_pinned[2 + 2 * slot + 1]) fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+        if (pb->h_pinned[2 + 2 * slot + 1]) {
+            check_tc("GMRES");
+            fail(MSD_ERR_NONFINITE, "GMRES: non-finite Arnoldi coefficient");
+        }
         any = pb->h_pinned[2 + 2 * slot];
     }
     if (any) {
@@ -1179,7 +1186,10 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
         bool all = true, improved = false;
         for (int i = 0; i < S; ++i) {
             const double rn = std::sqrt(std::max(hb[(size_t)i * cx.hstride].x, 0.0));
-            if (!std::isfinite(rn)) fail(MSD_ERR_NONFINITE, "GMRES: non-finite residual");
+            if (!std::isfinite(rn)) {
+                check_tc("GMRES");
+                fail(MSD_ERR_NONFINITE, "GMRES: non-finite residual");
+            }
             relres[i] = bnorm[i] > 0 ? rn / bnorm[i] : 0.0;
             if (relres[i] > o.tol) {
                 all = false;
@@ -1629,6 +1639,8 @@ msd_status msd_matvec_timing(msd_problem* pb, int enable, double* kernel_ms, int
 }
 
 int64_t msd_kernel_launches(void) { return g_msd_launches.load(); }
+
+void msd_test_expire_waits(int on) { g_msd_expire_waits.store(on ? 1 : 0); }
 
 msd_status msd_grad_farfield_misfit(msd_problem* pb, int R, const double* betas_host, int T,
                                     const double* thetas_host, const void* F_target, const msd_opts* opts,

@@ -105,7 +105,10 @@ int tc_tile_disks(int n);
 size_t tc_smem_bytes(int RC);
 void launch_bt_tc(int RC, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, const float2* G,
                   const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s);
-int tc_status_and_clear();  // bit 0: a pipeline wait of the tensor-core kernel expired
+int tc_status_and_clear();
+// Set by msd_test_expire_waits: kernels with bounded waits take their
+// expiry path once per launch (tests of the error path; no fault involved).
+extern std::atomic<int> g_msd_expire_waits;  // bit 0: a pipeline wait of the tensor-core kernel expired
 // the pieces of a product: xs = r .* x; y = x + l .* sum of the partials
 void launch_scale_cols(bool fp64, long long Ntot, int R, const void* rf, const void* x, void* xs, cudaStream_t s);
 void launch_finalize(bool fp64, long long Ntot, int R, int nsplit, const void* lf, const void* x, const void* part,

@@ -88,6 +88,7 @@ def _load():
         "msd_solve_penetrable": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
         "msd_solve_penetrable_pointsources": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
+        "msd_test_expire_waits": (V, [I]),
         "msd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -104,7 +105,7 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
             "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_formulation_kind",
-            "msd_formulation_weights", "msd_set_penetrable",
+            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_penetrable",
             "msd_penetrable_matvec", "msd_solve_penetrable", "msd_solve_penetrable_pointsources",
             "msd_last_error")
 
@@ -362,6 +363,11 @@ def formulation(kind: str, alpha: float = 0.5, eta=None, k: float | None = None)
 
 def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
+
+
+def msd_test_expire_waits(on: bool) -> None:
+    """Test hook: bounded device waits take their expiry path (include/msd.h)."""
+    _lib.msd_test_expire_waits(1 if on else 0)
 
 
 # ---------------------------------------------------------------- convenience wrapper
