@@ -226,7 +226,7 @@ def profile_only(what: str):
     torch.cuda.synchronize()
 
 
-def products_table(reps: int = 3):
+def products_table(reps: int = 3, only: str = ""):
     """One JSON line per (workload, columns R, precision, kernel, generator
     mode): the block-Toeplitz kernel's own time (CUDA events around each
     launch, averaged over `reps` products after one untimed product) and the
@@ -250,18 +250,24 @@ def products_table(reps: int = 3):
         ("lattice4000 (M=4000, N=15)", W.lattice_4000, [(F64, 1), (F32, 1), (F32, 64)], True),
     ]
     for name, make, shapes, try_recompute in cases:
+        if only and only not in name:
+            continue
         cl = make()
         for gen in (["streamed", "recompute"] if try_recompute else ["streamed"]):
             for prec, R in shapes:
                 kinds = ["auto", "model"]
                 if prec == F32:
                     kinds += [f"tc{rc}" for rc in (16, 32, 64) if R % rc == 0]
+                    if R % 8 == 0 and gen == "streamed":
+                        kinds.append("tcs")
                 for kind in kinds:
                     os.environ["MSD_AUTOTUNE"] = "0" if kind == "model" else "1"
                     pb = msd.Problem(cl)
                     if gen == "recompute":
                         pb.set_generator_mode(msd.MSD_GEN_RECOMPUTE)
-                    if kind.startswith("tc"):
+                    if kind == "tcs":
+                        pb.set_tile(R, prec, 0, 8)
+                    elif kind.startswith("tc"):
                         pb.set_tile(R, prec, 0, int(kind[2:]))
                     dt = torch.complex128 if prec == F64 else torch.complex64
                     g = torch.Generator(device="cpu").manual_seed(R)
@@ -286,7 +292,7 @@ def products_table(reps: int = 3):
                     gbs = by / (kms * 1e-3) / 1e9
                     if prec == F64:
                         bound, peak = "fp64 alu", FP64_PEAK_TFLOPS
-                    elif info["KB"] == 0:  # tensor cores: 3 TF32 products per real multiply-add
+                    elif info["KB"] == 0:  # tensor cores (both kernels): 3 TF32 products per real multiply-add
                         bound, peak = "tf32 tensor (3x executed)", tf32_peak / 3.0
                     else:
                         bound, peak = "fp32 alu", FP32_PEAK_TFLOPS
@@ -534,6 +540,8 @@ def main():
                     help="run a minimal workload for a profiler capture and print no JSON line")
     ap.add_argument("--products", action="store_true",
                     help="print a table (JSON lines) of block-product kernels over the workloads instead")
+    ap.add_argument("--products-only", default="",
+                    help="with --products: only the workloads whose name contains this text")
     ap.add_argument("--grad", action="store_true",
                     help="print the timing (JSON lines) of the far-field misfit gradient instead")
     ap.add_argument("--batched", action="store_true",
@@ -558,7 +566,7 @@ def main():
     if args.batched:
         return batched_timing()
     if args.products:
-        return products_table()
+        return products_table(only=args.products_only)
     if args.grad:
         return grad_timing()
     if args.impl == "reference":

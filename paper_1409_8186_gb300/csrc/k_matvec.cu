@@ -437,7 +437,7 @@ MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64) { return choose(R
 // RT = 1; FP32 KB = 4..9 with each column tile RT in {1, 2, 4, 8, 16} that
 // divides R and keeps I * RT / RB <= 16 warps per CTA, and the tensor-core
 // kernel with TC in {16, 32, 64} columns dividing R (n <= 128).
-int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap) {
+int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bool allow_sh) {
     const int n = 2 * Nmax + 1;
     int cnt = 0;
     for (int KB = kKbMin; KB <= (fp64 ? kKbMax64 : kKbMax32); ++KB) {
@@ -463,10 +463,15 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap) {
                 if (cnt < cap) out[cnt] = Choice{0, rc, 0, 0, rc};
                 ++cnt;
             }
+    if (!fp64 && allow_sh && tcs_supported(R, Nmax)) {
+        if (cnt < cap) out[cnt] = Choice{0, MSD_TCS_COLS, 0, 0, 0, 0, 1};
+        ++cnt;
+    }
     return cnt < cap ? cnt : cap;
 }
 
 size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64) {
+    if (c.SH) return tcs_smem_bytes(Nmax);
     if (c.TC) return tc_smem_bytes(c.TC);
     size_t b = 0;
     dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
@@ -475,7 +480,7 @@ size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64) {
 
 // Resident CTAs per SM of one product kernel instance.
 int matvec_blocks_per_sm(const MatvecChoice& c, int Nmax, bool fp64) {
-    if (c.TC) return 1;
+    if (c.TC || c.SH) return 1;
     int nb = 1;
     dispatch(c, fp64, [&](auto k) { nb = decltype(k)::occupancy(Nmax); });
     return nb;

@@ -222,6 +222,13 @@ struct msd_problem {
     float2* d_penA32 = nullptr;
     double2* d_penS = nullptr;
     double* d_pen_mu = nullptr;
+    // shift-GEMM tensor-core product: the complex64 generators in its
+    // A-operand order (TF32 hi/lo), built for geometry version gt_version;
+    // xrows = sum over configurations of Mq * n (its source rows per column)
+    float* d_GT = nullptr;
+    long long gt_floats = 0, gt_blocks = 0, xrows = 0, gt_version = -1;
+    long long* d_gt_blk = nullptr;
+    DBuf xt;
     // algorithmic size of one product with one column (section 5 storage):
     // sum over ordered pairs of the generator length, and of n^2
     double offdiag_L = 0, offdiag_n2 = 0;
@@ -251,7 +258,8 @@ void flush_timing(msd_problem* pb) {
 // A pipeline wait of the tensor-core product expired (results invalid).
 void check_tc(const char* where) {
     const int t = tc_status_and_clear();
-    if (t > 0) fail(MSD_ERR_CUDA, std::string(where) + ": a tensor-core pipeline wait expired");
+    const int u = tcs_status_and_clear();
+    if (t > 0 || u > 0) fail(MSD_ERR_CUDA, std::string(where) + ": a tensor-core pipeline wait expired");
 }
 
 void check_flags(msd_problem* pb, const char* where) {
@@ -342,6 +350,27 @@ void ensure_generators(msd_problem* pb, bool fp64) {
     check_flags(pb, "pair generators");
 }
 
+// Generators of the shift-GEMM tensor-core product (A-operand order, TF32
+// hi/lo), rebuilt after a geometry update.  Returns false when they would
+// take more than 60 % of the free device memory (the kernel is then not
+// offered).
+bool ensure_gt(msd_problem* pb) {
+    ensure_generators(pb, false);
+    if (!pb->d_GT) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        if ((double)pb->gt_floats * 4.0 > 0.6 * (double)free_b) return false;
+        pb->d_GT = dalloc<float>(pb->gt_floats);
+        pb->gt_version = -1;
+    }
+    if (pb->gt_version != pb->geom_version) {
+        launch_tcs_build_gt(pb->d_cfg, pb->C, pb->d_gt_blk, pb->gt_blocks, pb->d_G32, pb->d_GT, pb->stream);
+        CK_LAUNCH();
+        pb->gt_version = pb->geom_version;
+    }
+    return true;
+}
+
 // Target tiles of a product kernel within [P0, P1) (multiples of 32): 32
 // disks for the CUDA-core kernel; for the tensor-core kernel floor(128 / n)
 // disks, restarted at every 32-disk boundary and cut at M.
@@ -360,7 +389,64 @@ void tile_starts(const MsdConfig& c, int P0, int P1, const MatvecChoice& ch, std
 // sources split into ns ranges.  ns is chosen so that the CTAs fill whole
 // waves of the resident slots: efficiency(ns) = (work items / slots) /
 // ceil(...) times the balance of the largest source range against the mean.
+void build_work_tcs(msd_problem* pb, MatvecPlan& plan, int R) {
+    const int rtiles = R / MSD_TCS_COLS;
+    long long units = 0;
+    for (auto& c : pb->cfg) {
+        int mb = 8, nb = 1;
+        tcs_mode_blocks(c.n, &mb, &nb);
+        units += (long long)((c.M + 127) / 128) * ((nb + 1) / 2) * rtiles;
+    }
+    int sms = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long slots = sms;
+    int ns = 1;
+    double best = -1;
+    const int qc_max = (pb->Mmax + 7) / 8;
+    for (int t = 1; t <= std::min(64, qc_max); ++t) {
+        if (t > 1 && (size_t)t * pb->Ntot * R * 8 > (2ull << 30)) break;  // partial sums <= 2 GB
+        const double waves = (double)(units * t) / slots;
+        const double fill = waves / std::ceil(waves);
+        const double per = (double)qc_max / t;
+        const double bal = per / std::ceil(per);
+        const double eff = fill * bal;
+        if (eff > best + 1e-9) {
+            best = eff;
+            ns = t;
+        }
+    }
+    ns = std::max(1, ns / plan.ns_div);
+    plan.nsplit = ns;
+    plan.work.clear();
+    for (int ci = 0; ci < pb->C; ++ci) {
+        const MsdConfig& c = pb->cfg[ci];
+        int mb = 8, nb = 1;
+        tcs_mode_blocks(c.n, &mb, &nb);
+        const int nqc = c.Mq / 8;
+        for (int p0 = 0; p0 < c.M; p0 += 128)
+            for (int b0 = 0; b0 < nb; b0 += 2) {
+                const int nmb = std::min(2, nb - b0);
+                for (int sp = 0; sp < ns; ++sp) {
+                    const int qc0 = (int)((long long)nqc * sp / ns), qc1 = (int)((long long)nqc * (sp + 1) / ns);
+                    MatvecWork w;
+                    w.cfg = ci;
+                    w.p0 = p0;
+                    w.q0 = qc0 * 8;
+                    w.q1 = std::min(c.M, qc1 * 8);
+                    w.split = sp;
+                    w.pad = (b0 * mb) | (mb << 8) | (nmb << 12);
+                    plan.work.push_back(w);
+                }
+            }
+    }
+}
+
 void build_work(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
+    if (plan.ch.SH) {
+        build_work_tcs(pb, plan, R);
+        return;
+    }
     const int rtiles = R / plan.ch.RT;
     std::vector<int> starts;
     long long tiles = 0;
@@ -425,14 +511,14 @@ struct TuneResult {
     double ms;
 };
 
-void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
+void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64, bool allow_sh) {
     static std::mutex mu;
     static std::map<TuneKey, TuneResult> cache;
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    const TuneKey key{pb->Nmax, R, fp64 ? 1 : 0, pb->C, pb->Ntot, pb->Mmax, dev};
+    const TuneKey key{pb->Nmax, R, (fp64 ? 1 : 0) + (allow_sh ? 2 : 0), pb->C, pb->Ntot, pb->Mmax, dev};
     MatvecChoice cand[128];
-    const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 128);
+    const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 128, allow_sh);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -469,6 +555,12 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
         MatvecPlan trial;
         trial.ch = cand[i / 2];
         trial.ns_div = (i & 1) ? 4 : 1;
+        float* XT = nullptr;
+        if (trial.ch.SH) {
+            if (!ensure_gt(pb)) continue;
+            XT = (float*)pb->xt.get((size_t)pb->xrows * 4 * R * sizeof(float));
+            CK(cudaMemsetAsync(XT, 0, (size_t)pb->xrows * 4 * R * sizeof(float), pb->stream));
+        }
         build_work(pb, trial, R, fp64);
         if (!(i & 1)) model_ns = trial.nsplit;
         const int nfull = (int)trial.work.size();
@@ -479,7 +571,10 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
         double t = 1e300;
         for (int rep = 0; rep < 3; ++rep) {  // first run warms caches and the module
             CK(cudaEventRecord(e0, pb->stream));
-            launch_bt_only(cand[i / 2], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
+            if (trial.ch.SH)
+                launch_bt_tcs(pb->d_cfg, dw, nw, pb->Nmax, pb->d_GT, XT, (float2*)part, pb->Ntot, R, pb->stream);
+            else
+                launch_bt_only(cand[i / 2], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
             CK_LAUNCH();
             CK(cudaEventRecord(e1, pb->stream));
             CK(cudaEventSynchronize(e1));
@@ -505,17 +600,27 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64) {
     cache[key] = TuneResult{best, best_div, best_ms};
 }
 
-MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64) {
-    const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
+// Plans are kept per (R, precision) and per use: allow_sh = the forward
+// product of the default rows with stored generators (matvec_dev), the only
+// one that may run the shift-GEMM kernel; every other product (formulations,
+// penetrable, adjoint, raw, recomputed) uses a plan without it.
+long long plan_key(int R, bool fp64, bool allow_sh) {
+    return ((long long)R * 4 + (fp64 ? 0 : 1)) * 2 + (allow_sh ? 1 : 0);
+}
+
+MatvecPlan& get_plan(msd_problem* pb, int R, bool fp64, bool allow_sh = false) {
+    allow_sh = allow_sh && !fp64;
+    const long long key = plan_key(R, fp64, allow_sh);
     auto it = pb->plans.find(key);
     if (it != pb->plans.end()) return it->second;
     MatvecPlan plan;
-    auto pin = pb->pinned.find(key);
+    auto pin = pb->pinned.find((long long)R * 4 + (fp64 ? 0 : 1));
     if (pin != pb->pinned.end()) {
         plan.ch = pin->second;
+        if (plan.ch.SH && !(allow_sh && ensure_gt(pb))) plan.ch = matvec_default_choice(R, pb->Nmax, fp64);
     } else {
         plan.ch = matvec_default_choice(R, pb->Nmax, fp64);
-        if (autotune_enabled()) autotune(pb, plan, R, fp64);
+        if (autotune_enabled()) autotune(pb, plan, R, fp64, allow_sh);
     }
     build_work(pb, plan, R, fp64);
     plan.d_work = dalloc_copy(plan.work.data(), plan.work.size());
@@ -667,7 +772,7 @@ RecomputePlan& get_recompute_plan(msd_problem* pb, int R, bool fp64) {
     auto it = pb->rplans.find(key);
     if (it != pb->rplans.end()) return it->second;
     auto pin = pb->pinned.find(key);
-    if (pin != pb->pinned.end())
+    if (pin != pb->pinned.end() && !pin->second.SH)
         return pb->rplans.emplace(key, build_recompute_plan(pb, R, fp64, pin->second)).first->second;
     RecomputePlan rp = build_recompute_plan(pb, R, fp64, matvec_default_choice(R, pb->Nmax, fp64));
     int rc = 0;
@@ -804,9 +909,10 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
         return;
     }
     ensure_generators(pb, fp64);
-    MatvecPlan& plan = get_plan(pb, R, fp64);
+    MatvecPlan& plan = get_plan(pb, R, fp64, true);
+    if (plan.ch.SH && !ensure_gt(pb)) fail(MSD_ERR_OOM, "shift-GEMM generators do not fit in device memory");
     const size_t elem = fp64 ? 16 : 8;
-    void* xs = pb->xs.get((size_t)pb->Ntot * R * elem);
+    void* xs = plan.ch.SH ? nullptr : pb->xs.get((size_t)pb->Ntot * R * elem);
     void* part = pb->part.get((size_t)plan.nsplit * pb->Ntot * R * elem);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (pb->timing) {
@@ -824,7 +930,17 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
         pb->timed_flops += 8.0 * (double)R * pb->offdiag_n2;
         pb->timed_bytes += sc * ((double)pb->offdiag_L + 2.0 * (double)pb->Ntot * R);
     }
-    if (fp64)
+    if (plan.ch.SH) {
+        // shift-GEMM tensor-core product: columns scaled and split into the
+        // slab order, the kernel, then y = x + l .* (sum of the splits)
+        float* XT = (float*)pb->xt.get((size_t)pb->xrows * 4 * R * sizeof(float));
+        launch_tcs_prep_x(pb->d_cfg, pb->C, pb->xrows / 4, R, pb->d_rf32, (const float2*)x, XT, pb->stream);
+        if (e0) CK(cudaEventRecord(e0, pb->stream));
+        launch_bt_tcs(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_GT, XT, (float2*)part, pb->Ntot,
+                      R, pb->stream);
+        if (e1) CK(cudaEventRecord(e1, pb->stream));
+        launch_finalize(false, pb->Ntot, R, plan.nsplit, pb->d_lf32, x, part, y, pb->stream);
+    } else if (fp64)
         launch_matvec_f64(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G64, pb->d_rf64,
                           pb->d_lf64, pb->Ntot, R, (const double2*)x, (double2*)xs, (double2*)part,
                           plan.nsplit, (double2*)y, pb->stream, e0, e1, &plan.ch);
@@ -1326,6 +1442,7 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             pb->Mtot = Mtot;
             long long row = 0, gen = 0;
             std::vector<int> disk_cfg(Mtot);
+            std::vector<long long> gt_blk;
             for (int c = 0; c < C; ++c) {
                 MsdConfig m;
                 memset(&m, 0, sizeof(m));
@@ -1338,6 +1455,14 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
                 m.disk_off = disk_off[c];
                 m.row_off = row;
                 m.gen_off = gen;
+                m.Mq = (m.M + 7) / 8 * 8;
+                m.gt_off = pb->gt_floats;
+                m.xrow_off = pb->xrows;
+                const long long ptiles = (m.M + 127) / 128;
+                pb->gt_floats += ptiles * m.L * (long long)m.Mq * 512;
+                gt_blk.push_back(pb->gt_blocks);
+                pb->gt_blocks += ptiles * (m.Mq / 4);
+                pb->xrows += (long long)m.Mq * m.n;
                 row += (long long)m.M * m.n;
                 gen += (long long)m.M * m.Mp * m.L;
                 pb->offdiag_L += (double)m.M * (m.M - 1) * m.L;
@@ -1352,6 +1477,7 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             std::vector<double2> cen(Mtot);
             for (int d = 0; d < Mtot; ++d) cen[d] = make_double2(centres[2 * d], centres[2 * d + 1]);
             pb->d_cfg = dalloc_copy(pb->cfg.data(), C);
+            pb->d_gt_blk = dalloc_copy(gt_blk.data(), C);
             pb->d_centre = dalloc_copy(cen.data(), Mtot);
             pb->d_radius = dalloc_copy(radii, Mtot);
             pb->d_bc = dalloc_copy(bc, Mtot);
@@ -1415,7 +1541,7 @@ void msd_destroy(msd_problem* pb) {
                     pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rhs_scale, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                     pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off,
                     pb->d_chunks_coarse, pb->d_cfg_chunk_off_coarse,
-                    pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32};
+                    pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32, pb->d_GT, pb->d_gt_blk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : pb->plans)
@@ -1428,6 +1554,7 @@ void msd_destroy(msd_problem* pb) {
     for (cudaEvent_t e : pb->ring_ev)
         if (e) cudaEventDestroy(e);
     pb->xs.release();
+    pb->xt.release();
     pb->part.release();
     for (auto& b : pb->sbuf) b.release();
     for (auto& b : pb->gbuf) b.release();
@@ -1560,8 +1687,12 @@ msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes
         if (mode == MSD_GEN_RECOMPUTE) {
             if (pb->d_G64) cudaFree(pb->d_G64);
             if (pb->d_G32) cudaFree(pb->d_G32);
+            if (pb->d_GT) cudaFree(pb->d_GT);
             pb->d_G64 = nullptr;
             pb->d_G32 = nullptr;
+            pb->d_GT = nullptr;
+            pb->gt_version = -1;
+            pb->xt.release();
         } else {
             free_recompute_plans(pb);
             pb->genbuf.release();
@@ -1576,7 +1707,7 @@ msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double
         if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_plan_info: precision");
         const bool fp64 = precision == MSD_FP64;
         ensure_generators(pb, fp64);
-        MatvecPlan& plan = get_plan(pb, R, fp64);
+        MatvecPlan& plan = get_plan(pb, R, fp64, true);
         out[0] = plan.ch.KB + 100 * plan.ch.P2;
         out[1] = plan.ch.RT;
         out[2] = plan.nsplit;
@@ -1592,17 +1723,19 @@ msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT) {
         if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_set_tile: precision");
         const bool fp64 = precision == MSD_FP64;
         MatvecChoice cand[128];
-        const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 128);
+        const int nc = matvec_candidates(R, pb->Nmax, fp64, cand, 128, true);
         int hit = -1;
         for (int i = 0; i < nc; ++i)
             if (cand[i].KB + 100 * cand[i].P2 == KB && cand[i].RT == RT) hit = i;
         if (hit < 0) fail(MSD_ERR_ARG, "msd_set_tile: (KB, RT) is not an instantiated shape that fits");
         const long long key = (long long)R * 4 + (fp64 ? 0 : 1);
-        auto it = pb->plans.find(key);
-        if (it != pb->plans.end()) {
-            CK(cudaStreamSynchronize(pb->stream));  // the old work list may still be read
-            if (it->second.d_work) cudaFree(it->second.d_work);
-            pb->plans.erase(it);
+        for (int sh = 0; sh < 2; ++sh) {
+            auto it = pb->plans.find(plan_key(R, fp64, sh != 0));
+            if (it != pb->plans.end()) {
+                CK(cudaStreamSynchronize(pb->stream));  // the old work list may still be read
+                if (it->second.d_work) cudaFree(it->second.d_work);
+                pb->plans.erase(it);
+            }
         }
         auto rit = pb->rplans.find(key);
         if (rit != pb->rplans.end()) {

@@ -63,9 +63,14 @@ struct MsdConfig {
     int N, n, L;      // truncation, modes per disk (2N+1), generator length (4N+1)
     int M, Mp;        // disks, disks padded to a multiple of 32
     int disk_off;     // first global disk index
-    int pad0;
+    int Mq;           // disks padded to a multiple of 8 (sources of the shift-GEMM product)
     long long row_off;  // first unknown row
     long long gen_off;  // first generator element
+    // shift-GEMM tensor-core product (k_matvec_tcs.cu): first float of this
+    // configuration's generators in the A-operand order, and the sum of
+    // Mq * n over the configurations before it (its source rows per column)
+    long long gt_off;
+    long long xrow_off;
 };
 
 // One CTA of the block-Toeplitz product: a tile of 32 target disks
@@ -93,9 +98,13 @@ struct MatvecChoice {
     int KB, RT, RB, I;
     int TC;  // > 0: tensor-core kernel with TC columns per CTA (KB, RB, I unused; RT = TC)
     int P2;  // FP32: 1 = complex multiply-adds as paired FMAs (fma.rn.f32x2), 0 = four FFMAs
+    int SH;  // 1: the shift-GEMM tensor-core kernel (FP32, RT = MSD_TCS_COLS columns per CTA)
 };
+#define MSD_TCS_COLS 8
 MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64);
-int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap);
+// allow_sh: include the shift-GEMM kernel (forward products with stored
+// generators of the default rows only)
+int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bool allow_sh = false);
 size_t matvec_smem_bytes(const MatvecChoice& c, int Nmax, bool fp64);
 int matvec_blocks_per_sm(const MatvecChoice& c, int Nmax, bool fp64);
 // tensor-core product (k_matvec_tc.cu): targets in tiles of floor(128 / n)
@@ -106,6 +115,21 @@ size_t tc_smem_bytes(int RC);
 void launch_bt_tc(int RC, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, const float2* G,
                   const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s);
 int tc_status_and_clear();
+// shift-GEMM tensor-core product (k_matvec_tcs.cu): GT = generators in the
+// A-operand order (built from the complex64 generators), XT = scaled columns
+// in the slab order (built from x each product); work items: p0 a multiple
+// of 128, q0/q1 source range, pad = m0 | mb << 8 | nmb << 12 (first mode,
+// modes per block, blocks)
+size_t tcs_smem_bytes(int Nmax);
+bool tcs_supported(int R, int Nmax);
+void tcs_mode_blocks(int n, int* mb, int* nblocks);
+void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float* GT,
+                   const float* XT, float2* part, long long Ntot, int R, cudaStream_t s);
+void launch_tcs_build_gt(const MsdConfig* d_cfg, int C, const long long* d_blk_off, long long nblocks,
+                         const float2* G32, float* GT, cudaStream_t s);
+void launch_tcs_prep_x(const MsdConfig* d_cfg, int C, long long rows4, int R, const float* rf, const float2* x,
+                       float* XT, cudaStream_t s);
+int tcs_status_and_clear();
 // Set by msd_test_expire_waits: kernels with bounded waits take their
 // expiry path once per launch (tests of the error path; no fault involved).
 extern std::atomic<int> g_msd_expire_waits;  // bit 0: a pipeline wait of the tensor-core kernel expired

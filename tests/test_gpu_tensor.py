@@ -97,3 +97,71 @@ def test_tc_autotuner_candidates(msd):
     ref = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N) @ x.astype(np.complex128)
     y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
     assert relerr(y, ref) < 1e-5
+
+
+# ---------------------------------------------------------------- shift-GEMM kernel
+# KB = 0, RT = 8 pins the shift-GEMM tensor-core kernel (generators streamed
+# in their A-operand order, the sources as a slab, one GEMM per shift d = n - m).
+
+@pytest.mark.parametrize("R", [8, 24, 64])
+def test_shift_gemm_product_rand70(msd, R):
+    """rand70 (n = 25: mode blocks grouped in two CTAs, one ragged), M = 70
+    (one target tile, ragged at 70; 9 K-steps of 8 sources, ragged at 70;
+    three folds of the accumulators), mixed Dirichlet/Neumann."""
+    cl = rand70()
+    x = rand_x(cl.ntot, R, seed=R)
+    ref = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N) @ x.astype(np.complex128)
+    pb = msd.Problem(cl)
+    pb.set_tile(R, msd.MSD_FP32, 0, 8)
+    info, _ = pb.plan_info(R, msd.MSD_FP32)
+    assert info["RT"] == 8 and info["KB"] == 0
+    y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
+    assert relerr(y, ref) < 1e-5
+
+
+def test_shift_gemm_product_batched_and_two_target_tiles(msd):
+    """Batched configurations of different N (n = 3 .. 41) and sizes, one of
+    them with 150 disks (two target tiles of 128), 16 columns (two column
+    tiles); then a geometry update (generators rebuilt) and a second product."""
+    cls = [W.small_mixed(seed=3, M=6, N=10, k=2.0), rand70(), W.four_disks(),
+           W.random_cluster(seed=9, M=40, half_side=12.0, rmin=0.6, rmax=1.0, gap=0.2, k=3.0, N=20),
+           W.random_cluster(seed=10, M=150, half_side=24.0, rmin=0.4, rmax=0.7, gap=0.2, k=1.5, N=1,
+                            neumann_fraction=0.5)]
+    R = 16
+    pb = msd.Problem(cls)
+    pb.set_tile(R, msd.MSD_FP32, 0, 8)
+    for it in range(2):
+        x = rand_x(pb.ntot, R, seed=11 + it)
+        y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
+        off = 0
+        for cl in cls:
+            A = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N)
+            ref = A @ x[off:off + cl.ntot].astype(np.complex128)
+            assert relerr(y[off:off + cl.ntot], ref) < 1e-5, (it, cl.name)
+            off += cl.ntot
+        if it == 0:  # move every disk by the same small offset and rebuild
+            for cl in cls:
+                cl.centres = cl.centres + np.array([0.05, -0.03])
+            cen = np.concatenate([cl.centres for cl in cls])
+            pb.update_geometry(centres=cen)
+
+
+def test_shift_gemm_mixed_solve_and_adjoint_fallback(msd):
+    """A mixed-precision solve whose FP32 products run on the shift-GEMM
+    kernel, and an adjoint (gradient) solve on the same problem, which uses a
+    plan without it."""
+    cl = rand70()
+    betas = W.angles(16)
+    pb = msd.Problem(cl)
+    pb.set_tile(16, msd.MSD_FP32, 0, 8)
+    res = pb.solve(betas, tol=1e-12, precision=msd.MSD_MIXED)
+    assert (res.flags == 0).all(), res.relres
+    rho_ref, _ = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas)
+    assert relerr(res.rho.cpu().numpy(), rho_ref) < 1e-9
+    th = W.angles(12)
+    J, dO, da, dk = pb.grad_farfield_misfit(betas, th, np.zeros((1, 12, 16), np.complex128), tol=1e-12,
+                                            precision=msd.MSD_MIXED)
+    J64, dO64, _, _ = pb.grad_farfield_misfit(betas, th, np.zeros((1, 12, 16), np.complex128), tol=1e-12,
+                                              precision=msd.MSD_FP64)
+    assert abs(J[0] - J64[0]) <= 1e-9 * J64[0]
+    assert np.abs(dO - dO64).max() <= 1e-7 * np.abs(dO64).max()
