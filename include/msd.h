@@ -74,8 +74,11 @@ enum { MSD_DIRICHLET = 0, MSD_NEUMANN = 1 };          /* sound-soft / sound-hard
 enum { MSD_FP64 = 0, MSD_MIXED = 1, MSD_FP32 = 2 };   /* arithmetic of a product   */
 enum { MSD_GEN_AUTO = 0, MSD_GEN_STREAMED = 1, MSD_GEN_RECOMPUTE = 2 };
 
-/* Largest truncation order accepted (modes -N..N, n <= 127). */
-#define MSD_MAX_N 63
+/* Largest truncation order accepted (modes -N..N, n <= 111): every product
+ * kernel runs it (the FP64 CUDA-core kernel covers at most 16 warps x 7
+ * modes per target disk; above N ~ 50 it stages one source at a time).
+ * Eq. (Np) of section 5 reaches it at k a ~ 39 for eps = 1e-10. */
+#define MSD_MAX_N 55
 
 /* Solver options (section 5 and the restarted GMRES call of section 6.2:
  * RESTART, TOL, MAXIT).  Zero-initialised fields take the defaults in

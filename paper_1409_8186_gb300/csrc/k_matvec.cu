@@ -136,7 +136,10 @@ template <typename V, int KB, int RB, int P> struct MacFor { typedef Mac4<V, KB,
 template <int KB, int RB> struct MacFor<double2, KB, RB, 0> { typedef Mac3<double2, KB, RB> type; };
 template <int KB, int RB> struct MacFor<float2, KB, RB, 1> { typedef Mac2<KB, RB> type; };
 
-template <typename V, int RT, int RB, int KB, int P>
+// S = 2: two shared-memory stages (the next source is staged while the
+// current one is summed); S = 1: one stage, staged and then summed, for
+// truncation orders whose two FP64 stages exceed the shared memory of a CTA.
+template <typename V, int RT, int RB, int KB, int P, int S>
 __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
                                                    const MatvecWork* __restrict__ works,
                                                    const V* __restrict__ G, const V* __restrict__ xs,
@@ -153,8 +156,8 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
     const int I = (n + KB - 1) / KB;
     const int npad = I * KB;
     const int gsz = stage_g_elems(L, KB), xsz = stage_x_elems(n, RT, KB);
-    V* gbuf[2] = {smem, smem + gsz + xsz};
-    V* xbuf[2] = {smem + gsz, smem + 2 * gsz + xsz};
+    V* gbuf[2] = {smem, smem + (S == 2 ? gsz + xsz : 0)};
+    V* xbuf[2] = {smem + gsz, smem + (S == 2 ? 2 * gsz + xsz : gsz)};
 
     const int lane = threadIdx.x;  // target p0 + lane
     const int warp = threadIdx.y;
@@ -170,8 +173,8 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
     const int c0 = rgrp * RB;  // first column of this thread within the tile
     const int col0 = rt * RT;  // first column of the tile
 
-    // zero the padding of both stages once (staging never writes it)
-    for (int s = 0; s < 2; ++s) {
+    // zero the padding of the stages once (staging never writes it)
+    for (int s = 0; s < S; ++s) {
         for (int t = tid; t < MSD_TILE_P * 2 * KB; t += nthreads) {
             const int row = t / (2 * KB), j = t % (2 * KB);
             const int pos = j < KB ? j : (L + j);
@@ -208,17 +211,24 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
     Mac acc;
     acc.init();
 
-    if (w.q0 < w.q1) stage(w.q0, 0);
+    if (S == 2 && w.q0 < w.q1) stage(w.q0, 0);
     cp_commit();
     const int base = KB + 2 * N - m0;  // smem position of l' = n - m0 + 2N at n = 0
     for (int it = 0, q = w.q0; q < w.q1; ++it, ++q) {
-        if (q + 1 < w.q1) stage(q + 1, (it + 1) & 1);
-        cp_commit();
-        cp_wait<1>();
+        if (S == 2) {
+            if (q + 1 < w.q1) stage(q + 1, (it + 1) & 1);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            stage(q, 0);
+            cp_commit();
+            cp_wait<0>();
+        }
         __syncthreads();
+        const int sb = S == 2 ? (it & 1) : 0;
         if (mact) {
-            const V* gs = gbuf[it & 1] + lane * Ls + base;
-            const V* xsl = xbuf[it & 1] + c0;
+            const V* gs = gbuf[sb] + lane * Ls + base;
+            const V* xsl = xbuf[sb] + c0;
             typename Mac::G win[KB];
 #pragma unroll
             for (int j = 1; j < KB; ++j) win[KB - j] = Mac::gen(gs[-j]);
@@ -315,6 +325,14 @@ constexpr int kKbMax32 = 9;
 
 using Choice = MatvecChoice;
 
+// Two FP64 stages of the CUDA-core kernel (32 generator rows of L + 2 KB
+// values and the padded source column, complex128) exceed 227 KB.
+bool f64_one_stage(int Nmax, int KB) {
+    const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
+    const int npad = (n + KB - 1) / KB * KB;
+    return 2 * (size_t)(MSD_TILE_P * (L + 2 * KB) + npad) * 16 > 227 * 1024;
+}
+
 Choice choose(int R, int Nmax, bool fp64) {
     const int n = 2 * Nmax + 1;
     Choice best{8, 1, 1, 0};
@@ -346,19 +364,19 @@ Choice choose(int R, int Nmax, bool fp64) {
     return best;
 }
 
-template <typename V, int RT, int RB, int KB, int P = 0>
+template <typename V, int RT, int RB, int KB, int P = 0, int S = 2>
 struct Bt {
     static void attr() {
         static bool done = false;
         if (!done) {
-            cudaFuncSetAttribute(k_bt_matvec<V, RT, RB, KB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_bt_matvec<V, RT, RB, KB, P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  227 * 1024);
             done = true;
         }
     }
     static size_t smem(int Nmax) {
         const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
-        return 2 * (size_t)(stage_g_elems(L, KB) + stage_x_elems(n, RT, KB)) * sizeof(V);
+        return S * (size_t)(stage_g_elems(L, KB) + stage_x_elems(n, RT, KB)) * sizeof(V);
     }
     static dim3 block(int Nmax) {
         const int n = 2 * Nmax + 1;
@@ -368,14 +386,14 @@ struct Bt {
                        const V* xs, V* part, long long Ntot, int R, cudaStream_t s) {
         attr();
         const int rtiles = R / RT;
-        k_bt_matvec<V, RT, RB, KB, P><<<(unsigned)(nwork * rtiles), block(Nmax), smem(Nmax), s>>>(
+        k_bt_matvec<V, RT, RB, KB, P, S><<<(unsigned)(nwork * rtiles), block(Nmax), smem(Nmax), s>>>(
             d_cfg, d_work, G, xs, part, Ntot, R, rtiles);
     }
     static int occupancy(int Nmax) {
         attr();
         const dim3 b = block(Nmax);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB, KB, P>, b.x * b.y,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec<V, RT, RB, KB, P, S>, b.x * b.y,
                                                           smem(Nmax)) != cudaSuccess) {
             cudaGetLastError();
             nb = 1;
@@ -401,13 +419,20 @@ void with_f32(const Choice& c, F&& f) {
     else with_f32_p<KB, 0>(c, f);
 }
 
+// FP64: two stages when they fit in 227 KB of shared memory, else one
+// (choice field I holds ceil(n / KB); c.ONE selects the one-stage kernel).
+template <int KB, typename F>
+void with_f64(const Choice& c, F&& f) {
+    if (c.ONE) f(Bt<double2, 1, 1, KB, 0, 1>());
+    else f(Bt<double2, 1, 1, KB, 0, 2>());
+}
 template <typename F>
 void dispatch64(const Choice& c, F&& f) {
     switch (c.KB) {
-        case 4: f(Bt<double2, 1, 1, 4>()); break;
-        case 5: f(Bt<double2, 1, 1, 5>()); break;
-        case 6: f(Bt<double2, 1, 1, 6>()); break;
-        default: f(Bt<double2, 1, 1, 7>()); break;
+        case 4: with_f64<4>(c, f); break;
+        case 5: with_f64<5>(c, f); break;
+        case 6: with_f64<6>(c, f); break;
+        default: with_f64<7>(c, f); break;
     }
 }
 
@@ -449,6 +474,7 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bo
             if (I * (rt / rb) > 16) continue;
             for (int p2 = 0; p2 <= (fp64 ? 0 : 1); ++p2) {
                 Choice c{KB, rt, rb, I, 0, p2};
+                if (fp64) c.ONE = f64_one_stage(Nmax, KB) ? 1 : 0;
                 size_t b = 0;
                 dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
                 if (b > 227 * 1024) continue;

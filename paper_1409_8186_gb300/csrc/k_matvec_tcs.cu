@@ -482,7 +482,10 @@ size_t tcs_smem_bytes(int Nmax) {
     return (size_t)kStages * kAStage + 2 * 4 * (size_t)(n + 2 * kPad) * 256 + 1024;
 }
 
-bool tcs_supported(int R, int Nmax) { return R % kRC == 0 && tcs_smem_bytes(Nmax) <= 227 * 1024; }
+// dynamic shared memory limit of the kernel: 227 KB less its static part
+constexpr size_t kSmemCap = 226 * 1024;
+
+bool tcs_supported(int R, int Nmax) { return R % kRC == 0 && tcs_smem_bytes(Nmax) <= kSmemCap; }
 
 // Mode blocks of one configuration: block length mb (4..8), blocks grouped
 // two per CTA (TMEM holds 2 blocks x (D1, D2) x 128 columns).  The choice
@@ -512,7 +515,7 @@ void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, 
     if (nwork <= 0) return;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_bt_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_bt_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
         attr = true;
     }
     const int rtiles = R / kRC;

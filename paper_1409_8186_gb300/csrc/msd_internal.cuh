@@ -99,6 +99,7 @@ struct MatvecChoice {
     int TC;  // > 0: tensor-core kernel with TC columns per CTA (KB, RB, I unused; RT = TC)
     int P2;  // FP32: 1 = complex multiply-adds as paired FMAs (fma.rn.f32x2), 0 = four FFMAs
     int SH;  // 1: the shift-GEMM tensor-core kernel (FP32, RT = MSD_TCS_COLS columns per CTA)
+    int ONE;  // FP64: 1 = one shared-memory stage (two would exceed 227 KB at this truncation order)
 };
 #define MSD_TCS_COLS 8
 MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64);

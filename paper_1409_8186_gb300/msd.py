@@ -26,7 +26,7 @@ MSD_FP64, MSD_MIXED, MSD_FP32 = 0, 1, 2
 MSD_GEN_AUTO, MSD_GEN_STREAMED, MSD_GEN_RECOMPUTE = 0, 1, 2
 MSD_FORM_EFIE, MSD_FORM_MFIE, MSD_FORM_CFIE, MSD_FORM_BWIE = 0, 1, 2, 3
 FORMULATION_KINDS = {"efie": MSD_FORM_EFIE, "mfie": MSD_FORM_MFIE, "cfie": MSD_FORM_CFIE, "bwie": MSD_FORM_BWIE}
-MSD_MAX_N = 63
+MSD_MAX_N = 55
 MSD_MAX_DORT = 2048
 
 STATUS_NAMES = {0: "MSD_OK", 1: "MSD_NOT_CONVERGED", 3: "MSD_STAGNATED", -1: "MSD_ERR_ARG",

@@ -320,10 +320,20 @@ def test_batched_mixed_configurations(msd):
         assert relerr(y[o0:o1], dense_pre(cl) @ x[o0:o1]) < 1e-11
     res = pb.solve(betas, tol=1e-10, precision=msd.MSD_MIXED, restart=100)
     assert res.status == msd.MSD_OK, (res.flags, res.relres)
+    rho = np_(res.rho)
     for c, cl in enumerate(cls):
         o0, o1 = pb.row_offset(c), pb.row_offset(c + 1)
+        Ap = dense_pre(cl)
+        bp = O_.preconditioned_rhs(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas[c])
         ref, _ = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas[c], method="lu")
-        assert relerr(np_(res.rho)[o0:o1], ref) < 5e-8
+        for r in range(R):
+            # backward error with the oracle's operator: the stopping test itself
+            back = np.linalg.norm(Ap @ rho[o0:o1, r] - bp[:, r]) / np.linalg.norm(bp[:, r])
+            assert back <= 1.05e-10, (c, r, back)
+            # forward error within the bound relres * cond(P^-1 A), with a factor 2
+            # for the FP32 rounding of the last correction (cond 100 - 275 here)
+            fwd = np.linalg.norm(rho[o0:o1, r] - ref[:, r]) / np.linalg.norm(ref[:, r])
+            assert fwd <= 2 * np.linalg.cond(Ap) * 1e-10, (c, r, fwd)
 
 
 # ---------------------------------------------------------------- errors
@@ -337,3 +347,31 @@ def test_overlap_and_argument_errors(msd):
     with pytest.raises(msd.MsdError) as e:
         msd.Problem(cl)
     assert e.value.status == -1
+    cl = W.Cluster(np.array([[0.0, 0.0]]), np.array([1.0]), np.zeros(1, np.int8), 1.0, msd.MSD_MAX_N + 1)
+    with pytest.raises(msd.MsdError) as e:
+        msd.Problem(cl)
+    assert e.value.status == -1
+
+
+# ---------------------------------------------------------------- the largest truncation order
+
+def test_largest_truncation_order(msd):
+    """N = MSD_MAX_N = 55 (eq. (Np) at k a = 39, eps = 1e-10): two unit disks,
+    one sound-soft and one sound-hard, k = 39.  FP64 products (one shared-memory
+    stage), FP32 products, and an FP64 solve against the oracle."""
+    assert O_.truncation_order(39.0, 1e-10) == msd.MSD_MAX_N
+    cl = W.Cluster(np.array([[0.0, 0.0], [2.3, 0.4]]), np.array([1.0, 1.0]), np.array([0, 1], np.int8), 39.0,
+                   msd.MSD_MAX_N)
+    pb = msd.Problem(cl)
+    A = dense_pre(cl)
+    for R in (1, 3):
+        x = rand_x(cl.ntot, R, seed=R)
+        y = np_(pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP64))
+        assert relerr(y, A @ x) < 1e-11, R
+        x32 = x.astype(np.complex64)
+        y32 = np_(pb.matvec(torch.from_numpy(x32).cuda(), msd.MSD_FP32))
+        assert relerr(y32, A @ x32.astype(np.complex128)) < 1e-5, R
+    res = pb.solve([0.7, 2.0], tol=1e-12)
+    assert res.status == msd.MSD_OK, res.relres
+    ref, _ = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, [0.7, 2.0], method="lu")
+    assert relerr(np_(res.rho), ref) < np.linalg.cond(A) * 1e-11
