@@ -800,3 +800,97 @@ def truncation_order(ka: float, eps: float) -> int:
     (k a_p)^(1/3) + 1], [.] the integer part."""
     t = (np.log(2 * np.sqrt(2) * np.pi * ka / eps) / (2 * np.sqrt(2))) ** (2.0 / 3.0)
     return int(np.floor(ka + t * ka ** (1.0 / 3.0) + 1))
+
+
+# --------------------------------------------------------------------------
+# Section 5: per-disk truncation orders N_p (blocks of size (2N_p+1) x (2N_q+1))
+# --------------------------------------------------------------------------
+
+def ragged_offsets(Ns) -> np.ndarray:
+    """Row offset of each disk's modes -N_p..N_p in the ragged unknown vector
+    (disk after disk); the last entry is N_tot = sum (2 N_p + 1)."""
+    return np.concatenate([[0], np.cumsum(2 * np.asarray(Ns, dtype=int) + 1)])
+
+
+def assemble_ragged(O, a, bc, k, Ns) -> np.ndarray:
+    """Section 5 with a truncation order N_p per disk: the truncated system
+    keeps modes -N_p..N_p on disk p, so block (p, q) is (2N_p+1) x (2N_q+1).
+    Sound-soft rows: L^pq with entries (i pi sqrt(a_p a_q)/2) J_m(k a_p)
+    H_{n-m}(k b_pq) e^{i (n-m) alpha_pq} J_n(k a_q) (section 4.2, (S^pq)^T),
+    diagonal (i pi a_p/2) J_m H_m; sound-hard rows: k J'_m(k a_p) in place
+    of J_m(k a_p) off the diagonal and (i pi k a_p/2) J_m H'_m on it
+    (the exterior trace -I/2 + N, reading of the module header)."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    Ns = np.asarray(Ns, dtype=int)
+    off = ragged_offsets(Ns)
+    A = np.zeros((off[-1], off[-1]), dtype=np.complex128)
+    for p in range(len(a)):
+        m = modes(Ns[p])
+        Jp, dJp = special.jv(m, k * a[p]), special.jvp(m, k * a[p])
+        Hp, dHp = special.hankel1(m, k * a[p]), special.h1vp(m, k * a[p])
+        left = Jp if bc[p] == DIRICHLET else k * dJp
+        for q in range(len(a)):
+            if p == q:
+                d = Jp * Hp * 0.5j * np.pi * a[p] if bc[p] == DIRICHLET else 0.5j * np.pi * k * a[p] * Jp * dHp
+                A[off[p]:off[p + 1], off[p]:off[p + 1]] = np.diag(d)
+                continue
+            nn = modes(Ns[q])
+            _, b, alpha = pair_vector(O[p], O[q])
+            l = nn[None, :] - m[:, None]
+            ST = special.hankel1(l, k * b) * np.exp(1j * l * alpha)
+            Jq = special.jv(nn, k * a[q])
+            A[off[p]:off[p + 1], off[q]:off[q + 1]] = \
+                0.5j * np.pi * np.sqrt(a[p] * a[q]) * left[:, None] * ST * Jq[None, :]
+    return A
+
+
+def rhs_ragged(O, a, bc, k, Ns, betas) -> np.ndarray:
+    """Prop. 4.1 with N_p modes per disk: -U (sound-soft rows, d^p_m J_m) or
+    -dU (sound-hard rows, k d^p_m J'_m), [N_tot, R]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    off = ragged_offsets(Ns)
+    b = np.zeros((off[-1], len(np.atleast_1d(betas))), dtype=np.complex128)
+    for r, beta in enumerate(np.atleast_1d(betas)):
+        for p in range(len(a)):
+            m = modes(Ns[p])
+            phase = k * (np.cos(beta) * O[p, 0] + np.sin(beta) * O[p, 1])
+            d = np.sqrt(2 * np.pi * a[p]) * np.exp(1j * phase) * np.exp(1j * m * (np.pi / 2 - beta))
+            trace = special.jv(m, k * a[p]) if bc[p] == DIRICHLET else k * special.jvp(m, k * a[p])
+            b[off[p]:off[p + 1], r] = -d * trace
+    return b
+
+
+def solve_ragged(O, a, bc, k, Ns, betas) -> np.ndarray:
+    """Section 5: LU solve of the ragged system (the diagonal preconditioner
+    does not change the solution)."""
+    return np.linalg.solve(assemble_ragged(O, a, bc, k, Ns), rhs_ragged(O, a, bc, k, Ns, betas))
+
+
+def preconditioned_ragged(O, a, bc, k, Ns) -> np.ndarray:
+    """P^-1 A of the ragged system, P its diagonal (section 5)."""
+    A = assemble_ragged(O, a, bc, k, Ns)
+    return A / np.diag(A)[:, None]
+
+
+def farfield_ragged(O, a, k, Ns, rho, thetas) -> np.ndarray:
+    """Section 4.4 with N_p modes per disk: a_L(theta) = sum_p sum_m
+    i e^{-i pi/4} sqrt(a_p)/(2 sqrt k) e^{-i k |O_p| cos(theta - alpha_p)}
+    J_m(k a_p) e^{i m (theta - pi/2)} rho^p_m.  rho [N_tot, R] -> [T, R]."""
+    O = np.asarray(O, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    off = ragged_offsets(Ns)
+    rho = np.asarray(rho)
+    if rho.ndim == 1:
+        rho = rho[:, None]
+    th = np.atleast_1d(np.asarray(thetas, dtype=np.float64))
+    F = np.zeros((len(th), rho.shape[1]), dtype=np.complex128)
+    for p in range(len(a)):
+        m = modes(Ns[p])
+        bp, alp = np.hypot(O[p, 0], O[p, 1]), np.arctan2(O[p, 1], O[p, 0])
+        c = (1j * np.exp(-1j * np.pi / 4) * np.sqrt(a[p]) / (2 * np.sqrt(k))) \
+            * np.exp(-1j * bp * k * np.cos(th - alp))[:, None] * special.jv(m, k * a[p])[None, :] \
+            * np.exp(1j * m[None, :] * (th[:, None] - np.pi / 2))
+        F += c @ rho[off[p]:off[p + 1]]
+    return F
