@@ -86,8 +86,8 @@ def test_hankel_recurrences_vs_mpmath_table(msd):
     import os
     tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hankel_hp.json")))["table"]
     for ent in tab:
-        x, N = ent["x"], ent["N"]
-        ref = np.array(ent["re"]) + 1j * np.array(ent["im"])
+        x, N = ent["x"], min(ent["N"], msd.MSD_MAX_N)    # the table reaches l = 126; the library 2 MSD_MAX_N
+        ref = (np.array(ent["re"]) + 1j * np.array(ent["im"]))[:2 * N + 1]
         a = min(0.4 * x, 1.0)
         cl = W.Cluster(np.array([[0.0, 0.0], [x, 0.0]]), np.array([a, a]), np.zeros(2, np.int8), 1.0, N)
         pb = msd.Problem(cl)
