@@ -414,6 +414,25 @@ msd_status msd_dort(msd_problem* pb, int n_alpha, const msd_opts* opts, void* F_
  * Synchronises the stream. */
 msd_status msd_dort_eigen(msd_problem* pb, int n_alpha, const void* F, void* T_out, void* eig_out);
 
+/* Per-disk truncation orders (section 5: disk p keeps the modes
+ * -N_p..N_p, the blocks of the truncated system are (2N_p+1) x (2N_q+1);
+ * eq. (Np) gives N_p from k a_p).  Vectors keep the layout [N_tot][R] of the
+ * configurations' N: the rows of modes |m| > N_p of disk p become an
+ * identity block with a zero right-hand side that no product couples to the
+ * other rows, so every solve leaves them zero (GMRES from x0 = 0) and their
+ * densities add nothing to a far or near field.  On the other rows the
+ * solution is that of the system truncated at N_p on every disk; a product
+ * returns y = x on the dropped rows.  The kernels still run the padded
+ * blocks; msd_matvec_timing counts the flops and bytes of the truncated
+ * blocks.
+ *   Np  host int [disk_off[C]], 0 <= Np[d] <= N of the disk's configuration;
+ *       NULL restores N on every disk
+ * Needs the default rows: MSD_ERR_ARG with a formulation or penetrable
+ * obstacles (and msd_set_formulation, msd_set_formulation_kind,
+ * msd_set_penetrable and msd_grad_farfield_misfit refuse while orders are
+ * set).  Synchronises the stream. */
+msd_status msd_set_truncation(msd_problem* pb, const int* Np);
+
 /* Generators of the forward products (the Toeplitz storage of section 5).
  *   MSD_GEN_STREAMED (default): the 4N+1 values of every ordered pair are
  *     stored in HBM (complex128, plus complex64 for FP32 products) and read

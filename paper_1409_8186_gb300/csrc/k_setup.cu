@@ -84,6 +84,37 @@ __global__ void k_disk_diagonals(const MsdConfig* __restrict__ cfg, int Mtot,
     if (bad) atomicOr(flags, FLAG_NONFINITE);
 }
 
+// Per-disk truncation orders (section 5): the rows of modes |m| > N_p of
+// disk p get zero row and column factors and a zero right-hand-side scale,
+// so they form an identity block with a zero right-hand side that no product
+// couples to the other rows: the padded system has the solution of the one
+// truncated at N_p on every disk, and zeros on the dropped modes.
+__global__ void k_mask_rows(const MsdConfig* __restrict__ cfg, int Mtot, const int* __restrict__ disk_cfg,
+                            const int* __restrict__ Np, double2* lf64, float2* lf32, double* rf64, float* rf32,
+                            double2* rhs_scale) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= Mtot) return;
+    const MsdConfig c = cfg[disk_cfg[d]];
+    const long long row0 = c.row_off + (long long)(d - c.disk_off) * c.n;
+    const int np = Np[d];
+    for (int i = 0; i < c.n; ++i) {
+        const int m = i - c.N;
+        if (m >= -np && m <= np) continue;
+        const long long row = row0 + i;
+        lf64[row] = make_double2(0.0, 0.0);
+        lf32[row] = make_float2(0.f, 0.f);
+        rf64[row] = 0.0;
+        rf32[row] = 0.f;
+        rhs_scale[row] = make_double2(0.0, 0.0);
+    }
+}
+
+void launch_mask_rows(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg, const int* d_Np, double2* lf64,
+                      float2* lf32, double* rf64, float* rf32, double2* rhs_scale, cudaStream_t s) {
+    k_mask_rows<<<(Mtot + 127) / 128, 128, 0, s>>>(d_cfg, Mtot, d_disk_cfg, d_Np, lf64, lf32, rf64, rf32, rhs_scale);
+    g_msd_launches += 1;
+}
+
 void launch_disk_diagonals(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg,
                            const double* d_radius, const int8_t* d_bc, int /*Nmax*/,
                            double2* J, double2* dJ, double2* H, double2* dH,

@@ -225,6 +225,10 @@ struct msd_problem {
     // shift-GEMM tensor-core product: the complex64 generators in its
     // A-operand order (TF32 hi/lo), built for geometry version gt_version;
     // xrows = sum over configurations of Mq * n (its source rows per column)
+    // per-disk truncation orders (msd_set_truncation); d_Np == nullptr: N of
+    // the configuration on every disk
+    std::vector<int> Np;
+    int* d_Np = nullptr;
     float* d_GT = nullptr;
     long long gt_floats = 0, gt_blocks = 0, xrows = 0, gt_version = -1;
     long long* d_gt_blk = nullptr;
@@ -300,6 +304,31 @@ void form_rows(msd_problem* pb) {
         fail(MSD_ERR_NONFINITE,
              "msd_set_formulation: the self block of the combination vanishes for some mode (a resonance of this "
              "formulation at k a_p)");
+}
+
+// Per-disk truncation: mask the default rows' factors (after every K1).
+void apply_truncation(msd_problem* pb) {
+    if (!pb->d_Np) return;
+    launch_mask_rows(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_Np, pb->d_lf64, pb->d_lf32, pb->d_rf64, pb->d_rf32,
+                     pb->d_rhs_scale, pb->stream);
+    CK_LAUNCH();
+}
+
+// Algorithmic size of one product (generator values and multiply-adds of
+// the off-diagonal blocks) with the truncation orders in force.
+void count_offdiag(msd_problem* pb) {
+    pb->offdiag_L = pb->offdiag_n2 = 0;
+    for (const MsdConfig& c : pb->cfg) {
+        double sN = 0, sn = 0, sn2 = 0;
+        for (int d = c.disk_off; d < c.disk_off + c.M; ++d) {
+            const int np = pb->Np.empty() ? c.N : pb->Np[d];
+            sN += np;
+            sn += 2.0 * np + 1;
+            sn2 += (2.0 * np + 1) * (2.0 * np + 1);
+        }
+        pb->offdiag_L += 4.0 * (c.M - 1) * sN + (double)c.M * (c.M - 1);
+        pb->offdiag_n2 += sn * sn - sn2;
+    }
 }
 
 // Per-row transmission factors from the Bessel diagonals at k+ and k-.
@@ -1541,7 +1570,7 @@ void msd_destroy(msd_problem* pb) {
                     pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rhs_scale, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                     pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off,
                     pb->d_chunks_coarse, pb->d_cfg_chunk_off_coarse,
-                    pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32, pb->d_GT, pb->d_gt_blk};
+                    pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32, pb->d_GT, pb->d_gt_blk, pb->d_Np};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : pb->plans)
@@ -1657,6 +1686,7 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
         if (pb->d_G64 || pb->d_G32) launch_full_generators(pb, pb->d_G64, pb->d_G32);
         CK_LAUNCH();
         check_flags(pb, "msd_update_geometry");
+        apply_truncation(pb);
         if (pb->form) form_rows(pb);
         if (pb->pen_minus) {
             const msd_status st = msd_update_geometry(pb->pen_minus, centres, radii, nullptr);
@@ -1664,6 +1694,40 @@ msd_status msd_update_geometry(msd_problem* pb, const double* centres, const dou
             pen_rows(pb);
         }
         pb->geom_version += 1;  // adjoint operator data is rebuilt on next use
+        return MSD_OK;
+    });
+}
+
+msd_status msd_set_truncation(msd_problem* pb, const int* Np) {
+    return guarded([&]() -> msd_status {
+        if (!pb) fail(MSD_ERR_ARG, "msd_set_truncation: bad handle");
+        if (pb->form || pb->pen_minus || pb->pen_parent)
+            fail(MSD_ERR_ARG, "msd_set_truncation: needs the default rows (no formulation, not penetrable)");
+        if (Np)
+            for (const MsdConfig& c : pb->cfg)
+                for (int d = c.disk_off; d < c.disk_off + c.M; ++d)
+                    if (Np[d] < 0 || Np[d] > c.N)
+                        fail(MSD_ERR_ARG, "msd_set_truncation: N_p of disk " + std::to_string(d) +
+                                              " outside 0..N of its configuration");
+        CK(cudaStreamSynchronize(pb->stream));
+        if (pb->d_Np) cudaFree(pb->d_Np);
+        pb->d_Np = nullptr;
+        pb->Np.clear();
+        if (Np) {
+            pb->Np.assign(Np, Np + pb->Mtot);
+            pb->d_Np = dalloc_copy(pb->Np.data(), pb->Mtot);
+        }
+        // fresh factors of every row, then the mask
+        CK(cudaMemsetAsync(pb->d_flags, 0, sizeof(int), pb->stream));
+        launch_disk_diagonals(pb->d_cfg, pb->Mtot, pb->d_disk_cfg, pb->d_radius, pb->d_bc, pb->Nmax, pb->d_J,
+                              pb->d_dJ, pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rf64, pb->d_lf32, pb->d_rf32,
+                              pb->d_rhs_scale, pb->d_flags, pb->stream);
+        CK_LAUNCH();
+        check_flags(pb, "msd_set_truncation");
+        apply_truncation(pb);
+        count_offdiag(pb);
+        pb->geom_version += 1;  // adjoint row factors are rebuilt on next use
+        CK(cudaStreamSynchronize(pb->stream));
         return MSD_OK;
     });
 }
@@ -1782,6 +1846,7 @@ msd_status msd_grad_farfield_misfit(msd_problem* pb, int R, const double* betas_
         if (!pb || R <= 0 || T <= 0 || !betas_host || !thetas_host || !F_target)
             fail(MSD_ERR_ARG, "msd_grad_farfield_misfit: bad argument");
         if (pb->form) fail(MSD_ERR_ARG, "msd_grad_farfield_misfit: needs the default formulation");
+        if (pb->d_Np) fail(MSD_ERR_ARG, "msd_grad_farfield_misfit: not with per-disk truncation orders");
         cudaStream_t s = pb->stream;
         const long long nv = pb->Ntot * R;
         const size_t nF = (size_t)pb->C * T * R;
@@ -1905,6 +1970,7 @@ msd_status msd_set_penetrable(msd_problem* pb, const double* k_minus, const doub
             pen_release(pb);
             return MSD_OK;
         }
+        if (pb->d_Np) fail(MSD_ERR_ARG, "msd_set_penetrable: not with per-disk truncation orders");
         if (pb->form) fail(MSD_ERR_ARG, "msd_set_penetrable: needs the default formulation");
         const int C = pb->C, Mtot = pb->Mtot;
         for (int c = 0; c < C; ++c)
@@ -2059,6 +2125,7 @@ msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const 
         }
         if (!rhs_weights || !rep_weights) fail(MSD_ERR_ARG, "msd_set_formulation: bad argument");
         if (pb->pen_minus) fail(MSD_ERR_ARG, "msd_set_formulation: not with penetrable obstacles");
+        if (pb->d_Np) fail(MSD_ERR_ARG, "msd_set_formulation: not with per-disk truncation orders");
         MsdFormulation w{};
         for (int c = 0; c < 2; ++c) {
             for (int o = 0; o < 5; ++o)
@@ -2101,6 +2168,7 @@ msd_status msd_set_formulation_kind(msd_problem* pb, int kind, double alpha, con
         if (!pb) fail(MSD_ERR_ARG, "msd_set_formulation_kind: bad handle");
         check_kind("msd_set_formulation_kind", kind, alpha, eta);
         if (pb->pen_minus) fail(MSD_ERR_ARG, "msd_set_formulation_kind: not with penetrable obstacles");
+        if (pb->d_Np) fail(MSD_ERR_ARG, "msd_set_formulation_kind: not with per-disk truncation orders");
         MsdFormulation w{};
         w.kind = kind;
         w.alpha = alpha;

@@ -197,6 +197,11 @@ void launch_pen_finalize(bool fp64, const MsdConfig* cfg, int C, long long Ntot,
 void launch_pen_layout(const MsdConfig* cfg, int C, long long Ntot, int R, bool to_pen, double2* pen, double2* xp,
                        double2* xm, cudaStream_t s);
 
+// Per-disk truncation N_p <= N (section 5): zero the row factors l, the
+// column factors r and the right-hand-side scale of the rows |m| > N_p.
+void launch_mask_rows(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg, const int* d_Np, double2* lf64,
+                      float2* lf32, double* rf64, float* rf32, double2* rhs_scale, cudaStream_t s);
+
 // Integral-equation formulation (sections 3, 4.2, 5): per boundary
 // condition c (0 Dirichlet, 1 Neumann) the weights of I, L, M, N, D in the
 // rows of its disks and of U, dU in their right-hand side, and the weights

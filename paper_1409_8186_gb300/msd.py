@@ -89,6 +89,7 @@ def _load():
         "msd_solve_penetrable_pointsources": (I, [P, I, P, ctypes.POINTER(msd_opts), P, P, P]),
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_test_expire_waits": (V, [I]),
+        "msd_set_truncation": (I, [P, P]),
         "msd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -105,7 +106,7 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
             "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_formulation_kind",
-            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_penetrable",
+            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_truncation", "msd_set_penetrable",
             "msd_penetrable_matvec", "msd_solve_penetrable", "msd_solve_penetrable_pointsources",
             "msd_last_error")
 
@@ -365,6 +366,15 @@ def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
 
 
+def msd_set_truncation(h, Np) -> None:
+    """Per-disk truncation orders N_p (host int [disk_off[C]]); None restores N."""
+    if Np is None:
+        _check(_lib.msd_set_truncation(h, None))
+        return
+    arr = np.ascontiguousarray(Np, dtype=np.int32)
+    _check(_lib.msd_set_truncation(h, _ptr(arr)))
+
+
 def msd_test_expire_waits(on: bool) -> None:
     """Test hook: bounded device waits take their expiry path (include/msd.h)."""
     _lib.msd_test_expire_waits(1 if on else 0)
@@ -595,6 +605,10 @@ class Problem:
 
     def update_geometry(self, centres=None, radii=None, k=None):
         msd_update_geometry(self.handle, centres, radii, k)
+
+    def set_truncation(self, Np=None):
+        """Per-disk truncation orders N_p <= N (None: N on every disk)."""
+        msd_set_truncation(self.handle, Np)
 
     def grad_farfield_misfit(self, betas, thetas, F_target, tol=1e-12, precision=MSD_FP64, restart=0,
                              maxit=3000):
