@@ -350,6 +350,7 @@ Choice choose(int R, int Nmax, bool fp64) {
             best = Choice{KB, 1, 1, I};
         }
     }
+    if (fp64) best.ONE = f64_one_stage(Nmax, best.KB) ? 1 : 0;
     if (!fp64) {
         const int rb_max = 4;
         for (int rt = 2; rt <= 16; rt *= 2) {
