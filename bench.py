@@ -190,18 +190,21 @@ def aggregate(local_ms: float, local_bytes: float, dist, device="cpu"):
 def profile_only(what: str):
     """Minimal runs for ncu captures: 'matvec' = three FP64 then three FP32
     products of the 400-disk operator; 'fp64' / 'mixed' = one solve;
-    'tc' = three tensor-core FP32 products with 64 columns on the first 800
-    sites of the 4000-disk lattice (generators 0.31 GB, above L2);
+    'tc' / 'tcs' = three tensor-core FP32 products with 64 columns on the
+    first 800 sites of the 4000-disk lattice (generators 0.31 GB, above L2;
+    the expanding kernel / the shift-GEMM kernel);
     'recompute' = three FP32 products of the same operator with recomputed
     generators."""
     import torch
     from paper_1409_8186_gb300 import msd, workloads as W
-    if what in ("tc", "recompute"):
+    if what in ("tc", "tcs", "recompute"):
         cl = W.lattice_4000(M=800)
         pb = msd.Problem(cl)
-        R = 64 if what == "tc" else 1
+        R = 64 if what in ("tc", "tcs") else 1
         if what == "tc":
             pb.set_tile(R, msd.MSD_FP32, 0, 64)
+        elif what == "tcs":
+            pb.set_tile(R, msd.MSD_FP32, 0, 8)
         else:
             pb.set_generator_mode(msd.MSD_GEN_RECOMPUTE)
         g = torch.Generator(device="cpu").manual_seed(0)
@@ -368,6 +371,104 @@ def batched_timing(count: int = 16):
                           "iters_max": int(res.iters.max()), "refine_steps": int(res.refine_steps.max()),
                           "relres_max": float(res.relres.max())}), flush=True)
     pb.close()
+
+
+def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_rows: int = 2):
+    """The batched workload as specified: 256 seeded clusters (M ~ U{50..800},
+    unit radii, area fraction 0.2, gap 0.01, k ~ U[1, 8], N = ceil(k) + 8,
+    Dirichlet/Neumann per disk ~ Bernoulli(1/2)), 32 incidences each,
+    mixed-precision solve (FP32 inner sweeps, FP64 refinement) to relres
+    1e-10.  The clusters are ordered by M and solved as `groups` batched
+    problems of consecutive sizes (each group's Krylov basis and generators
+    fit in HBM together with a long restart); one JSON line per group and
+    one for the whole batch.  Every cluster is checked on `check_rows`
+    sampled target disks: the oracle's residual of the GPU densities on
+    those rows must be within the stopping bound (1.05e-10 ||P^-1 b||)."""
+    import numpy as np
+    import torch
+    import oracle.msd_oracle as O_
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cls = W.batched_clusters(count=256)
+    order = sorted(range(len(cls)), key=lambda i: cls[i].M)[:take]
+    R = 32
+    betas_all = W.angles(R)
+    chunks = np.array_split(np.array(order), groups)
+    tot_ms, worst_rel, worst_check, tot_iters = 0.0, 0.0, 0.0, 0
+    rows_done = 0
+    for gi, idx in enumerate(chunks):
+        sub = [cls[i] for i in idx]
+        pb = msd.Problem(sub)
+        betas = np.stack([betas_all] * len(sub))
+        info32, _ = pb.plan_info(R, msd.MSD_FP32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = pb.solve(betas, tol=1e-10, precision=msd.MSD_MIXED, maxit=maxit)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rho = res.rho.cpu().numpy()
+        worst = 0.0
+        for c, cl in enumerate(sub):
+            o0 = pb.row_offset(c)
+            b = O_.preconditioned_rhs(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas[c])
+            bn = np.linalg.norm(b, axis=0)
+            tg = sorted(set([0, cl.M - 1] + list(np.random.default_rng(c).choice(cl.M, check_rows, replace=False))))
+            rows = O_.preconditioned_rows(cl.centres, cl.radii, cl.bc, cl.k, cl.N, rho[o0:o0 + cl.ntot], tg)
+            for i, p in enumerate(tg):
+                r = b[p * cl.n:(p + 1) * cl.n] - rows[i]
+                worst = max(worst, float((np.linalg.norm(r, axis=0) / bn).max()))
+        tot_ms += ms
+        worst_rel = max(worst_rel, float(res.relres.max()))
+        worst_check = max(worst_check, worst)
+        tot_iters = max(tot_iters, int(res.iters.max()))
+        rows_done += pb.ntot
+        print(json.dumps({"workload": f"batched recipe, group {gi + 1}/{len(chunks)} (M {sub[0].M}..{sub[-1].M})",
+                          "clusters": len(sub), "systems": len(sub) * R, "unknowns": int(pb.ntot),
+                          "fp32_product_shape": info32, "solve_ms": round(ms, 1), "status": int(res.status),
+                          "iters_max": int(res.iters.max()), "iters_median": float(np.median(res.iters)),
+                          "refine_steps": int(res.refine_steps.max()), "relres_max": float(res.relres.max()),
+                          "sampled_residual_max": worst}), flush=True)
+        pb.close()
+        del pb, res, rho
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"batched recipe, {len(order)} clusters x {R} incidences, mixed precision to relres 1e-10",
+                      "groups": len(chunks), "unknowns_per_column": int(rows_done), "solve_ms_total": round(tot_ms, 1),
+                      "iters_max": tot_iters, "relres_max": worst_rel, "sampled_residual_max": worst_check,
+                      "all_within_bound": bool(worst_check <= 1.05e-10 and worst_rel <= 1e-10)}), flush=True)
+
+
+def lattice_solve(R: int = 8, maxit: int = 30000, check_rows: int = 6):
+    """The 4000-disk lattice (radius 0.3, spacing 1, jitter 0.02, k = 5,
+    N = 15, 124,000 unknowns) with R incidences, mixed-precision solve to
+    relres 1e-10 (restart sized to HBM, up to 4000); CUDA events around the
+    solve; the oracle's residual on sampled target rows of every column."""
+    import numpy as np
+    import torch
+    import oracle.msd_oracle as O_
+    from paper_1409_8186_gb300 import msd, workloads as W
+    cl = W.lattice_4000()
+    pb = msd.Problem(cl)
+    betas = W.angles(R)
+    info32, _ = pb.plan_info(R, msd.MSD_FP32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = pb.solve(betas, tol=1e-10, precision=msd.MSD_MIXED, maxit=maxit)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rho = res.rho.cpu().numpy()
+    b = O_.preconditioned_rhs(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas)
+    bn = np.linalg.norm(b, axis=0)
+    tg = sorted(set([0, cl.M - 1] + list(np.random.default_rng(5).choice(cl.M, check_rows, replace=False))))
+    rows = O_.preconditioned_rows(cl.centres, cl.radii, cl.bc, cl.k, cl.N, rho, tg)
+    worst = max(float((np.linalg.norm(b[p * cl.n:(p + 1) * cl.n] - rows[i], axis=0) / bn).max())
+                for i, p in enumerate(tg))
+    print(json.dumps({"workload": f"lattice4000 (M=4000, N=15, 124000 unknowns), {R} incidences, mixed to 1e-10",
+                      "fp32_product_shape": info32, "solve_ms": round(ms, 1), "status": int(res.status),
+                      "iters_max": int(res.iters.max()), "refine_steps": int(res.refine_steps.max()),
+                      "relres_max": float(res.relres.max()), "sampled_residual_max": worst}), flush=True)
 
 
 def nearfield_timing(n: int = 512):
@@ -546,6 +647,12 @@ def main():
                     help="print the timing (JSON lines) of the far-field misfit gradient instead")
     ap.add_argument("--batched", action="store_true",
                     help="print FP64 and mixed batched solve times (JSON lines) instead")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="solve all 256 batched clusters (32 incidences, mixed precision) and print JSON lines")
+    ap.add_argument("--groups", type=int, default=8, help="with --batched-full: batched problems of similar M")
+    ap.add_argument("--take", type=int, default=256, help="with --batched-full: the smallest TAKE clusters only")
+    ap.add_argument("--lattice-solve", type=int, default=0, metavar="R",
+                    help="solve the 4000-disk lattice with R incidences (mixed precision) and print a JSON line")
     ap.add_argument("--nearfield", action="store_true",
                     help="print the timing (JSON line) of the near field on a grid instead")
     ap.add_argument("--penetrable", action="store_true",
@@ -563,6 +670,10 @@ def main():
         return penetrable_timing()
     if args.nearfield:
         return nearfield_timing()
+    if args.lattice_solve:
+        return lattice_solve(R=args.lattice_solve)
+    if args.batched_full:
+        return batched_full(groups=args.groups, take=args.take)
     if args.batched:
         return batched_timing()
     if args.products:

@@ -1214,21 +1214,21 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     } mode_guard{pb, pb->gen_mode};
     if (o.gen_mode != MSD_GEN_AUTO && !adjoint) pb->gen_mode = o.gen_mode;
     if (o.tol <= 0) o.tol = 1e-10;
+    if (o.maxit <= 0) o.maxit = 3000;
     if (o.restart <= 0) {
         // Automatic restart length: GMRES converges fastest unrestarted, and
         // HBM is large, so take the longest Krylov basis that fits in half of
         // the free device memory and keeps the per-system Hessenberg
-        // matrices within 2 GB, capped by maxit and by 4000.
+        // matrices within 8 % of it (at least 2 GB), capped by maxit and by 4000.
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
         const double vec = (double)pb->Ntot * R * ((o.precision == MSD_MIXED) ? 8 : 16);
         const double S_ = (double)pb->C * R;
         const long long m_mem = (long long)(0.5 * (double)free_b / vec) - 2;
-        const long long m_hess = (long long)std::sqrt(2e9 / (16.0 * S_));
+        const long long m_hess = (long long)std::sqrt(std::max(2e9, 0.08 * (double)free_b) / (16.0 * S_));
         long long m = std::min<long long>({m_mem, m_hess, (long long)o.maxit, 4000LL});
         o.restart = (int)std::max<long long>(m, 10);
     }
-    if (o.maxit <= 0) o.maxit = 3000;
     if (o.max_refine <= 0) o.max_refine = 60;
     if (o.inner_tol <= 0) o.inner_tol = 2e-6;
     if (o.precision != MSD_FP64 && o.precision != MSD_MIXED) fail(MSD_ERR_ARG, "msd_solve_planewaves: precision");
