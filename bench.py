@@ -637,7 +637,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed", "tc", "recompute"], default=None,
+    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed", "tc", "tcs", "recompute"], default=None,
                     help="run a minimal workload for a profiler capture and print no JSON line")
     ap.add_argument("--products", action="store_true",
                     help="print a table (JSON lines) of block-product kernels over the workloads instead")
