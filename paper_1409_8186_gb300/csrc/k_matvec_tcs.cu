@@ -37,6 +37,7 @@
 // writes nothing, frees TMEM and returns.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "msd_internal.cuh"
@@ -47,7 +48,7 @@ namespace {
 
 constexpr int kRC = MSD_TCS_COLS;  // columns per CTA (8)
 constexpr int kPad = 7;             // zero modes on either side of the slab
-constexpr int kStages = 4;          // A ring
+constexpr int kStagesMax = 8;       // A ring: as many 16 KB stages as fit next to the slab, 3..8
 constexpr int kAStage = 16384;      // bytes of one A stage (Gr hi/lo, Gi hi/lo, 2 x 4 sources)
 constexpr int kThreads = 320;
 constexpr int kFoldQc = 4;          // K-steps of 8 sources between folds into registers
@@ -143,11 +144,11 @@ __device__ __forceinline__ float tf32_rna(float x) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_bt_tcs(const MsdConfig* __restrict__ cfgs, const MatvecWork* __restrict__ works, const float* __restrict__ GT,
              const float* __restrict__ XT, float2* __restrict__ part, long long Ntot, int R, int rtiles,
-             int expire_test) {
+             int kStages, int expire_test) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint32_t tmem_sh;
-    __shared__ __align__(8) uint64_t a_full[kStages], a_empty[kStages];
+    __shared__ __align__(8) uint64_t a_full[kStagesMax], a_empty[kStagesMax];
     __shared__ __align__(8) uint64_t s_full[2], s_empty[2];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
     __shared__ int abort_sh, never_sh;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         abort_sh = 0;
         never_sh = 0;
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kStagesMax; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_empty[s])));
         }
@@ -215,7 +216,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float* gt = GT + c.gt_off + (long long)ptile * L * (c.Mq / 4) * 2048;
         const float* xt = XT + c.xrow_off * 4 * R + (long long)rt * c.Mq * n * 32;
         long long ait = 0;
-        for (int qi = 0; qi < nqc; ++qi) {
+        // slab of K-step qi; issued one K-step ahead, once the MMAs of K-step
+        // qi - 2 (the previous user of its buffer) have certainly completed
+        auto issue_slab = [&](int qi) {
             const int qc = qc0 + qi, sb = qi & 1;
             if (qi >= 2) {
                 if (!*abort_v && !mbar_wait(smem_u32(&s_empty[sb]), ((qi >> 1) - 1) & 1)) *abort_v = 1;
@@ -228,7 +231,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int hl = 0; hl < 2; ++hl)
                     bulk_g2s(smem_u32(slab + sb * buf + (h * 2 + hl) * blk + kPad * 256),
                              xt + ((long long)(2 * qc + h) * 2 + hl) * n * 64, (uint32_t)n * 256u, sbar);
+        };
+        if (nqc > 0) issue_slab(0);
+        const int next_at = min(nd - 1, kStages);
+        for (int qi = 0; qi < nqc; ++qi) {
+            const int qc = qc0 + qi;
             for (int d = dlo; d <= dhi; ++d, ++ait) {
+                // the next slab once kStages A stages of this K-step are issued:
+                // the MMAs of K-step qi - 1 are then complete
+                if (d - dlo == next_at && qi + 1 < nqc) issue_slab(qi + 1);
                 const int s = (int)(ait % kStages);
                 if (ait >= kStages) {
                     const uint32_t ph = (uint32_t)((ait / kStages - 1) & 1);
@@ -477,15 +488,20 @@ __global__ void k_tcs_prep_x(const MsdConfig* __restrict__ cfgs, int C, long lon
 
 }  // namespace
 
-size_t tcs_smem_bytes(int Nmax) {
-    const int n = 2 * Nmax + 1;
-    return (size_t)kStages * kAStage + 2 * 4 * (size_t)(n + 2 * kPad) * 256 + 1024;
-}
-
 // dynamic shared memory limit of the kernel: 227 KB less its static part
 constexpr size_t kSmemCap = 226 * 1024;
 
-bool tcs_supported(int R, int Nmax) { return R % kRC == 0 && tcs_smem_bytes(Nmax) <= kSmemCap; }
+size_t tcs_slab_bytes(int Nmax) { return 2 * 4 * (size_t)(2 * Nmax + 1 + 2 * kPad) * 256; }
+
+// A stages that fit next to the two slab buffers (at most kStagesMax)
+int tcs_stages(int Nmax) {
+    const long long room = (long long)kSmemCap - 1024 - (long long)tcs_slab_bytes(Nmax);
+    return (int)std::min<long long>(kStagesMax, std::max<long long>(0, room / kAStage));
+}
+
+size_t tcs_smem_bytes(int Nmax) { return (size_t)tcs_stages(Nmax) * kAStage + tcs_slab_bytes(Nmax) + 1024; }
+
+bool tcs_supported(int R, int Nmax) { return R % kRC == 0 && tcs_stages(Nmax) >= 3; }
 
 // Mode blocks of one configuration: block length mb (4..8), blocks grouped
 // two per CTA (TMEM holds 2 blocks x (D1, D2) x 128 columns).  The choice
@@ -520,7 +536,7 @@ void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, 
     }
     const int rtiles = R / kRC;
     k_bt_tcs<<<(unsigned)((long long)nwork * rtiles), kThreads, tcs_smem_bytes(Nmax), s>>>(
-        d_cfg, d_work, GT, XT, part, Ntot, R, rtiles, g_msd_expire_waits.load());
+        d_cfg, d_work, GT, XT, part, Ntot, R, rtiles, tcs_stages(Nmax), g_msd_expire_waits.load());
     g_msd_launches += 1;
 }
 

@@ -1770,6 +1770,16 @@ msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double
         if (!pb || R <= 0 || !out) fail(MSD_ERR_ARG, "msd_plan_info: bad argument");
         if (precision != MSD_FP64 && precision != MSD_FP32) fail(MSD_ERR_ARG, "msd_plan_info: precision");
         const bool fp64 = precision == MSD_FP64;
+        if (pb->gen_mode == MSD_GEN_RECOMPUTE && !pb->form && !pb->pen_minus) {
+            // the plan of recomputed products (chunked generators)
+            RecomputePlan& rp = get_recompute_plan(pb, R, fp64);
+            out[0] = rp.ch.KB + 100 * rp.ch.P2;
+            out[1] = rp.ch.RT;
+            out[2] = rp.nsplit;
+            out[3] = 0;
+            if (tuned_ms) *tuned_ms = 0;
+            return MSD_OK;
+        }
         ensure_generators(pb, fp64);
         MatvecPlan& plan = get_plan(pb, R, fp64, true);
         out[0] = plan.ch.KB + 100 * plan.ch.P2;
