@@ -262,14 +262,14 @@ def products_table(reps: int = 3, only: str = ""):
                 if prec == F32:
                     kinds += [f"tc{rc}" for rc in (16, 32, 64) if R % rc == 0]
                     if R % 8 == 0 and gen == "streamed":
-                        kinds.append("tcs")
+                        kinds += ["tcs", "tcsw"]
                 for kind in kinds:
                     os.environ["MSD_AUTOTUNE"] = "0" if kind == "model" else "1"
                     pb = msd.Problem(cl)
                     if gen == "recompute":
                         pb.set_generator_mode(msd.MSD_GEN_RECOMPUTE)
-                    if kind == "tcs":
-                        pb.set_tile(R, prec, 0, 8)
+                    if kind in ("tcs", "tcsw"):
+                        pb.set_tile(R, prec, 0 if kind == "tcs" else 1, 8)
                     elif kind.startswith("tc"):
                         pb.set_tile(R, prec, 0, int(kind[2:]))
                     dt = torch.complex128 if prec == F64 else torch.complex64
@@ -295,7 +295,7 @@ def products_table(reps: int = 3, only: str = ""):
                     gbs = by / (kms * 1e-3) / 1e9
                     if prec == F64:
                         bound, peak = "fp64 alu", FP64_PEAK_TFLOPS
-                    elif info["KB"] == 0:  # tensor cores (both kernels): 3 TF32 products per real multiply-add
+                    elif info["KB"] < 4:  # tensor cores (all kernels): 3 TF32 products per real multiply-add
                         bound, peak = "tf32 tensor (3x executed)", tf32_peak / 3.0
                     else:
                         bound, peak = "fp32 alu", FP32_PEAK_TFLOPS
@@ -373,7 +373,7 @@ def batched_timing(count: int = 16):
     pb.close()
 
 
-def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_rows: int = 2):
+def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_rows: int = 2, only_group: int = -1):
     """The batched workload as specified: 256 seeded clusters (M ~ U{50..800},
     unit radii, area fraction 0.2, gap 0.01, k ~ U[1, 8], N = ceil(k) + 8,
     Dirichlet/Neumann per disk ~ Bernoulli(1/2)), 32 incidences each,
@@ -396,6 +396,8 @@ def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_row
     tot_ms, worst_rel, worst_check, tot_iters = 0.0, 0.0, 0.0, 0
     rows_done = 0
     for gi, idx in enumerate(chunks):
+        if only_group >= 0 and gi != only_group:
+            continue
         sub = [cls[i] for i in idx]
         pb = msd.Problem(sub)
         betas = np.stack([betas_all] * len(sub))
@@ -651,6 +653,7 @@ def main():
                     help="solve all 256 batched clusters (32 incidences, mixed precision) and print JSON lines")
     ap.add_argument("--groups", type=int, default=8, help="with --batched-full: batched problems of similar M")
     ap.add_argument("--take", type=int, default=256, help="with --batched-full: the smallest TAKE clusters only")
+    ap.add_argument("--only-group", type=int, default=-1, help="with --batched-full: run this group only")
     ap.add_argument("--lattice-solve", type=int, default=0, metavar="R",
                     help="solve the 4000-disk lattice with R incidences (mixed precision) and print a JSON line")
     ap.add_argument("--nearfield", action="store_true",
@@ -673,7 +676,7 @@ def main():
     if args.lattice_solve:
         return lattice_solve(R=args.lattice_solve)
     if args.batched_full:
-        return batched_full(groups=args.groups, take=args.take)
+        return batched_full(groups=args.groups, take=args.take, only_group=args.only_group)
     if args.batched:
         return batched_timing()
     if args.products:

@@ -471,7 +471,13 @@ msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes
  *   RT 1; FP32: KB 4..9, RT in {1,2,4,8,16} dividing R, at most 16 warps
  *   per CTA, shared memory <= 227 KB; FP32 KB + 100 selects the same window
  *   with each complex multiply-add issued as two paired FP32 FMAs; KB = 0,
- *   RT in {16, 32, 64} dividing R: the tensor-core kernel).  KB reported by
+ *   RT in {16, 32, 64} dividing R: the tensor-core kernel that expands the
+ *   Toeplitz blocks in shared memory; RT = 8 with KB = 0 or 1, R a multiple
+ *   of 8: the shift-GEMM tensor-core kernel, one dense GEMM over the source
+ *   disks per shift d = n - m, with mode blocks of <= 8 two per CTA (KB = 0)
+ *   or one block of <= 16 modes per CTA (KB = 1); it serves the forward
+ *   products of the default rows with stored generators, every other product
+ *   of a problem pinned to it takes the cost-model shape).  KB reported by
  *   msd_plan_info uses the same encoding. */
 msd_status msd_plan_info(msd_problem* pb, int R, int precision, int* out, double* tuned_ms);
 msd_status msd_set_tile(msd_problem* pb, int R, int precision, int KB, int RT);

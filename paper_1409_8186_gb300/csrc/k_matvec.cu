@@ -490,10 +490,11 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bo
                 if (cnt < cap) out[cnt] = Choice{0, rc, 0, 0, rc};
                 ++cnt;
             }
-    if (!fp64 && allow_sh && tcs_supported(R, Nmax)) {
-        if (cnt < cap) out[cnt] = Choice{0, MSD_TCS_COLS, 0, 0, 0, 0, 1};
-        ++cnt;
-    }
+    if (!fp64 && allow_sh && tcs_supported(R, Nmax))
+        for (int sh = 1; sh <= 2; ++sh) {  // KB = sh - 1 in the encoding of msd_set_tile
+            if (cnt < cap) out[cnt] = Choice{sh - 1, MSD_TCS_COLS, 0, 0, 0, 0, sh};
+            ++cnt;
+        }
     return cnt < cap ? cnt : cap;
 }
 

@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issue
         const uint32_t id = idesc_tf32(128, 16 * mb);
+        const uint32_t d2off = mb > kMbMax ? 256u : 128u;  // D2 after D1 (N = 16 mb columns each)
         const uint32_t albo = 8192, sbo = 128, blbo = 2 * blk;
         long long ait = 0;
         int group = 0;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t bh = sdesc(sbase + boff, blbo, sbo), bl = sdesc(sbase + blk + boff, blbo, sbo);
                     const uint64_t grh = sdesc(a0, albo, sbo), grl = sdesc(a0 + 2048, albo, sbo);
                     const uint64_t gih = sdesc(a0 + 4096, albo, sbo), gil = sdesc(a0 + 6144, albo, sbo);
-                    const uint32_t d1 = tmem + (uint32_t)(b * 256), d2 = d1 + 128;
+                    const uint32_t d1 = tmem + (uint32_t)(b * 256), d2 = d1 + d2off;
                     const uint32_t acc = ((fresh >> b) & 1) ? 0u : 1u;
                     mma_tf32(d1, grh, bh, id, acc);
                     mma_tf32(d1, grh, bl, id, 1u);
@@ -311,7 +312,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (issued_mma) mma_commit(smem_u32(&mma_done));
     } else if (warp >= 2) {
         // ---------------- fold the accumulators into FP32 registers (round to nearest)
-        const int quarter = warp & 3, b = (warp - 2) >> 2;
+        // warp group g = (warp - 2) / 4 folds block g (two blocks of <= 8
+        // modes), or modes 8 g .. 8 g + 7 of the single block (<= 16 modes)
+        const int quarter = warp & 3, g4 = (warp - 2) >> 2;
+        const bool wide = mb > kMbMax;
+        const int b = wide ? 0 : g4;
+        const int u0 = wide ? kMbMax * g4 : 0;
+        const int ucnt = wide ? min(kMbMax, mb - u0) : mb;
+        const uint32_t d2off = wide ? 256u : 128u;
         const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
         float sr[kMbMax][kRC], si[kMbMax][kRC];
 #pragma unroll
@@ -326,10 +334,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                 for (int u = 0; u < kMbMax; ++u) {
-                    if (u < mb) {
+                    if (u < ucnt) {
                         float v1[16], v2[16];
-                        tmem_ld16(lane_addr + u * 16, v1);
-                        tmem_ld16(lane_addr + 128 + u * 16, v2);
+                        tmem_ld16(lane_addr + (u0 + u) * 16, v1);
+                        tmem_ld16(lane_addr + d2off + (u0 + u) * 16, v2);
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                         for (int r = 0; r < kRC; ++r) {
@@ -349,8 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float2* out = part + (long long)w.split * Ntot * R + rt * kRC;
 #pragma unroll
                 for (int u = 0; u < kMbMax; ++u) {
-                    const int m = m0 + b * mb + u;
-                    if (u < mb && m < n) {
+                    const int m = m0 + b * mb + u0 + u;
+                    if (u < ucnt && m < n) {
                         float2* o = out + (c.row_off + (long long)p * n + m) * R;
 #pragma unroll
                         for (int r = 0; r < kRC; r += 2)
@@ -507,7 +515,13 @@ bool tcs_supported(int R, int Nmax) { return R % kRC == 0 && tcs_stages(Nmax) >=
 // two per CTA (TMEM holds 2 blocks x (D1, D2) x 128 columns).  The choice
 // minimises the streamed A stages per CTA group, n + span - 1 each, with
 // the MMA work of padded modes as a tie-break.
-void tcs_mode_blocks(int n, int* mb_out, int* nblocks_out) {
+void tcs_mode_blocks(int n, int* mb_out, int* nblocks_out, bool wide) {
+    if (wide) {  // single blocks of at most 16 modes, balanced
+        const int nb = (n + 2 * kMbMax - 1) / (2 * kMbMax);
+        *mb_out = (n + nb - 1) / nb;
+        *nblocks_out = nb;
+        return;
+    }
     double best = 1e300;
     for (int mb = 4; mb <= kMbMax; ++mb) {
         const int nb = (n + mb - 1) / mb;

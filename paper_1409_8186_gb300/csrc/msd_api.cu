@@ -420,11 +420,13 @@ void tile_starts(const MsdConfig& c, int P0, int P1, const MatvecChoice& ch, std
 // ceil(...) times the balance of the largest source range against the mean.
 void build_work_tcs(msd_problem* pb, MatvecPlan& plan, int R) {
     const int rtiles = R / MSD_TCS_COLS;
+    const bool wide = plan.ch.SH == 2;
+    const int per_cta = wide ? 1 : 2;  // mode blocks per CTA
     long long units = 0;
     for (auto& c : pb->cfg) {
         int mb = 8, nb = 1;
-        tcs_mode_blocks(c.n, &mb, &nb);
-        units += (long long)((c.M + 127) / 128) * ((nb + 1) / 2) * rtiles;
+        tcs_mode_blocks(c.n, &mb, &nb, wide);
+        units += (long long)((c.M + 127) / 128) * ((nb + per_cta - 1) / per_cta) * rtiles;
     }
     int sms = 0, dev = 0;
     CK(cudaGetDevice(&dev));
@@ -451,11 +453,11 @@ void build_work_tcs(msd_problem* pb, MatvecPlan& plan, int R) {
     for (int ci = 0; ci < pb->C; ++ci) {
         const MsdConfig& c = pb->cfg[ci];
         int mb = 8, nb = 1;
-        tcs_mode_blocks(c.n, &mb, &nb);
+        tcs_mode_blocks(c.n, &mb, &nb, wide);
         const int nqc = c.Mq / 8;
         for (int p0 = 0; p0 < c.M; p0 += 128)
-            for (int b0 = 0; b0 < nb; b0 += 2) {
-                const int nmb = std::min(2, nb - b0);
+            for (int b0 = 0; b0 < nb; b0 += per_cta) {
+                const int nmb = std::min(per_cta, nb - b0);
                 for (int sp = 0; sp < ns; ++sp) {
                     const int qc0 = (int)((long long)nqc * sp / ns), qc1 = (int)((long long)nqc * (sp + 1) / ns);
                     MatvecWork w;

@@ -98,7 +98,8 @@ struct MatvecChoice {
     int KB, RT, RB, I;
     int TC;  // > 0: tensor-core kernel with TC columns per CTA (KB, RB, I unused; RT = TC)
     int P2;  // FP32: 1 = complex multiply-adds as paired FMAs (fma.rn.f32x2), 0 = four FFMAs
-    int SH;  // 1: the shift-GEMM tensor-core kernel (FP32, RT = MSD_TCS_COLS columns per CTA)
+    int SH;  // shift-GEMM tensor-core kernel (FP32, RT = MSD_TCS_COLS columns per CTA): 1 = mode
+             // blocks of <= 8 two per CTA, 2 = one block of <= 16 modes per CTA; 0 = not used
     int ONE;  // FP64: 1 = one shared-memory stage (two would exceed 227 KB at this truncation order)
 };
 #define MSD_TCS_COLS 8
@@ -123,7 +124,9 @@ int tc_status_and_clear();
 // modes per block, blocks)
 size_t tcs_smem_bytes(int Nmax);
 bool tcs_supported(int R, int Nmax);
-void tcs_mode_blocks(int n, int* mb, int* nblocks);
+// blocks of <= 8 modes grouped two per CTA (N = 16 mb <= 128 per MMA), or
+// wide: one block of <= 16 modes per CTA (N <= 256 per MMA)
+void tcs_mode_blocks(int n, int* mb, int* nblocks, bool wide);
 void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float* GT,
                    const float* XT, float2* part, long long Ntot, int R, cudaStream_t s);
 void launch_tcs_build_gt(const MsdConfig* d_cfg, int C, const long long* d_blk_off, long long nblocks,

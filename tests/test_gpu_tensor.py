@@ -104,17 +104,19 @@ def test_tc_autotuner_candidates(msd):
 # in their A-operand order, the sources as a slab, one GEMM per shift d = n - m).
 
 @pytest.mark.parametrize("R", [8, 24, 64])
-def test_shift_gemm_product_rand70(msd, R):
-    """rand70 (n = 25: mode blocks grouped in two CTAs, one ragged), M = 70
-    (one target tile, ragged at 70; 9 K-steps of 8 sources, ragged at 70;
-    three folds of the accumulators), mixed Dirichlet/Neumann."""
+@pytest.mark.parametrize("KB", [0, 1])
+def test_shift_gemm_product_rand70(msd, R, KB):
+    """rand70 (n = 25: mode blocks of <= 8 grouped two per CTA (KB = 0), or
+    blocks of <= 16 one per CTA (KB = 1); M = 70 (one target tile, ragged at
+    70; 9 K-steps of 8 sources, ragged at 70; three folds of the
+    accumulators), mixed Dirichlet/Neumann."""
     cl = rand70()
     x = rand_x(cl.ntot, R, seed=R)
     ref = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N) @ x.astype(np.complex128)
     pb = msd.Problem(cl)
-    pb.set_tile(R, msd.MSD_FP32, 0, 8)
+    pb.set_tile(R, msd.MSD_FP32, KB, 8)
     info, _ = pb.plan_info(R, msd.MSD_FP32)
-    assert info["RT"] == 8 and info["KB"] == 0
+    assert info["RT"] == 8 and info["KB"] == KB
     y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
     assert relerr(y, ref) < 1e-5
 
@@ -130,20 +132,25 @@ def test_shift_gemm_product_batched_and_two_target_tiles(msd):
     R = 16
     pb = msd.Problem(cls)
     pb.set_tile(R, msd.MSD_FP32, 0, 8)
+    pw = msd.Problem(cls)
+    pw.set_tile(R, msd.MSD_FP32, 1, 8)
     for it in range(2):
         x = rand_x(pb.ntot, R, seed=11 + it)
         y = pb.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
+        yw = pw.matvec(torch.from_numpy(x).cuda(), msd.MSD_FP32).cpu().numpy()
         off = 0
         for cl in cls:
             A = O_.preconditioned_dense(cl.centres, cl.radii, cl.bc, cl.k, cl.N)
             ref = A @ x[off:off + cl.ntot].astype(np.complex128)
             assert relerr(y[off:off + cl.ntot], ref) < 1e-5, (it, cl.name)
+            assert relerr(yw[off:off + cl.ntot], ref) < 1e-5, (it, cl.name, "wide")
             off += cl.ntot
         if it == 0:  # move every disk by the same small offset and rebuild
             for cl in cls:
                 cl.centres = cl.centres + np.array([0.05, -0.03])
             cen = np.concatenate([cl.centres for cl in cls])
             pb.update_geometry(centres=cen)
+            pw.update_geometry(centres=cen)
 
 
 def test_shift_gemm_mixed_solve_and_adjoint_fallback(msd):
