@@ -15,7 +15,7 @@
 //    copy.
 //  * B (N = 16 mb rows for a block of mb modes): the 8 columns of Xs for
 //    modes j = m + d, real and imaginary rows, hi and lo.  The sources of one
-//    K-step are staged once as a "slab" of all n modes (plus 7 zero modes on
+//    K-step are staged once as a "slab" of all n modes (plus 15 zero modes on
 //    either side, which give the zeros outside 0 <= j < n); the B operand of
 //    shift d is the slab seen from mode m0 + d, i.e. the same bytes with a
 //    start address 256 bytes further per shift.
@@ -47,7 +47,8 @@ __device__ int g_tcs_status;  // bit 0: a wait of the shift-GEMM kernel expired
 namespace {
 
 constexpr int kRC = MSD_TCS_COLS;  // columns per CTA (8)
-constexpr int kPad = 7;             // zero modes on either side of the slab
+constexpr int kPad = 15;            // zero modes on either side of the slab: a B operand of a block
+                                    // of mb <= 16 modes starts at most mb - 1 modes outside 0..n-1
 constexpr int kStagesMax = 8;       // A ring: as many 16 KB stages as fit next to the slab, 3..8
 constexpr int kAStage = 16384;      // bytes of one A stage (Gr hi/lo, Gi hi/lo, 2 x 4 sources)
 constexpr int kThreads = 320;
@@ -285,7 +286,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int mb0 = m0 + b * mb;
                     const int mb1 = min(n, mb0 + mb) - 1;
                     if (d < -mb1 || d > n - 1 - mb0) continue;  // no mode of the block meets a source mode
-                    const uint32_t boff = (uint32_t)(mb0 + d + kPad) * 256u;
+                    const int jb = mb0 + d + kPad;  // first slab mode of the B operand
+                    if (jb < 0 || jb + mb > n + 2 * kPad) {  // outside the slab block: never by construction
+                        *abort_v = 1;
+                        continue;
+                    }
+                    const uint32_t boff = (uint32_t)jb * 256u;
                     const uint64_t bh = sdesc(sbase + boff, blbo, sbo), bl = sdesc(sbase + blk + boff, blbo, sbo);
                     const uint64_t grh = sdesc(a0, albo, sbo), grl = sdesc(a0 + 2048, albo, sbo);
                     const uint64_t gih = sdesc(a0 + 4096, albo, sbo), gil = sdesc(a0 + 6144, albo, sbo);
