@@ -54,6 +54,10 @@ constexpr int kAStage = 16384;      // bytes of one A stage (Gr hi/lo, Gi hi/lo,
 constexpr int kThreads = 320;
 constexpr int kFoldQc = 4;          // K-steps of 8 sources between folds into registers
 constexpr int kMbMax = 8;           // modes per block (N = 16 mb <= 128)
+// Wide blocks: at most 13 modes (MMA N = 16 mb <= 208).  An autotuner run
+// whose wide blocks had 16 modes (N = 256) on the lattice ended in an
+// illegal-instruction fault; N <= 208 ran correctly, so wider is not offered.
+constexpr int kMbWide = 13;
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 constexpr long long kTestWaitCycles = 20000;     // msd_test_expire_waits
 
@@ -522,8 +526,8 @@ bool tcs_supported(int R, int Nmax) { return R % kRC == 0 && tcs_stages(Nmax) >=
 // minimises the streamed A stages per CTA group, n + span - 1 each, with
 // the MMA work of padded modes as a tie-break.
 void tcs_mode_blocks(int n, int* mb_out, int* nblocks_out, bool wide) {
-    if (wide) {  // single blocks of at most 16 modes, balanced
-        const int nb = (n + 2 * kMbMax - 1) / (2 * kMbMax);
+    if (wide) {  // single blocks of at most kMbWide modes, balanced
+        const int nb = (n + kMbWide - 1) / kMbWide;
         *mb_out = (n + nb - 1) / nb;
         *nblocks_out = nb;
         return;

@@ -454,6 +454,8 @@ void build_work_tcs(msd_problem* pb, MatvecPlan& plan, int R) {
         const MsdConfig& c = pb->cfg[ci];
         int mb = 8, nb = 1;
         tcs_mode_blocks(c.n, &mb, &nb, wide);
+        if (16 * mb > 208 || mb < 1 || (!wide && mb > 8))
+            fail(MSD_ERR_ARG, "shift-GEMM product: mode block outside the validated MMA shapes");
         const int nqc = c.Mq / 8;
         for (int p0 = 0; p0 < c.M; p0 += 128)
             for (int b0 = 0; b0 < nb; b0 += per_cta) {
