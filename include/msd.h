@@ -321,6 +321,22 @@ msd_status msd_solve_penetrable(msd_problem* pb, int R, const double* betas_host
 msd_status msd_solve_penetrable_pointsources(msd_problem* pb, int R, const double* sources, const msd_opts* opts,
                                              void* rho_plus, void* rho_minus, msd_stats* stats_host);
 
+/* The interior field of penetrable obstacles (section 7, Example II):
+ * u-(x) = L- rho- (x) for points x inside a disk of configuration `config`,
+ * the single layers of every circle at the interior wavenumber k-; for x
+ * inside disk p the circle of p takes its interior expansion
+ * (i pi a_p/2) H_m(k- a_p) J_m(k- r_p) e^{i m theta_p} rho-^p_m / sqrt(2 pi a_p),
+ * the other circles their exterior one with H_m(k- r_q) (Prop. 4.3 at k-).
+ * With u+ from msd_nearfield(rho_plus) and the incident wave, this gives the
+ * total field everywhere (u+ + u_inc outside, u- inside).
+ *   rho_minus  host or device, complex128 [N_tot][R] (msd_solve_penetrable)
+ *   points     host or device, double [P][2]
+ *   u_out      host or device, complex128 [P][R]; 0 at points outside every disk
+ * Needs msd_set_penetrable.  FP64.  Synchronises the stream when u_out is
+ * host memory. */
+msd_status msd_penetrable_interior_field(msd_problem* pb, int config, const void* rho_minus, int R, int64_t P,
+                                         const double* points, void* u_out);
+
 /* Integral-equation formulation (sections 3, 4.2, 5): replaces the default
  * rows (EFIE L rho = -U on sound-soft disks, (-I/2 + N) rho = -dU on
  * sound-hard ones, u = L rho) by linear combinations of the identity and

@@ -448,7 +448,94 @@ __global__ void __launch_bounds__(128) k_nearfield(const MsdConfig* __restrict__
     }
 }
 
+// Interior field of penetrable obstacles (section 7, Example II):
+// u-(x) = L- rho- at points x inside the disks, the single layers of every
+// circle at the interior wavenumber k-.  For x inside disk p the own circle
+// takes the interior expansion (Graf's theorem with x and y exchanged),
+//   V^p_m J_m(k- r_p) e^{i m theta_p},   V^p_m = (i pi a_p/2) H_m(k- a_p) rho-^p_m / sqrt(2 pi a_p),
+// the other circles the exterior one, W^q_m H_m(k- r_q) e^{i m theta_q} with
+// W^q_m = (i pi a_q/2) J_m(k- a_q) rho-^q_m / sqrt(2 pi a_q).  Points outside
+// every disk get 0.  One thread per point and column block, FP64.
+template <int RC>
+__global__ void __launch_bounds__(128) k_nearfield_inside(const MsdConfig* __restrict__ cfg, int ci, double km,
+                                                          const double2* __restrict__ centre,
+                                                          const double* __restrict__ radius,
+                                                          const double2* __restrict__ W, const double2* __restrict__ V,
+                                                          int R, int r0, int ncol, const double2* __restrict__ pts,
+                                                          long long P, double2* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P) return;
+    const MsdConfig c = cfg[ci];
+    const int N = c.N, n = c.n;
+    const double2 x = pts[t];
+    int own = -1;
+    for (int p = 0; p < c.M; ++p) {
+        const double2 O = centre[c.disk_off + p];
+        if (hypot(x.x - O.x, x.y - O.y) <= radius[c.disk_off + p]) {
+            own = p;
+            break;
+        }
+    }
+    double2 u[RC];
+#pragma unroll
+    for (int j = 0; j < RC; ++j) u[j] = make_double2(0.0, 0.0);
+    if (own >= 0) {
+        for (int q = 0; q < c.M; ++q) {
+            const double2 O = centre[c.disk_off + q];
+            const double dx = x.x - O.x, dy = x.y - O.y;
+            const double r = hypot(dx, dy);
+            const double kr = km * r;
+            const bool self = q == own;
+            const double2* w = (self ? V : W) + (c.row_off + (long long)q * n + N) * R + r0;  // mode m = 0
+            double J[MAXL], Y[MAXL];
+            bessel_jy(kr > 1e-300 ? kr : 1e-300, N, J, Y);
+            // angle of x - O_q (any angle at the centre: only m = 0 survives there)
+            const double2 e1 = r > 0.0 ? make_double2(dx / r, dy / r) : make_double2(1.0, 0.0);
+            double2 e = make_double2(1.0, 0.0);
+            for (int m = 0; m <= N; ++m) {
+                const double2 Z = self ? make_double2(J[m], 0.0) : make_double2(J[m], Y[m]);
+                const double2 zp = cmul(Z, e);
+                double2 zm = cmul(Z, cconj(e));
+                if (m & 1) zm = make_double2(-zm.x, -zm.y);  // Z_{-m} = (-1)^m Z_m
+#pragma unroll
+                for (int j = 0; j < RC; ++j) {
+                    if (j >= ncol) break;
+                    u[j] = cadd(u[j], cmul(w[(long long)m * R + j], zp));
+                    if (m > 0) u[j] = cadd(u[j], cmul(w[-(long long)m * R + j], zm));
+                }
+                e = cmul(e, e1);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+        if (j >= ncol) break;
+        out[t * R + r0 + j] = u[j];
+    }
+}
+
 }  // namespace
+
+void launch_nearfield_inside(const MsdConfig* d_cfg, int ci, const MsdConfig& h_cfg, double km, const double2* d_centre,
+                             const double* d_radius, const double2* Jm, const double2* Hm, const double2* rho_minus,
+                             int R, double2* W, double2* V, const double2* d_pts, long long P, double2* out,
+                             cudaStream_t s) {
+    const long long nw = (long long)h_cfg.M * h_cfg.n * R;
+    k_nf_weights<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d_cfg, ci, d_radius, Jm, rho_minus, R, W);
+    k_nf_weights<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d_cfg, ci, d_radius, Hm, rho_minus, R, V);
+    const unsigned blocks = (unsigned)((P + 127) / 128);
+    for (int r0 = 0; r0 < R; r0 += 4) {
+        const int nc = R - r0 < 4 ? R - r0 : 4;
+        if (nc <= 1)
+            k_nearfield_inside<1><<<blocks, 128, 0, s>>>(d_cfg, ci, km, d_centre, d_radius, W, V, R, r0, nc, d_pts, P,
+                                                         out);
+        else
+            k_nearfield_inside<4><<<blocks, 128, 0, s>>>(d_cfg, ci, km, d_centre, d_radius, W, V, R, r0, nc, d_pts, P,
+                                                         out);
+        g_msd_launches += 1;
+    }
+    g_msd_launches += 2;
+}
 
 void launch_generator_blocks(const MsdConfig* d_cfg, const GenBlock* d_blocks, int nblocks, long long nitems,
                              const double2* d_centre, double2* G64, float2* G32, int* d_flags, cudaStream_t s,

@@ -2157,6 +2157,26 @@ msd_status msd_set_formulation(msd_problem* pb, const double* op_weights, const 
     });
 }
 
+msd_status msd_penetrable_interior_field(msd_problem* pb, int config, const void* rho_minus, int R, int64_t P,
+                                         const double* points, void* u_out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || !pb->pen_minus || !rho_minus || R <= 0 || P <= 0 || !points || !u_out || config < 0 ||
+            config >= pb->C)
+            fail(MSD_ERR_ARG, "msd_penetrable_interior_field: bad argument (msd_set_penetrable first)");
+        msd_problem* pm = pb->pen_minus;
+        const double2* d_rho = (const double2*)stage_in(pb, pb->nfbuf[0], rho_minus, (size_t)pb->Ntot * R * 16);
+        const double2* d_pts = (const double2*)stage_in(pb, pb->nfbuf[1], points, (size_t)P * 16);
+        double2* W = (double2*)pb->nfbuf[2].get((size_t)pb->Ntot * R * 2 * 16);
+        OutStage o(pb, pb->nfbuf[3], u_out, (size_t)P * R * 16);
+        launch_nearfield_inside(pm->d_cfg, config, pm->cfg[config], pm->cfg[config].k, pm->d_centre, pm->d_radius,
+                                pm->d_J, pm->d_H, d_rho, R, W, W + (size_t)pb->Ntot * R, d_pts, P, (double2*)o.dev,
+                                pb->stream);
+        CK_LAUNCH();
+        o.finish();
+        return MSD_OK;
+    });
+}
+
 }  // extern "C"
 
 namespace {

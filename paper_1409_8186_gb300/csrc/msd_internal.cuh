@@ -299,6 +299,15 @@ void launch_nearfield(const MsdConfig* d_cfg, int ci, const MsdConfig& h_cfg, co
                       const double* d_radius, const double2* J, const double2* rho, int R, double2* W,
                       const double2* d_pts, long long P, double2* out, cudaStream_t s);
 
+// Interior field of penetrable obstacles: u- = L- rho- at points inside the
+// disks of configuration ci (0 outside), k- = km, Jm / Hm the Bessel
+// diagonals at k- (the internal problem's J and H), W, V work buffers of
+// N_tot * R complex128 each.
+void launch_nearfield_inside(const MsdConfig* d_cfg, int ci, const MsdConfig& h_cfg, double km, const double2* d_centre,
+                             const double* d_radius, const double2* Jm, const double2* Hm, const double2* rho_minus,
+                             int R, double2* W, double2* V, const double2* d_pts, long long P, double2* out,
+                             cudaStream_t s);
+
 // K5': preconditioned point-source right-hand sides, sources [C][R] (x, y).
 void launch_rhs_pointsource(const MsdConfig* d_cfg, int Mtot, const int* d_disk_cfg, const double2* d_centre,
                             const double* d_radius, const double2* rhs_scale, int R, const double2* d_src,

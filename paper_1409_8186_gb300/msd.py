@@ -90,6 +90,7 @@ def _load():
         "msd_kernel_launches": (ctypes.c_int64, []),
         "msd_test_expire_waits": (V, [I]),
         "msd_set_truncation": (I, [P, P]),
+        "msd_penetrable_interior_field": (I, [P, I, P, I, ctypes.c_int64, P, P]),
         "msd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -106,7 +107,7 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
             "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_formulation_kind",
-            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_truncation", "msd_set_penetrable",
+            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_truncation", "msd_penetrable_interior_field", "msd_set_penetrable",
             "msd_penetrable_matvec", "msd_solve_penetrable", "msd_solve_penetrable_pointsources",
             "msd_last_error")
 
@@ -366,6 +367,11 @@ def msd_kernel_launches() -> int:
     return int(_lib.msd_kernel_launches())
 
 
+def msd_penetrable_interior_field(h, config: int, rho_minus, R: int, points, u_out) -> None:
+    pts = points if hasattr(points, "data_ptr") else np.ascontiguousarray(points, dtype=np.float64)
+    _check(_lib.msd_penetrable_interior_field(h, config, _ptr(rho_minus), R, len(pts), _ptr(pts), _ptr(u_out)))
+
+
 def msd_set_truncation(h, Np) -> None:
     """Per-disk truncation orders N_p (host int [disk_off[C]]); None restores N."""
     if Np is None:
@@ -527,6 +533,16 @@ class Problem:
         pts = np.ascontiguousarray(points, dtype=np.float64)
         u = torch.empty((pts.shape[0], R), dtype=torch.complex128, device="cuda") if out is None else out
         msd_nearfield(self.handle, config, rho, R, pts, u)
+        return u
+
+    def interior_field(self, rho_minus, points, config: int = 0, out=None):
+        """Penetrable obstacles: u- = L- rho- at points [P, 2] inside the disks
+        of `config` (complex128 [P, R] on the device; 0 outside every disk)."""
+        import torch
+        R = rho_minus.shape[1]
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        u = torch.empty((pts.shape[0], R), dtype=torch.complex128, device="cuda") if out is None else out
+        msd_penetrable_interior_field(self.handle, config, rho_minus, R, pts, u)
         return u
 
     def dort(self, n_alpha: int, tol=1e-12, precision=MSD_FP64, restart=0, maxit=3000, want_F=True,

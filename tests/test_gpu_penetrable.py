@@ -142,3 +142,47 @@ def test_point_source_solve(msd):
     got = np.concatenate([rp.cpu().numpy(), rm.cpu().numpy()])
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
     pb.close()
+
+
+def test_interior_field_and_transmission(msd):
+    """The interior field u- = L- rho- (msd_penetrable_interior_field) at
+    points inside every disk against the oracle's single_layer_potential_inside
+    on the oracle's densities (1e-10 of the largest value), and the
+    transmission condition u+ + u_inc = u- across each circle: the GPU's
+    exterior near field plus the incident wave just outside, and its interior
+    field just inside, agree to the truncation level of the solve (the
+    oracle's own pointwise residual on this case at N = 12 is 2.2e-6)."""
+    cl, km, mu = cases()[0]
+    betas = [0.4]
+    rp_ref, rm_ref = O_.solve_penetrable(cl.centres, cl.radii, cl.k, km, mu, cl.N, betas)
+    pb = msd.Problem(cl)
+    pb.set_penetrable(km, mu)
+    rng = np.random.default_rng(7)
+    pts, owner = [], []
+    for p in range(cl.M):
+        r = cl.radii[p] * np.sqrt(rng.uniform(0.0, 0.95, 6))
+        t = rng.uniform(0, 2 * np.pi, 6)
+        pts.append(cl.centres[p] + np.stack([r * np.cos(t), r * np.sin(t)], 1))
+        owner += [p] * 6
+    pts = np.concatenate(pts + [np.array([[40.0, 40.0]])])   # last point outside every disk
+    u = pb.interior_field(torch.from_numpy(rm_ref).cuda(), pts).cpu().numpy()
+    ref = np.concatenate([O_.single_layer_potential_inside(cl.centres, cl.radii, km, cl.N, rm_ref,
+                                                           pts[i:i + 1], owner[i]) for i in range(len(owner))])
+    assert np.abs(u[:-1] - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.abs(u[-1]).max() == 0.0
+    # transmission condition from the GPU's own solve
+    res_p = torch.empty((cl.ntot, 1), dtype=torch.complex128, device="cuda")
+    res_m = torch.empty_like(res_p)
+    st = msd.msd_solve_penetrable(pb.handle, 1, np.array([betas]), msd.msd_opts(1e-12, 0, 3000, 0, 0.0, 0, 0),
+                                  res_p, res_m)
+    assert st == msd.MSD_OK
+    th = np.linspace(0.0, 2 * np.pi, 8, endpoint=False)
+    for p in range(cl.M):
+        e = np.stack([np.cos(th), np.sin(th)], 1)
+        out_pts = cl.centres[p] + (cl.radii[p] * (1 + 1e-9)) * e
+        in_pts = cl.centres[p] + (cl.radii[p] * (1 - 1e-9)) * e
+        us = pb.nearfield(res_p, out_pts).cpu().numpy()[:, 0]
+        uinc = np.exp(1j * cl.k * (np.cos(betas[0]) * out_pts[:, 0] + np.sin(betas[0]) * out_pts[:, 1]))
+        ui = pb.interior_field(res_m, in_pts).cpu().numpy()[:, 0]
+        assert np.abs(us + uinc - ui).max() <= 1e-5 * np.abs(uinc).max(), p
+    pb.close()
