@@ -239,53 +239,72 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         if (nqc > 0) issue_slab(0);
         const int next_at = min(nd - 1, kStages);
+        // ring position of the next A stage and the parity of its previous use
+        int s = 0;
+        uint32_t ph = 1;  // parity of the phase to wait for before reuse (first lap: none)
+        bool lap1 = true;
+        const float* gq = gt + (long long)(dlo + 2 * N) * (c.Mq / 4) * 2048;
+        const long long dstep = (long long)(c.Mq / 4) * 2048;
         for (int qi = 0; qi < nqc; ++qi) {
-            const int qc = qc0 + qi;
-            for (int d = dlo; d <= dhi; ++d, ++ait) {
+            const float* gd = gq + (long long)(2 * (qc0 + qi)) * 2048;
+            for (int t = 0; t < nd; ++t, gd += dstep) {
                 // the next slab once kStages A stages of this K-step are issued:
                 // the MMAs of K-step qi - 1 are then complete
-                if (d - dlo == next_at && qi + 1 < nqc) issue_slab(qi + 1);
-                const int s = (int)(ait % kStages);
-                if (ait >= kStages) {
-                    const uint32_t ph = (uint32_t)((ait / kStages - 1) & 1);
+                if (t == next_at && qi + 1 < nqc) issue_slab(qi + 1);
+                if (!lap1) {
                     if (!*abort_v && !mbar_wait(smem_u32(&a_empty[s]), ph)) *abort_v = 1;
                     mbar_wait(smem_u32(&a_full[s]), ph);
                 }
                 const uint32_t abar = smem_u32(&a_full[s]);
                 mbar_expect_tx(abar, kAStage);
-                bulk_g2s(smem_u32(A + s * kAStage), gt + ((long long)(d + 2 * N) * (c.Mq / 4) + 2 * qc) * 2048,
-                         kAStage, abar);
+                bulk_g2s(smem_u32(A + s * kAStage), gd, kAStage, abar);
+                ++ait;
+                if (++s == kStages) {
+                    s = 0;
+                    ph ^= 1;
+                    if (lap1) {
+                        lap1 = false;
+                        ph = 0;
+                    }
+                }
             }
         }
         // every copy of this CTA has landed before it exits
-        for (int s = 0; s < kStages; ++s)
-            if (ait > s) mbar_wait(smem_u32(&a_full[s]), (uint32_t)(((ait - 1 - s) / kStages) & 1));
+        for (int s2 = 0; s2 < kStages; ++s2)
+            if (ait > s2) mbar_wait(smem_u32(&a_full[s2]), (uint32_t)(((ait - 1 - s2) / kStages) & 1));
         for (int sb = 0; sb < 2; ++sb)
             if (nqc > sb) mbar_wait(smem_u32(&s_full[sb]), (uint32_t)(((nqc - 1 - sb) >> 1) & 1));
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issue
+        // Descriptors are linear in the start address (field = address / 16),
+        // so the per-stage and per-shift ones are base descriptors plus
+        // offsets; stage and phase advance incrementally.
         const uint32_t id = idesc_tf32(128, 16 * mb);
         const uint32_t d2off = mb > kMbMax ? 256u : 128u;  // D2 after D1 (N = 16 mb columns each)
-        const uint32_t albo = 8192, sbo = 128, blbo = 2 * blk;
-        long long ait = 0;
+        const uint32_t sbo = 128;
+        const uint64_t adesc0 = sdesc(smem_u32(A), 8192, sbo);
+        const uint64_t bdesc0[2] = {sdesc(smem_u32(slab), 2 * blk, sbo), sdesc(smem_u32(slab + buf), 2 * blk, sbo)};
+        const uint64_t blo = (uint64_t)(blk >> 4);
         int group = 0;
         int fresh = 3;  // bit b: the next MMA into block b's accumulators overwrites them
         bool first_wait = true;
+        int s = 0;
+        uint32_t ph = 0;  // parity of the stage's current fill
         for (int qi = 0; qi < nqc; ++qi) {
             const int sb = qi & 1;
             if (!*abort_v && !mbar_wait(smem_u32(&s_full[sb]), (qi >> 1) & 1)) *abort_v = 1;
-            const uint32_t sbase = smem_u32(slab + sb * buf);
-            for (int d = dlo; d <= dhi; ++d, ++ait) {
-                const int s = (int)(ait % kStages);
-                bool ok = *abort_v ? true : mbar_wait(smem_u32(&a_full[s]), (uint32_t)((ait / kStages) & 1));
+            const uint64_t bd = bdesc0[sb];
+            const bool fold_wait = qi % kFoldQc == 0 && group > 0;
+            for (int d = dlo; d <= dhi; ++d) {
+                bool ok = *abort_v ? true : mbar_wait(smem_u32(&a_full[s]), ph);
                 if (expire_test && first_wait) ok = wait_unset_flag(&never_sh) && ok;
                 first_wait = false;
                 if (!ok) *abort_v = 1;
-                if (qi % kFoldQc == 0 && d == dlo && group > 0 && !*abort_v &&
-                    !mbar_wait(smem_u32(&acc_empty), (uint32_t)((group - 1) & 1)))
+                if (fold_wait && d == dlo && !*abort_v && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((group - 1) & 1)))
                     *abort_v = 1;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t a0 = smem_u32(A + s * kAStage);
+                const uint64_t grh = adesc0 + (uint64_t)(s * (kAStage >> 4));
+                const uint64_t grl = grh + 128, gih = grh + 256, gil = grh + 384;  // + 2, 4, 6 KB
                 for (int b = 0; b < nmb; ++b) {
                     const int mb0 = m0 + b * mb;
                     const int mb1 = min(n, mb0 + mb) - 1;
@@ -295,10 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         *abort_v = 1;
                         continue;
                     }
-                    const uint32_t boff = (uint32_t)jb * 256u;
-                    const uint64_t bh = sdesc(sbase + boff, blbo, sbo), bl = sdesc(sbase + blk + boff, blbo, sbo);
-                    const uint64_t grh = sdesc(a0, albo, sbo), grl = sdesc(a0 + 2048, albo, sbo);
-                    const uint64_t gih = sdesc(a0 + 4096, albo, sbo), gil = sdesc(a0 + 6144, albo, sbo);
+                    const uint64_t bh = bd + (uint64_t)(jb * 16), bl = bh + blo;  // jb * 256 bytes
                     const uint32_t d1 = tmem + (uint32_t)(b * 256), d2 = d1 + d2off;
                     const uint32_t acc = ((fresh >> b) & 1) ? 0u : 1u;
                     mma_tf32(d1, grh, bh, id, acc);
@@ -311,6 +327,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     issued_mma = 1;
                 }
                 mma_commit(smem_u32(&a_empty[s]));
+                if (++s == kStages) {
+                    s = 0;
+                    ph ^= 1;
+                }
             }
             mma_commit(smem_u32(&s_empty[sb]));
             if ((qi + 1) % kFoldQc == 0 || qi == nqc - 1) {
