@@ -430,6 +430,36 @@ msd_status msd_dort(msd_problem* pb, int n_alpha, const msd_opts* opts, void* F_
  * Synchronises the stream. */
 msd_status msd_dort_eigen(msd_problem* pb, int n_alpha, const void* F, void* T_out, void* eig_out);
 
+/* Eigenvectors of the time-reversal matrix (section 7: the eigenvectors of
+ * T = conj(F)^T F for its significant eigenvalues are the mirror signals
+ * that focus on one obstacle each, see msd_herglotz_wave): for each of the
+ * problem's C configurations, T and its eigenvalues as msd_dort_eigen, then
+ * the eigenvectors of the K largest eigenvalues: inverse iteration on the
+ * real tridiagonal form of T (orthogonalised within clusters of eigenvalues
+ * closer than 1e-3 of the norm bound), mapped back through the phase
+ * similarity and the Householder reflections of the reduction.
+ *   F        host or device complex128 [C][n_alpha][n_alpha]
+ *   K        1..n_alpha eigenvectors (largest eigenvalues first)
+ *   eig_out  NULL or host/device double [C][n_alpha]
+ *   vec_out  host or device complex128 [C][K][n_alpha]: unit 2-norm, the
+ *            entry of largest modulus real and positive (an eigenvector is
+ *            fixed up to a phase; vectors of a multiple eigenvalue span its
+ *            eigenspace)
+ * Synchronises the stream. */
+msd_status msd_dort_eigenvectors(msd_problem* pb, int n_alpha, const void* F, int K, void* eig_out, void* vec_out);
+
+/* The discrete Herglotz wave of section 7 emitted by the mirror of n_alpha
+ * transducers at the angles alpha_j = 2 pi j / n_alpha, for K parameter
+ * vectors g (for instance eigenvectors of the time-reversal matrix), at
+ * the wavenumber k of configuration `config`:
+ *   u[p][r] = (2 pi / n_alpha) sum_j g[r][j] exp(i k (x_p cos alpha_j + y_p sin alpha_j)).
+ *   g       host or device complex128 [K][n_alpha]
+ *   points  host or device double [P][2]
+ *   u_out   host or device complex128 [P][K]
+ * FP64.  Synchronises the stream when u_out is host memory. */
+msd_status msd_herglotz_wave(msd_problem* pb, int config, int n_alpha, int K, const void* g, int64_t P,
+                             const double* points, void* u_out);
+
 /* Per-disk truncation orders (section 5: disk p keeps the modes
  * -N_p..N_p, the blocks of the truncated system are (2N_p+1) x (2N_q+1);
  * eq. (Np) gives N_p from k a_p).  Vectors keep the layout [N_tot][R] of the

@@ -128,8 +128,8 @@ constexpr int kTdBatch = 8;  // row entries per lane whose loads are issued toge
 // every configuration, w, and tau and ||x_k||^2 per configuration.
 __global__ void __launch_bounds__(kTdThreads)
     k_dort_tridiag(int C, int n, double2* __restrict__ Aall, double2* __restrict__ pbuf,
-                   double2* __restrict__ colbuf, double* __restrict__ e_all, unsigned* __restrict__ bar,
-                   int* __restrict__ err, int expire_test) {
+                   double2* __restrict__ colbuf, double* __restrict__ e_all, double* __restrict__ tau_all,
+                   double2* __restrict__ ph_all, unsigned* __restrict__ bar, int* __restrict__ err, int expire_test) {
     extern __shared__ double2 td_sh[];
     double2* xs = td_sh;                    // [2][C][n]
     double2* w_sh = td_sh + 2 * (size_t)C * n;  // [n]
@@ -172,7 +172,14 @@ __global__ void __launch_bounds__(kTdThreads)
                     x[0] = cadd(x0, cscale(ph, sigma));  // x now holds v
                 }
                 tau_sh[c] = tau;
-                if (blockIdx.x == 0) e_all[(long long)c * n + k] = sigma;
+                if (blockIdx.x == 0) {
+                    // the reflector of this step, for eigenvectors: tau, the phase of
+                    // x0 (the new sub-diagonal entry is -phase sigma); v goes to row k
+                    e_all[(long long)c * n + k] = sigma;
+                    tau_all[(long long)c * n + k] = tau;
+                    ph_all[(long long)c * n + k] =
+                        ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+                }
             }
             __syncthreads();
             const double2* A = Aall + (long long)c * n * n;
@@ -215,6 +222,10 @@ __global__ void __launch_bounds__(kTdThreads)
             for (int r = threadIdx.x; r < m; r += kTdThreads) w_sh[r] = csub(w_sh[r], cscale(v[r], K));
             __syncthreads();
             double2* A = Aall + (long long)c * n * n;
+            // v of this step into row k right of the diagonal: no step reads or
+            // writes that part of row k after step k - 1
+            if (blockIdx.x == 0)
+                for (int r = threadIdx.x; r < m; r += kTdThreads) A[(long long)k * n + k + 1 + r] = v[r];
             double2* col_out = colbuf + ((size_t)par * C + c) * n;
             for (int R = R0; R < n; R += GW) {
                 const int r = R - k - 1;
@@ -382,11 +393,228 @@ __global__ void __launch_bounds__(kBsWarps * 32)
     if (lane == 0) eig[(long long)c * n + i] = ldexp(0.5 * (lo + hi), sc);
 }
 
+// ---------------------------------------------------------------- eigenvectors
+//
+// After the reduction T' = Q^H T Q with Q = H_0 H_1 ... H_{n-3}
+// (H_k = I - tau_k v_k v_k^H on indices k+1..n-1), T' is Hermitian
+// tridiagonal with sub-diagonal beta_k = -ph_k sigma_k (k < n - 2) and
+// beta_{n-2} = A[n-1][n-2]; with D = diag(delta), delta_0 = 1,
+// delta_{k+1} = delta_k beta_k / |beta_k|, T' = D S D^H for the real
+// symmetric tridiagonal S with off-diagonal |beta_k| (the matrix whose
+// eigenvalues the bisection found).  An eigenvector y of S gives the
+// eigenvector Q D y of T.
+
+__device__ __forceinline__ double2 beta_of(int k, int n, const double2* A, const double* e, const double2* ph) {
+    if (k < n - 2) return cscale(ph[k], -e[k]);
+    return A[(long long)(k + 1) * n + k];
+}
+
+// Eigenvectors y of S for the K largest eigenvalues, one warp per
+// configuration, in order: inverse iteration (three solves with
+// (S - lambda I) by Gaussian elimination with partial pivoting of the
+// tridiagonal, a zero pivot replaced by eps ||S||), each iterate
+// orthogonalised against the earlier vectors whose eigenvalues lie within
+// 1e-3 ||S|| (a cluster) and normalised.  Scratch: 5 n doubles per
+// configuration (sub-diagonal after elimination, diagonal, two
+// super-diagonals, pivots).
+__global__ void __launch_bounds__(32) k_dort_trivec(int n, int K, const double2* __restrict__ Aall,
+                                                    const double* __restrict__ e_all, const double2* __restrict__ ph_all,
+                                                    const double* __restrict__ eig, double* __restrict__ scratch,
+                                                    double* __restrict__ Y) {
+    const int c = blockIdx.x, lane = threadIdx.x;
+    const double2* A = Aall + (long long)c * n * n;
+    const double* e = e_all + (long long)c * n;
+    const double2* ph = ph_all + (long long)c * n;
+    double* dl = scratch + (long long)c * 5 * n;
+    double* dd = dl + n;
+    double* du = dd + n;
+    double* du2 = du + n;
+    double* piv = du2 + n;
+    double* Yc = Y + (long long)c * K * n;
+    // norm bound of S (Gershgorin)
+    double nb = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        double r = fabs(A[(long long)j * n + j].x);
+        if (j > 0) r += sqrt(cabs2(beta_of(j - 1, n, A, e, ph)));
+        if (j < n - 1) r += sqrt(cabs2(beta_of(j, n, A, e, ph)));
+        nb = fmax(nb, r);
+    }
+    for (int off = 16; off > 0; off >>= 1) nb = fmax(nb, __shfl_xor_sync(0xffffffffu, nb, off));
+    if (nb == 0.0) nb = 1.0;
+    const double tiny = 0x1p-52 * nb;
+    for (int i = 0; i < K; ++i) {
+        const double lam = eig[(long long)c * n + i];
+        double* y = Yc + (long long)i * n;
+        if (lane == 0) {
+            // factor S - lam I = P L U (rows i, i+1 swapped where the
+            // sub-diagonal entry is the larger), U with two super-diagonals
+            for (int j = 0; j < n; ++j) {
+                dd[j] = A[(long long)j * n + j].x - lam;
+                if (j < n - 1) dl[j] = du[j] = sqrt(cabs2(beta_of(j, n, A, e, ph)));
+                du2[j] = 0.0;
+            }
+            for (int j = 0; j < n - 1; ++j) {
+                if (fabs(dd[j]) >= fabs(dl[j])) {
+                    piv[j] = 0.0;
+                    if (dd[j] == 0.0) dd[j] = tiny;
+                    const double f = dl[j] / dd[j];
+                    dl[j] = f;
+                    dd[j + 1] -= f * du[j];
+                } else {
+                    piv[j] = 1.0;
+                    const double f = dd[j] / dl[j];
+                    dd[j] = dl[j];
+                    dl[j] = f;
+                    const double t = du[j];
+                    du[j] = dd[j + 1];
+                    dd[j + 1] = t - f * dd[j + 1];
+                    if (j < n - 2) {
+                        du2[j] = du[j + 1];
+                        du[j + 1] = -f * du[j + 1];
+                    }
+                }
+            }
+            if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
+            for (int j = 0; j < n; ++j) y[j] = 1.0 + 0.25 * sin(1.0 + j);  // fixed start vector
+        }
+        __syncwarp();
+        for (int it = 0; it < 3; ++it) {
+            if (lane == 0) {
+                // forward: apply P and L^-1; backward: U^-1
+                for (int j = 0; j < n - 1; ++j) {
+                    if (piv[j] == 0.0) {
+                        y[j + 1] -= dl[j] * y[j];
+                    } else {
+                        const double t = y[j];
+                        y[j] = y[j + 1];
+                        y[j + 1] = t - dl[j] * y[j];
+                    }
+                }
+                y[n - 1] /= dd[n - 1];
+                if (n > 1) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / dd[n - 2];
+                for (int j = n - 3; j >= 0; --j) y[j] = (y[j] - du[j] * y[j + 1] - du2[j] * y[j + 2]) / dd[j];
+            }
+            __syncwarp();
+            // orthogonalise against earlier vectors of the cluster, then normalise
+            for (int j = 0; j < i; ++j) {
+                if (fabs(eig[(long long)c * n + j] - lam) > 1e-3 * nb) continue;
+                const double* yj = Yc + (long long)j * n;
+                double dot = 0.0;
+                for (int t = lane; t < n; t += 32) dot += yj[t] * y[t];
+                for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+                for (int t = lane; t < n; t += 32) y[t] -= dot * yj[t];
+                __syncwarp();
+            }
+            double nrm = 0.0;
+            for (int t = lane; t < n; t += 32) nrm += y[t] * y[t];
+            for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+            const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+            for (int t = lane; t < n; t += 32) y[t] *= inv;
+            __syncwarp();
+        }
+    }
+}
+
+constexpr int kBtThreads = 256;
+
+// u = Q D y for eigenvector i of configuration c (grid: K x C): the phases
+// delta, then the reflectors applied last to first; finally the phase of the
+// vector is fixed (its largest-modulus entry real and positive).  Dynamic
+// shared memory: z [n] complex.
+__global__ void __launch_bounds__(kBtThreads) k_dort_backtransform(int n, int K, const double2* __restrict__ Aall,
+                                                                   const double* __restrict__ e_all,
+                                                                   const double* __restrict__ tau_all,
+                                                                   const double2* __restrict__ ph_all,
+                                                                   const double* __restrict__ Y,
+                                                                   double2* __restrict__ U) {
+    extern __shared__ double2 z[];
+    __shared__ double2 red[kBtThreads / 32];
+    __shared__ double2 dot_sh;
+    const int i = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+    const double2* A = Aall + (long long)c * n * n;
+    const double* e = e_all + (long long)c * n;
+    const double2* ph = ph_all + (long long)c * n;
+    const double* y = Y + ((long long)c * K + i) * n;
+    if (t == 0) {
+        double2 delta = make_double2(1.0, 0.0);
+        for (int k = 0; k < n; ++k) {
+            z[k] = cscale(delta, y[k]);
+            if (k < n - 1) {
+                const double2 b = beta_of(k, n, A, e, ph);
+                const double ab = sqrt(cabs2(b));
+                if (ab > 0.0) delta = cmul(delta, make_double2(b.x / ab, b.y / ab));
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = n - 3; k >= 0; --k) {
+        const int m = n - k - 1;
+        const double tau = tau_all[(long long)c * n + k];
+        const double2* v = A + (long long)k * n + k + 1;
+        double2 s = make_double2(0.0, 0.0);  // v^H z[k+1:]
+        for (int r = t; r < m; r += kBtThreads) s = cadd(s, cmul(cconj(v[r]), z[k + 1 + r]));
+        for (int off = 16; off > 0; off >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+        }
+        if ((t & 31) == 0) red[t >> 5] = s;
+        __syncthreads();
+        if (t == 0) {
+            double2 a = make_double2(0.0, 0.0);
+            for (int w = 0; w < kBtThreads / 32; ++w) a = cadd(a, red[w]);
+            dot_sh = cscale(a, tau);
+        }
+        __syncthreads();
+        const double2 f = dot_sh;
+        for (int r = t; r < m; r += kBtThreads) z[k + 1 + r] = csub(z[k + 1 + r], cmul(v[r], f));
+        __syncthreads();
+    }
+    // phase: the entry of largest modulus real and positive
+    if (t == 0) {
+        int jm = 0;
+        double am = -1.0;
+        for (int j = 0; j < n; ++j) {
+            const double a2 = cabs2(z[j]);
+            if (a2 > am) {
+                am = a2;
+                jm = j;
+            }
+        }
+        const double a = sqrt(am);
+        dot_sh = a > 0.0 ? make_double2(z[jm].x / a, -z[jm].y / a) : make_double2(1.0, 0.0);
+    }
+    __syncthreads();
+    const double2 f = dot_sh;
+    for (int j = t; j < n; j += kBtThreads) U[((long long)c * K + i) * n + j] = cmul(z[j], f);
+}
+
+// Discrete Herglotz waves (section 7): u[p][r] = h sum_j g[r][j]
+// exp(i k (x_p cos a_j + y_p sin a_j)), a_j = 2 pi j / na, h = 2 pi / na.
+__global__ void k_herglotz(double k, int na, int K, const double2* __restrict__ g, long long P,
+                           const double2* __restrict__ pts, double2* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P * K) return;
+    const long long p = t / K;
+    const int r = (int)(t - p * K);
+    const double2 x = pts[p];
+    const double h = 2.0 * M_PI / na;
+    double2 u = make_double2(0.0, 0.0);
+    for (int j = 0; j < na; ++j) {
+        double sa, ca;
+        sincospi(2.0 * j / na, &sa, &ca);
+        double sp, cp;
+        sincos(k * (x.x * ca + x.y * sa), &sp, &cp);
+        u = cadd(u, cmul(g[(long long)r * na + j], make_double2(cp, sp)));
+    }
+    out[p * K + r] = cscale(u, h);
+}
+
 }  // namespace
 
 size_t dort_work_bytes(int C, int n) {
-    // T copy, p and column buffers (two each), e, barrier counter and error flag
-    return (size_t)C * n * n * 16 + 4 * (size_t)C * n * 16 + (size_t)C * n * 8 + 16;
+    // T copy, p and column buffers (two each), e, tau, phases, barrier counter and error flag
+    return (size_t)C * n * n * 16 + 4 * (size_t)C * n * 16 + (size_t)C * n * 8 + (size_t)C * n * 8 +
+           (size_t)C * n * 16 + 16;
 }
 
 namespace {
@@ -412,7 +640,11 @@ cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, 
     w += 2 * (size_t)C * n * 16;
     double2* colbuf = (double2*)w;  // [2][C][n]
     w += 2 * (size_t)C * n * 16;
+    double2* ph = (double2*)w;  // 16-byte aligned: it follows the complex buffers
+    w += (size_t)C * n * 16;
     double* e = (double*)w;
+    w += (size_t)C * n * 8;
+    double* tau = (double*)w;
     w += (size_t)C * n * 8;
     unsigned* bar = (unsigned*)w;
     int* err = (int*)(w + 4);
@@ -442,8 +674,10 @@ cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, 
             if (c0 > 0 && (ce = cudaMemsetAsync(bar, 0, 4, s)) != cudaSuccess) return ce;
             double2* Ag = A + (size_t)c0 * n * n;
             double* eg = e + (size_t)c0 * n;
+            double* tg = tau + (size_t)c0 * n;
+            double2* pg = ph + (size_t)c0 * n;
             int expire_test = g_msd_expire_waits.load();
-            void* args[] = {&Cg, (void*)&n, &Ag, &pbuf, &colbuf, &eg, &bar, &err, &expire_test};
+            void* args[] = {&Cg, (void*)&n, &Ag, &pbuf, &colbuf, &eg, &tg, &pg, &bar, &err, &expire_test};
             ce = cudaLaunchCooperativeKernel((const void*)k_dort_tridiag, dim3(grid), dim3(kTdThreads), args, smem, s);
             if (ce != cudaSuccess) return ce;
             ++launches;
@@ -452,4 +686,36 @@ cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, 
     k_dort_bisect<<<dim3((n + kBsWarps - 1) / kBsWarps, C), kBsWarps * 32, (size_t)n * 16, s>>>(n, A, e, eig);
     g_msd_launches += launches;
     return cudaMemcpyAsync(err_host_flag, err, 4, cudaMemcpyDeviceToHost, s);
+}
+
+// Eigenvectors of the K largest eigenvalues after launch_dort with the same
+// work buffer (reflectors, taus, phases and the reduced matrices kept there):
+// U [C][K][n] complex128, unit 2-norm, the largest-modulus entry real positive.
+// scratch: dort_vec_scratch_bytes(C, n, K).
+size_t dort_vec_scratch_bytes(int C, int n, int K) { return (size_t)C * 5 * n * 8 + (size_t)C * K * n * 8; }
+
+cudaError_t launch_dort_vectors(int C, int n, int K, void* work, const double* eig, void* scratch, double2* U,
+                                cudaStream_t s) {
+    char* w = (char*)work;
+    double2* A = (double2*)w;
+    w += (size_t)C * n * n * 16 + 4 * (size_t)C * n * 16;
+    double2* ph = (double2*)w;
+    w += (size_t)C * n * 16;
+    double* e = (double*)w;
+    w += (size_t)C * n * 8;
+    double* tau = (double*)w;
+    double* lu = (double*)scratch;
+    double* Y = lu + (size_t)C * 5 * n;
+    k_dort_trivec<<<C, 32, 0, s>>>(n, K, A, e, ph, eig, lu, Y);
+    k_dort_backtransform<<<dim3(K, C), kBtThreads, (size_t)n * 16, s>>>(n, K, A, e, tau, ph, Y, U);
+    g_msd_launches += 2;
+    return cudaGetLastError();
+}
+
+void launch_herglotz(double k, int na, int K, const double2* g, long long P, const double2* pts, double2* out,
+                     cudaStream_t s) {
+    const long long tot = P * K;
+    if (tot <= 0) return;
+    k_herglotz<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(k, na, K, g, P, pts, out);
+    g_msd_launches += 1;
 }

@@ -2337,6 +2337,42 @@ msd_status msd_dort_eigen(msd_problem* pb, int n_alpha, const void* F, void* T_o
     });
 }
 
+msd_status msd_dort_eigenvectors(msd_problem* pb, int n_alpha, const void* F, int K, void* eig_out, void* vec_out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || n_alpha <= 0 || n_alpha > MSD_MAX_DORT || !F || K <= 0 || K > n_alpha || !vec_out)
+            fail(MSD_ERR_ARG, "msd_dort_eigenvectors: bad argument (1 <= K <= n_alpha)");
+        const int n = n_alpha;
+        const size_t nn = (size_t)pb->C * n * n;
+        const double2* d_F = (const double2*)stage_in(pb, pb->dortbuf[2], F, nn * 16);
+        dort_eigen(pb, n, d_F, nullptr, eig_out);  // eigenvalues (and the reduction kept in the work buffer)
+        const double* eig = (const double*)pb->dortbuf[4].p;
+        void* work = pb->dortbuf[5].p;
+        void* scratch = pb->dortbuf[0].get(dort_vec_scratch_bytes(pb->C, n, K));
+        OutStage o(pb, pb->dortbuf[1], vec_out, (size_t)pb->C * K * n * 16);
+        CK(launch_dort_vectors(pb->C, n, K, work, eig, scratch, (double2*)o.dev, pb->stream));
+        CK_LAUNCH();
+        o.finish();
+        CK(cudaStreamSynchronize(pb->stream));
+        dort_check(pb);
+        return MSD_OK;
+    });
+}
+
+msd_status msd_herglotz_wave(msd_problem* pb, int config, int n_alpha, int K, const void* g, int64_t P,
+                             const double* points, void* u_out) {
+    return guarded([&]() -> msd_status {
+        if (!pb || config < 0 || config >= pb->C || n_alpha <= 0 || K <= 0 || !g || P <= 0 || !points || !u_out)
+            fail(MSD_ERR_ARG, "msd_herglotz_wave: bad argument");
+        const double2* d_g = (const double2*)stage_in(pb, pb->nfbuf[0], g, (size_t)K * n_alpha * 16);
+        const double2* d_pts = (const double2*)stage_in(pb, pb->nfbuf[1], points, (size_t)P * 16);
+        OutStage o(pb, pb->nfbuf[3], u_out, (size_t)P * K * 16);
+        launch_herglotz(pb->cfg[config].k, n_alpha, K, d_g, P, d_pts, (double2*)o.dev, pb->stream);
+        CK_LAUNCH();
+        o.finish();
+        return MSD_OK;
+    });
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free product

@@ -341,6 +341,15 @@ size_t dort_work_bytes(int C, int n);
 cudaError_t dort_set_smem_limits(int n);
 cudaError_t launch_dort(int C, int n, const double2* F, double2* T, void* work, double* eig, int* err_flag,
                         cudaStream_t s);
+// Eigenvectors of the K largest eigenvalues of every T after launch_dort
+// (same work buffer): U [C][K][n], unit norm, largest entry real positive.
+size_t dort_vec_scratch_bytes(int C, int n, int K);
+cudaError_t launch_dort_vectors(int C, int n, int K, void* work, const double* eig, void* scratch, double2* U,
+                                cudaStream_t s);
+// Discrete Herglotz waves of K parameter vectors g [K][na] at points [P]:
+// out [P][K] = (2 pi / na) sum_j g_j exp(i k x . (cos a_j, sin a_j)), a_j = 2 pi j / na.
+void launch_herglotz(double k, int na, int K, const double2* g, long long P, const double2* pts, double2* out,
+                     cudaStream_t s);
 
 // J: the per-row field factor, as for launch_nearfield.
 void launch_farfield(const MsdConfig* d_cfg, int C, const MsdConfig* h_cfg,

@@ -91,6 +91,8 @@ def _load():
         "msd_test_expire_waits": (V, [I]),
         "msd_set_truncation": (I, [P, P]),
         "msd_penetrable_interior_field": (I, [P, I, P, I, ctypes.c_int64, P, P]),
+        "msd_dort_eigenvectors": (I, [P, I, P, I, P, P]),
+        "msd_herglotz_wave": (I, [P, I, I, I, P, ctypes.c_int64, P, P]),
         "msd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -107,7 +109,8 @@ EXPORTED = ("msd_create", "msd_destroy", "msd_num_unknowns", "msd_row_offset", "
             "msd_matvec_noalloc", "msd_grad_farfield_misfit", "msd_plan_info", "msd_set_tile",
             "msd_set_generator_mode", "msd_nearfield", "msd_rhs_pointsource", "msd_solve_pointsources",
             "msd_dort", "msd_dort_eigen", "msd_set_formulation", "msd_set_formulation_kind",
-            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_truncation", "msd_penetrable_interior_field", "msd_set_penetrable",
+            "msd_formulation_weights", "msd_test_expire_waits", "msd_set_truncation", "msd_penetrable_interior_field", "msd_dort_eigenvectors", "msd_herglotz_wave",
+            "msd_set_penetrable",
             "msd_penetrable_matvec", "msd_solve_penetrable", "msd_solve_penetrable_pointsources",
             "msd_last_error")
 
@@ -372,6 +375,20 @@ def msd_penetrable_interior_field(h, config: int, rho_minus, R: int, points, u_o
     _check(_lib.msd_penetrable_interior_field(h, config, _ptr(rho_minus), R, len(pts), _ptr(pts), _ptr(u_out)))
 
 
+def msd_dort_eigenvectors(h, n_alpha: int, F, K: int, eig_out, vec_out) -> None:
+    if not hasattr(F, "data_ptr"):
+        F = np.ascontiguousarray(F, dtype=np.complex128)
+    _check(_lib.msd_dort_eigenvectors(h, n_alpha, _ptr(F), K, _ptr(eig_out) if eig_out is not None else None,
+                                      _ptr(vec_out)))
+
+
+def msd_herglotz_wave(h, config: int, n_alpha: int, K: int, g, points, u_out) -> None:
+    if not hasattr(g, "data_ptr"):
+        g = np.ascontiguousarray(g, dtype=np.complex128)
+    pts = points if hasattr(points, "data_ptr") else np.ascontiguousarray(points, dtype=np.float64)
+    _check(_lib.msd_herglotz_wave(h, config, n_alpha, K, _ptr(g), len(pts), _ptr(pts), _ptr(u_out)))
+
+
 def msd_set_truncation(h, Np) -> None:
     """Per-disk truncation orders N_p (host int [disk_off[C]]); None restores N."""
     if Np is None:
@@ -618,6 +635,27 @@ class Problem:
         eig = torch.empty((self.C, n), dtype=torch.float64, device="cuda")
         msd_dort_eigen(self.handle, n, F, T, eig)
         return eig, T
+
+    def dort_eigenvectors(self, F, K: int):
+        """Eigenvalues [C, n] and the eigenvectors [C, K, n] of the K largest
+        eigenvalues of T = conj(F)^T F, for far-field matrices F [C, n, n]."""
+        import torch
+        n = F.shape[-1]
+        eig = torch.empty((self.C, n), dtype=torch.float64, device="cuda")
+        vec = torch.empty((self.C, K, n), dtype=torch.complex128, device="cuda")
+        msd_dort_eigenvectors(self.handle, n, F, K, eig, vec)
+        return eig, vec
+
+    def herglotz_wave(self, g, points, config: int = 0):
+        """Discrete Herglotz waves of parameter vectors g [K, n_alpha] at points
+        [P, 2] (complex128 [P, K] on the device)."""
+        import torch
+        g = g if hasattr(g, "data_ptr") else np.ascontiguousarray(g, dtype=np.complex128)
+        K, na = g.shape
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        u = torch.empty((pts.shape[0], K), dtype=torch.complex128, device="cuda")
+        msd_herglotz_wave(self.handle, config, na, K, g, pts, u)
+        return u
 
     def update_geometry(self, centres=None, radii=None, k=None):
         msd_update_geometry(self.handle, centres, radii, k)
