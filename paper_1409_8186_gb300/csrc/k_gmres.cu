@@ -57,7 +57,7 @@ __device__ __forceinline__ void atomic_add_v(float2* p, double2 v) {
 template <typename V>
 __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb,
                             long long vstride, int nv, int self, const V* __restrict__ w,
-                            const int* __restrict__ skip, double2* __restrict__ part) {
+                            const int* __restrict__ skip, int skipval, double2* __restrict__ part) {
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
     const int RY = blockDim.x / RC;  // kThreads and RC are powers of two
@@ -75,7 +75,7 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
     A ax[kI], ay[kI];
 #pragma unroll
     for (int ii = 0; ii < kI; ++ii) ax[ii] = ay[ii] = A(0);
-    const bool live = r < R && !(skip && skip[ch.cfg * R + r]);
+    const bool live = r < R && !(skip && skip[ch.cfg * R + r] == skipval);
     if (live) {
         for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
             const V wv = w[row * R + r];
@@ -128,7 +128,8 @@ template <typename V, int Q>
 __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restrict__ chunks, int R,
                                                         const V* __restrict__ Vb, long long vstride, int nv,
                                                         int self, const V* __restrict__ w,
-                                                        const int* __restrict__ skip, double2* __restrict__ part) {
+                                                        const int* __restrict__ skip, int skipval,
+                                                        double2* __restrict__ part) {
     const RowChunk ch = chunks[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.y * (kThreads / 32) + warp;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
     if (skip) {
         bool live = false;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) live |= !skip[ch.cfg * R + (int)((e0 + lane + 32 * q) % R)];
+        for (int q = 0; q < Q; ++q) live |= skip[ch.cfg * R + (int)((e0 + lane + 32 * q) % R)] != skipval;
         if (!__any_sync(0xffffffffu, live)) {
 #pragma unroll
             for (int q = 0; q < Q; ++q)
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
     for (int q = 0; q < Q; ++q) {
         if (Q == 1 && lane >= R) break;
         const int r = (int)((e0 + lane + 32 * q) % R);
-        const bool sk = skip && skip[ch.cfg * R + r];
+        const bool sk = skip && skip[ch.cfg * R + r] == skipval;
         part[((long long)blockIdx.x * nvv + i) * R + r] =
             sk ? make_double2(0.0, 0.0) : make_double2((double)ax[q], (double)ay[q]);
     }
@@ -230,7 +231,7 @@ template <typename V, typename W>
 __global__ void __launch_bounds__(kThreads, 4)
     k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
                          int nv, const double2* __restrict__ h, int hstride, const int* __restrict__ skip,
-                         double sign, W* __restrict__ w) {
+                         int skipval, double sign, W* __restrict__ w) {
     typedef decltype(V{}.x) A;
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     }
     __syncthreads();
     if (r >= R || i0 >= i1) return;
-    if (skip && skip[ch.cfg * R + r]) return;
+    if (skip && skip[ch.cfg * R + r] == skipval) return;
     const bool atomic = gridDim.z > 1;
     const int cnt = i1 - i0;
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
@@ -550,18 +551,18 @@ inline unsigned rgroups(int R) { return (unsigned)((R + col_lanes(R) - 1) / col_
 template <typename V>
 void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
              int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
-             cudaStream_t s) {
+             cudaStream_t s, int skipval) {
     const int nvv = nv + self;
     constexpr int WPB = kThreads / 32;
     if (32 % d.R == 0) {
         k_dots_warp<V, 1><<<dim3(d.nchunk, (nvv + WPB - 1) / WPB), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv,
-                                                                                    self, w, skip, part);
+                                                                                    self, w, skip, skipval, part);
     } else if (d.R == 64) {
         k_dots_warp<V, 2><<<dim3(d.nchunk, (nvv + WPB - 1) / WPB), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv,
-                                                                                    self, w, skip, part);
+                                                                                    self, w, skip, skipval, part);
     } else {
         dim3 g(d.nchunk, rgroups(d.R), (nvv + kI - 1) / kI);
-        k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, part);
+        k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, skipval, part);
     }
     const long long tot = (long long)d.S * nvv;
     k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
@@ -570,10 +571,10 @@ void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
 
 template <typename V, typename W>
 void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv, const double2* h,
-               int hstride, const int* skip, double sign, W* w, cudaStream_t s) {
+               int hstride, const int* skip, double sign, W* w, cudaStream_t s, int skipval) {
     if (nv <= 0) return;
     dim3 g(d.nchunk, rgroups(d.R), (nv + kU - 1) / kU);
-    k_update<V, W><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, h, hstride, skip, sign, w);
+    k_update<V, W><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, h, hstride, skip, skipval, sign, w);
     g_msd_launches += 1;
 }
 
@@ -628,15 +629,15 @@ void gm_zero(long long n, double2* x, cudaStream_t s) {
 }
 
 template void gm_dots<double2>(const GmresDims&, const RowChunk*, const int*, const double2*, long long, int, int,
-                               const double2*, const int*, double2*, double2*, int, cudaStream_t);
+                               const double2*, const int*, double2*, double2*, int, cudaStream_t, int);
 template void gm_dots<float2>(const GmresDims&, const RowChunk*, const int*, const float2*, long long, int, int,
-                              const float2*, const int*, double2*, double2*, int, cudaStream_t);
+                              const float2*, const int*, double2*, double2*, int, cudaStream_t, int);
 template void gm_update<double2, double2>(const GmresDims&, const RowChunk*, const double2*, long long, int,
-                                          const double2*, int, const int*, double, double2*, cudaStream_t);
+                                          const double2*, int, const int*, double, double2*, cudaStream_t, int);
 template void gm_update<float2, float2>(const GmresDims&, const RowChunk*, const float2*, long long, int,
-                                        const double2*, int, const int*, double, float2*, cudaStream_t);
+                                        const double2*, int, const int*, double, float2*, cudaStream_t, int);
 template void gm_update<float2, double2>(const GmresDims&, const RowChunk*, const float2*, long long, int,
-                                         const double2*, int, const int*, double, double2*, cudaStream_t);
+                                         const double2*, int, const int*, double, double2*, cudaStream_t, int);
 template void gm_scale<double2, double2>(const GmresDims&, const RowChunk*, const double2*, const double*,
                                          const int*, double2*, cudaStream_t);
 template void gm_scale<double2, float2>(const GmresDims&, const RowChunk*, const double2*, const double*,

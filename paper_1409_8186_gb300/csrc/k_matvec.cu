@@ -143,7 +143,8 @@ template <typename V, int RT, int RB, int KB, int P, int S>
 __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
                                                    const MatvecWork* __restrict__ works,
                                                    const V* __restrict__ G, const V* __restrict__ xs,
-                                                   V* __restrict__ part, long long Ntot, int R, int rtiles) {
+                                                   V* __restrict__ part, long long Ntot, int R, int rtiles,
+                                                   const int* __restrict__ live) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* smem = reinterpret_cast<V*>(smem_raw);
 
@@ -172,6 +173,24 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
     const int m0 = mblk * KB;
     const int c0 = rgrp * RB;  // first column of this thread within the tile
     const int col0 = rt * RT;  // first column of the tile
+
+    // no active column in this tile (converged Krylov systems): zero raw
+    // sums, no other work
+    if (live) {
+        bool any = false;
+        for (int r = 0; r < RT; ++r) any |= live[w.cfg * R + col0 + r] != 0;
+        if (!any) {
+            const int p = w.p0 + lane;
+            if (!w.pad && mact && p < c.M) {
+                V* out = part + (long long)w.split * Ntot * R;
+                for (int b = 0; b < KB; ++b)
+                    if (m0 + b < n)
+                        for (int r = 0; r < RB; ++r)
+                            out[(c.row_off + (long long)p * n + m0 + b) * R + col0 + c0 + r] = vzero<V>();
+            }
+            return;
+        }
+    }
 
     // zero the padding of the stages once (staging never writes it)
     for (int s = 0; s < S; ++s) {
@@ -384,11 +403,11 @@ struct Bt {
         return dim3(32, ((n + KB - 1) / KB) * (RT / RB));
     }
     static void launch(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const V* G,
-                       const V* xs, V* part, long long Ntot, int R, cudaStream_t s) {
+                       const V* xs, V* part, long long Ntot, int R, cudaStream_t s, const int* live = nullptr) {
         attr();
         const int rtiles = R / RT;
         k_bt_matvec<V, RT, RB, KB, P, S><<<(unsigned)(nwork * rtiles), block(Nmax), smem(Nmax), s>>>(
-            d_cfg, d_work, G, xs, part, Ntot, R, rtiles);
+            d_cfg, d_work, G, xs, part, Ntot, R, rtiles, live);
     }
     static int occupancy(int Nmax) {
         attr();
@@ -557,14 +576,14 @@ void launch_bt_only(const MatvecChoice& c, bool fp64, const MsdConfig* d_cfg, co
 void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const double2* G, const double* rf, const double2* lf, long long Ntot, int R,
                        const double2* x, double2* xs, double2* part, int nsplit, double2* y, cudaStream_t s,
-                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch) {
+                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch, const int* live) {
     const long long tot = Ntot * R;
     const int th = 256;
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
     k_scale_cols<double2, double><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
     if (ev0) cudaEventRecord(ev0, s);
     dispatch64(ch ? *ch : choose(R, Nmax, true), [&](auto k) {
-        decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s);
+        decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s, live);
     });
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize<double2><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);
@@ -574,7 +593,7 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
 void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const float2* G, const float* rf, const float2* lf, long long Ntot, int R,
                        const float2* x, float2* xs, float2* part, int nsplit, float2* y, cudaStream_t s,
-                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch) {
+                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch, const int* live) {
     const long long tot = Ntot * R;
     const int th = 256;
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
@@ -582,10 +601,12 @@ void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
     if (ev0) cudaEventRecord(ev0, s);
     const Choice c = ch ? *ch : choose(R, Nmax, false);
     if (c.TC) {
-        launch_bt_tc(c.TC, d_cfg, d_work, nwork, G, xs, part, Ntot, R, s);
+        launch_bt_tc(c.TC, d_cfg, d_work, nwork, G, xs, part, Ntot, R, s, live);
         g_msd_launches -= 1;  // counted below with the scaling and the reduction
     } else {
-        dispatch32(c, [&](auto k) { decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s); });
+        dispatch32(c, [&](auto k) {
+            decltype(k)::launch(d_cfg, d_work, nwork, Nmax, G, xs, part, Ntot, R, s, live);
+        });
     }
     if (ev1) cudaEventRecord(ev1, s);
     k_finalize<float2><<<(unsigned)((tot * kFinLanes + th - 1) / th), th, 0, s>>>(Ntot, R, nsplit, lf, x, part, y);

@@ -134,7 +134,7 @@ template <int RC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_bt_tc(const MsdConfig* __restrict__ cfgs, const MatvecWork* __restrict__ works, const float2* __restrict__ G,
             const float2* __restrict__ xs, float2* __restrict__ part, long long Ntot, int R, int rtiles,
-            int expire_test) {
+            int expire_test, const int* __restrict__ live) {
     typedef TcLayout<RC> Lay;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -154,6 +154,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nk = (n + kKc - 1) / kKc;                          // stages per source
     const int col0 = rt * RC;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // no active column in this tile (converged Krylov systems): zero raw
+    // sums, no other work
+    if (live) {
+        bool any = false;
+        for (int r = 0; r < RC; ++r) any |= live[w.cfg * R + col0 + r] != 0;
+        if (!any) {
+            if (!w.pad) {
+                float2* out = part + (long long)w.split * Ntot * R + col0;
+                for (int t = tid; t < np * n * RC; t += kTcThreads) {
+                    const int i = t / RC, j = t - i * RC;
+                    out[(c.row_off + (long long)w.p0 * n + i) * R + j] = make_float2(0.f, 0.f);
+                }
+            }
+            return;
+        }
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
@@ -385,7 +402,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 template <int RC>
 void launch_rc(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, const float2* G, const float2* xs,
-               float2* part, long long Ntot, int R, cudaStream_t s) {
+               float2* part, long long Ntot, int R, cudaStream_t s, const int* live) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_bt_tc<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<RC>::kSmem);
@@ -394,7 +411,7 @@ void launch_rc(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, cons
     const int rtiles = R / RC;
     k_bt_tc<RC><<<(unsigned)(nwork * rtiles), kTcThreads, TcLayout<RC>::kSmem, s>>>(d_cfg, d_work, G, xs, part, Ntot,
                                                                                     R, rtiles,
-                                                                                    g_msd_expire_waits.load());
+                                                                                    g_msd_expire_waits.load(), live);
 }
 
 }  // namespace
@@ -413,12 +430,12 @@ size_t tc_smem_bytes(int RC) {
 }
 
 void launch_bt_tc(int RC, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, const float2* G,
-                  const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s) {
+                  const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s, const int* live) {
     if (nwork <= 0) return;
     switch (RC) {
-        case 16: launch_rc<16>(d_cfg, d_work, nwork, G, xs, part, Ntot, R, s); break;
-        case 32: launch_rc<32>(d_cfg, d_work, nwork, G, xs, part, Ntot, R, s); break;
-        default: launch_rc<64>(d_cfg, d_work, nwork, G, xs, part, Ntot, R, s); break;
+        case 16: launch_rc<16>(d_cfg, d_work, nwork, G, xs, part, Ntot, R, s, live); break;
+        case 32: launch_rc<32>(d_cfg, d_work, nwork, G, xs, part, Ntot, R, s, live); break;
+        default: launch_rc<64>(d_cfg, d_work, nwork, G, xs, part, Ntot, R, s, live); break;
     }
     g_msd_launches += 1;
 }

@@ -149,7 +149,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_bt_tcs(const MsdConfig* __restrict__ cfgs, const MatvecWork* __restrict__ works, const float* __restrict__ GT,
              const float* __restrict__ XT, float2* __restrict__ part, long long Ntot, int R, int rtiles,
-             int kStages, int expire_test) {
+             int kStages, int expire_test, const int* __restrict__ live) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint32_t tmem_sh;
@@ -169,6 +169,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ptile = w.p0 >> 7;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+    // no active column in this tile (converged Krylov systems): zero raw
+    // sums, no other work
+    if (live) {
+        bool any = false;
+        for (int r = 0; r < kRC; ++r) any |= live[w.cfg * R + rt * kRC + r] != 0;
+        if (!any) {
+            const int mend0 = min(n, m0 + nmb * mb), nm = mend0 - m0;
+            float2* out = part + (long long)w.split * Ntot * R + rt * kRC;
+            for (int t = threadIdx.x; t < 128 * nm; t += kThreads) {
+                const int p = w.p0 + t / nm, m = m0 + t % nm;
+                if (p < c.M) {
+                    float4* o = (float4*)(out + (c.row_off + (long long)p * n + m) * R);
+#pragma unroll
+                    for (int r = 0; r < kRC / 2; ++r) o[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            return;
+        }
+    }
     unsigned char* A = sm;                                   // [kStages][16 KB]
     unsigned char* slab = sm + kStages * kAStage;            // [2][4][(n + 14) * 256]
     const int blk = (n + 2 * kPad) * 256;                    // bytes of one slab block
@@ -571,7 +590,7 @@ void tcs_mode_blocks(int n, int* mb_out, int* nblocks_out, bool wide) {
 }
 
 void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float* GT,
-                   const float* XT, float2* part, long long Ntot, int R, cudaStream_t s) {
+                   const float* XT, float2* part, long long Ntot, int R, cudaStream_t s, const int* live) {
     if (nwork <= 0) return;
     static bool attr = false;
     if (!attr) {
@@ -580,7 +599,7 @@ void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, 
     }
     const int rtiles = R / kRC;
     k_bt_tcs<<<(unsigned)((long long)nwork * rtiles), kThreads, tcs_smem_bytes(Nmax), s>>>(
-        d_cfg, d_work, GT, XT, part, Ntot, R, rtiles, tcs_stages(Nmax), g_msd_expire_waits.load());
+        d_cfg, d_work, GT, XT, part, Ntot, R, rtiles, tcs_stages(Nmax), g_msd_expire_waits.load(), live);
     g_msd_launches += 1;
 }
 

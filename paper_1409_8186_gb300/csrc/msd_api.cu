@@ -225,6 +225,11 @@ struct msd_problem {
     // shift-GEMM tensor-core product: the complex64 generators in its
     // A-operand order (TF32 hi/lo), built for geometry version gt_version;
     // xrows = sum over configurations of Mq * n (its source rows per column)
+    // active flags [C*R] of the Krylov systems while an Arnoldi step runs its
+    // product (nullptr otherwise): forward products of the default rows skip
+    // the tiles none of whose columns are active (converged systems, whose
+    // columns of the step are never read) and leave zero sums there
+    const int* live = nullptr;
     // per-disk truncation orders (msd_set_truncation); d_Np == nullptr: N of
     // the configuration on every disk
     std::vector<int> Np;
@@ -970,17 +975,17 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
         launch_tcs_prep_x(pb->d_cfg, pb->C, pb->xrows / 4, R, pb->d_rf32, (const float2*)x, XT, pb->stream);
         if (e0) CK(cudaEventRecord(e0, pb->stream));
         launch_bt_tcs(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_GT, XT, (float2*)part, pb->Ntot,
-                      R, pb->stream);
+                      R, pb->stream, pb->live);
         if (e1) CK(cudaEventRecord(e1, pb->stream));
         launch_finalize(false, pb->Ntot, R, plan.nsplit, pb->d_lf32, x, part, y, pb->stream);
     } else if (fp64)
         launch_matvec_f64(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G64, pb->d_rf64,
                           pb->d_lf64, pb->Ntot, R, (const double2*)x, (double2*)xs, (double2*)part,
-                          plan.nsplit, (double2*)y, pb->stream, e0, e1, &plan.ch);
+                          plan.nsplit, (double2*)y, pb->stream, e0, e1, &plan.ch, pb->live);
     else
         launch_matvec_f32(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G32, pb->d_rf32,
                           pb->d_lf32, pb->Ntot, R, (const float2*)x, (float2*)xs, (float2*)part,
-                          plan.nsplit, (float2*)y, pb->stream, e0, e1, &plan.ch);
+                          plan.nsplit, (float2*)y, pb->stream, e0, e1, &plan.ch, pb->live);
     CK_LAUNCH();
 }
 
@@ -1109,6 +1114,14 @@ void norm2_f64(SolveCtx& cx, const double2* u, double2* out) {
 // Basis size from which projections run over the coarse row chunks.
 constexpr int kCoarseFrom = 64;
 
+// Hands the active flags of the Krylov systems to the products of one
+// Arnoldi step, and takes them back however the step ends.
+struct LiveScope {
+    msd_problem* pb;
+    LiveScope(msd_problem* p, const int* active) : pb(p) { pb->live = active; }
+    ~LiveScope() { pb->live = nullptr; }
+};
+
 // One restart cycle of GMRES on P^-1 A d = r (x += d), basis type V.
 template <typename V>
 void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* steps_taken) {
@@ -1143,7 +1156,11 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
             if (!pb->h_pinned[2 + 2 * slot]) break;
         }
         V* vj = Vb + (long long)j * vstride;
-        operator_dev(pb, d.R, fp64, cx.adjoint, vj, w);
+        {
+            // the product may skip configurations with no active column
+            LiveScope live(pb, cx.active);
+            operator_dev(pb, d.R, fp64, cx.adjoint, vj, w);
+        }
         // projections onto many basis vectors: the coarse row chunks when the
         // block-reduction kernel serves this column count (warp-per-vector
         // kernels need no reduction and run on the fine chunks: more warps)
@@ -1152,9 +1169,10 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         if (coarse) db.nchunk = (int)pb->chunks_coarse.size();
         const RowChunk* chb = coarse ? pb->d_chunks_coarse : ch;
         const int* cob = coarse ? pb->d_cfg_chunk_off_coarse : co;
-        // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1
-        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, nullptr, cx.part, cx.h1, cx.hstride, s);
-        gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, nullptr, -1.0, w, s);
+        // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1;
+        // systems that have converged (zero vectors from here on) are skipped
+        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, cx.active, cx.part, cx.h1, cx.hstride, s, 0);
+        gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, cx.active, -1.0, w, s, 0);
         // second projection only where the first removed more than half of ||w||^2
         gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
         gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s);
@@ -1347,7 +1365,9 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
                 // on the rounding of the inner product)
                 if (relres[i] < (1.0 - 1e-3) * prev[i]) improved = true;
             }
-            tol_cycle[i] = mixed ? std::max(tol_abs[i], o.inner_tol * rn) : tol_abs[i];
+            // FP32 sweeps aim 20x below the stopping tolerance, so that the
+            // rounding of the FP32 correction cannot leave a system just above it
+            tol_cycle[i] = mixed ? std::max(0.05 * tol_abs[i], o.inner_tol * rn) : tol_abs[i];
         }
         if (all) break;
         if (mixed && sweeps > 0 && !improved) {

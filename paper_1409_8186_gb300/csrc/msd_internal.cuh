@@ -115,7 +115,7 @@ bool tc_supported(int R, int Nmax, int RC);
 int tc_tile_disks(int n);
 size_t tc_smem_bytes(int RC);
 void launch_bt_tc(int RC, const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, const float2* G,
-                  const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s);
+                  const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s, const int* live = nullptr);
 int tc_status_and_clear();
 // shift-GEMM tensor-core product (k_matvec_tcs.cu): GT = generators in the
 // A-operand order (built from the complex64 generators), XT = scaled columns
@@ -127,8 +127,12 @@ bool tcs_supported(int R, int Nmax);
 // blocks of <= 8 modes grouped two per CTA (N = 16 mb <= 128 per MMA), or
 // wide: one block of <= 16 modes per CTA (N <= 256 per MMA)
 void tcs_mode_blocks(int n, int* mb, int* nblocks, bool wide);
+// live: NULL, or active flags [C*R]; a CTA whose columns are all inactive
+// writes zero raw sums and does no other work (the caller reads none of
+// those columns)
 void launch_bt_tcs(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float* GT,
-                   const float* XT, float2* part, long long Ntot, int R, cudaStream_t s);
+                   const float* XT, float2* part, long long Ntot, int R, cudaStream_t s,
+                   const int* live = nullptr);
 void launch_tcs_build_gt(const MsdConfig* d_cfg, int C, const long long* d_blk_off, long long nblocks,
                          const float2* G32, float* GT, cudaStream_t s);
 void launch_tcs_prep_x(const MsdConfig* d_cfg, int C, long long rows4, int R, const float* rf, const float2* x,
@@ -324,12 +328,12 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
                        const double2* G, const double* rf, const double2* lf, long long Ntot,
                        int R, const double2* x, double2* xs, double2* part, int nsplit,
                        double2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                       const MatvecChoice* ch = nullptr);
+                       const MatvecChoice* ch = nullptr, const int* live = nullptr);
 void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const float2* G, const float* rf, const float2* lf, long long Ntot,
                        int R, const float2* x, float2* xs, float2* part, int nsplit,
                        float2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                       const MatvecChoice* ch = nullptr);
+                       const MatvecChoice* ch = nullptr, const int* live = nullptr);
 
 // K6: far field.
 // Time reversal (section 7): T = conj(F)^T F for C far-field matrices
@@ -370,15 +374,17 @@ struct GmresDims {
 };
 
 // out[s][i] = sum over the rows of cfg(s) of conj(u_i) w for u = V_0..V_{nv-1}
-// (and w itself when self = 1); systems with skip[s] != 0 get zeros.
+// (and w itself when self = 1); systems with skip[s] == skipval get zeros
+// (skipval 1 with a skip-flag array, 0 with the active flags: inactive
+// systems have zero vectors, so skipping them changes no value).
 template <typename V>
 void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
              int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
-             cudaStream_t s);
-// w += sign * sum_i V_i h[s][i]  (skip[s] != 0: unchanged)
+             cudaStream_t s, int skipval = 1);
+// w += sign * sum_i V_i h[s][i]  (skip[s] == skipval: unchanged)
 template <typename V, typename W>
 void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv, const double2* h,
-               int hstride, const int* skip, double sign, W* w, cudaStream_t s);
+               int hstride, const int* skip, double sign, W* w, cudaStream_t s, int skipval = 1);
 // v = w * scale[s] for active systems, 0 otherwise
 template <typename Vin, typename Vout>
 void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale, const int* active,

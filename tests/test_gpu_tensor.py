@@ -172,3 +172,33 @@ def test_shift_gemm_mixed_solve_and_adjoint_fallback(msd):
                                               precision=msd.MSD_FP64)
     assert abs(J[0] - J64[0]) <= 1e-9 * J64[0]
     assert np.abs(dO - dO64).max() <= 1e-7 * np.abs(dO64).max()
+
+
+# ---------------------------------------------------------------- converged systems skipped
+
+@pytest.mark.parametrize("precision,KB,RT", [("mixed", 0, 8), ("mixed", 0, 16), ("mixed", 6, 8), ("fp64", None, None)])
+def test_converged_configurations_skipped_by_products(msd, precision, KB, RT):
+    """Two configurations of very different difficulty in one batched solve:
+    four disks converge in a few steps, rand70 needs many more.  After the
+    four-disk systems converge, the products of the later Arnoldi steps skip
+    their tiles (no active column) and write zero sums there; the solutions of
+    both configurations must still equal the oracle's direct solve.  Covers
+    the shift-GEMM (KB 0, RT 8), expanded-Toeplitz tensor-core (KB 0, RT 16),
+    CUDA-core FP32 and FP64 product kernels."""
+    cls = [W.four_disks(), rand70()]
+    R = 16
+    pb = msd.Problem(cls)
+    prec = msd.MSD_MIXED if precision == "mixed" else msd.MSD_FP64
+    if KB is not None:
+        pb.set_tile(R, msd.MSD_FP32, KB, RT)
+    betas = np.stack([W.angles(R), W.angles(R) + 0.05])
+    res = pb.solve(betas, tol=1e-12, precision=prec, restart=200)
+    assert (res.flags == 0).all(), res.relres
+    it = np.asarray(res.iters).reshape(2, R)
+    assert it[0].max() < it[1].min(), it          # the skip happened
+    rho = res.rho.cpu().numpy()
+    for c, cl in enumerate(cls):
+        o0 = pb.row_offset(c)
+        ref, _ = O_.solve(cl.centres, cl.radii, cl.bc, cl.k, cl.N, betas[c], method="lu")
+        assert relerr(rho[o0:o0 + cl.ntot], ref) < 1e-9, (c, relerr(rho[o0:o0 + cl.ntot], ref))
+    pb.close()
