@@ -373,7 +373,8 @@ def batched_timing(count: int = 16):
     pb.close()
 
 
-def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_rows: int = 2, only_group: int = -1):
+def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_rows: int = 2, only_group: int = -1,
+                 fp64_groups=()):
     """The batched workload as specified: 256 seeded clusters (M ~ U{50..800},
     unit radii, area fraction 0.2, gap 0.01, k ~ U[1, 8], N = ceil(k) + 8,
     Dirichlet/Neumann per disk ~ Bernoulli(1/2)), 32 incidences each,
@@ -383,7 +384,9 @@ def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_row
     fit in HBM together with a long restart); one JSON line per group and
     one for the whole batch.  Every cluster is checked on `check_rows`
     sampled target disks: the oracle's residual of the GPU densities on
-    those rows must be within the stopping bound (1.05e-10 ||P^-1 b||)."""
+    those rows must be within the stopping bound (1.05e-10 ||P^-1 b||).
+    The groups listed in `fp64_groups` are solved a second time in FP64 (the
+    plain GPU solve the mixed one is compared with)."""
     import numpy as np
     import torch
     import oracle.msd_oracle as O_
@@ -420,6 +423,17 @@ def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_row
             for i, p in enumerate(tg):
                 r = b[p * cl.n:(p + 1) * cl.n] - rows[i]
                 worst = max(worst, float((np.linalg.norm(r, axis=0) / bn).max()))
+        fp64 = None
+        if gi in fp64_groups:
+            torch.cuda.synchronize()
+            e0.record()
+            r64 = pb.solve(betas, tol=1e-10, precision=msd.MSD_FP64, maxit=maxit)
+            e1.record()
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            fp64 = {"solve_ms": round(ms64, 1), "status": int(r64.status), "iters_max": int(r64.iters.max()),
+                    "relres_max": float(r64.relres.max()), "mixed_speedup": round(ms64 / ms, 2)}
+            del r64
         tot_ms += ms
         worst_rel = max(worst_rel, float(res.relres.max()))
         worst_check = max(worst_check, worst)
@@ -430,7 +444,7 @@ def batched_full(groups: int = 8, take: int = 256, maxit: int = 20000, check_row
                           "fp32_product_shape": info32, "solve_ms": round(ms, 1), "status": int(res.status),
                           "iters_max": int(res.iters.max()), "iters_median": float(np.median(res.iters)),
                           "refine_steps": int(res.refine_steps.max()), "relres_max": float(res.relres.max()),
-                          "sampled_residual_max": worst}), flush=True)
+                          "sampled_residual_max": worst, "fp64": fp64}), flush=True)
         pb.close()
         del pb, res, rho
         torch.cuda.empty_cache()
@@ -654,6 +668,8 @@ def main():
     ap.add_argument("--groups", type=int, default=8, help="with --batched-full: batched problems of similar M")
     ap.add_argument("--take", type=int, default=256, help="with --batched-full: the smallest TAKE clusters only")
     ap.add_argument("--only-group", type=int, default=-1, help="with --batched-full: run this group only")
+    ap.add_argument("--fp64-groups", type=str, default="",
+                    help="with --batched-full: comma-separated groups also solved in FP64")
     ap.add_argument("--lattice-solve", type=int, default=0, metavar="R",
                     help="solve the 4000-disk lattice with R incidences (mixed precision) and print a JSON line")
     ap.add_argument("--nearfield", action="store_true",
@@ -676,7 +692,8 @@ def main():
     if args.lattice_solve:
         return lattice_solve(R=args.lattice_solve)
     if args.batched_full:
-        return batched_full(groups=args.groups, take=args.take, only_group=args.only_group)
+        fg = tuple(int(v) for v in args.fp64_groups.split(",") if v.strip())
+        return batched_full(groups=args.groups, take=args.take, only_group=args.only_group, fp64_groups=fg)
     if args.batched:
         return batched_timing()
     if args.products:
