@@ -393,8 +393,32 @@ template <> struct AffOps<AffF> {
 // on this GPU, and the chain made the step ~20 us).  The rotation itself is
 // formed in FP64.  The raw column is stored; k_apply_rotations rotates all
 // columns at the end of the cycle in FP64, in parallel across columns.
+// Warp-shuffle transfer of the maps (lane + off -> lane).
+__device__ __forceinline__ Aff shfl_down(const Aff& f, int off) {
+    return Aff{make_double2(__shfl_down_sync(0xffffffffu, f.A.x, off), __shfl_down_sync(0xffffffffu, f.A.y, off)),
+               make_double2(__shfl_down_sync(0xffffffffu, f.B.x, off), __shfl_down_sync(0xffffffffu, f.B.y, off))};
+}
+__device__ __forceinline__ AffF shfl_down(const AffF& f, int off) {
+    return AffF{make_float2(__shfl_down_sync(0xffffffffu, f.A.x, off), __shfl_down_sync(0xffffffffu, f.A.y, off)),
+                make_float2(__shfl_down_sync(0xffffffffu, f.B.x, off), __shfl_down_sync(0xffffffffu, f.B.y, off))};
+}
+// Ordered reduction over the 32 lanes of a warp: lane 0 receives
+// f_31 o ... o f_1 o f_0 (later lanes compose onto earlier ones).
 template <typename Map>
-__global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2* __restrict__ h1,
+__device__ __forceinline__ Map warp_compose(Map f) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off *= 2) {
+        const Map later = shfl_down(f, off);
+        if ((lane & (2 * off - 1)) == 0) f = compose(later, f);
+    }
+    return f;
+}
+
+constexpr int kGivensThreads = 1024;
+
+template <typename Map>
+__global__ void __launch_bounds__(kGivensThreads) k_givens(int m, int j, const double2* __restrict__ h1,
                                                      const double2* __restrict__ h2, int hstride,
                                                      const double2* __restrict__ wn2a,
                                                      const double2* __restrict__ wn2b,
@@ -408,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
                                                      double2* __restrict__ rdiag) {
     const int s = blockIdx.x;
     if (!active[s]) return;
-    __shared__ Map red[kThreads];
+    __shared__ Map red[kGivensThreads / 32];
     const int tid = threadIdx.x, T = blockDim.x;
     const bool second = !skip2[s];
     const double2* a = h1 + (long long)s * hstride;
@@ -427,15 +451,16 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
     const int lo = min(j, tid * per), hi = min(j, lo + per);
     Map seg = AffOps<Map>::id();
     for (int i = lo; i < hi; ++i) seg = compose(AffOps<Map>::step(csj[i], snj[i], hval(i + 1)), seg);
-    red[tid] = seg;
+    // ordered reduction: within each warp by shuffles, then over the warps
+    seg = warp_compose(seg);
+    const int nw = T >> 5;
+    if ((tid & 31) == 0) red[tid >> 5] = seg;
     __syncthreads();
-    // ordered tree: later segments compose onto earlier ones
-    for (int off = 1; off < T; off *= 2) {
-        if ((tid & (2 * off - 1)) == 0 && tid + off < T) red[tid] = compose(red[tid + off], red[tid]);
-        __syncthreads();
-    }
+    if (tid >= 32) return;
+    seg = tid < nw ? red[tid] : AffOps<Map>::id();
+    seg = warp_compose(seg);
     if (tid != 0) return;
-    const double2 hjj = AffOps<Map>::apply(red[0], hval(0));
+    const double2 hjj = AffOps<Map>::apply(seg, hval(0));
     const double wn = second ? wn2b[(long long)s * hstride].x : wn2a[(long long)s * hstride].x;
     const double hn = sqrt(fmax(wn, 0.0));
     const double ajj = sqrt(cabs2(hjj));
@@ -463,14 +488,14 @@ __global__ void __launch_bounds__(kThreads) k_givens(int m, int j, const double2
     iters[s] += 1;
     const double res = sqrt(cabs2(gs[j + 1]));
     const bool bad = !isfinite(res) || !isfinite(rjj.x) || !isfinite(rjj.y);
-    if (bad) atomicOr(nonfinite, 1);
+    if (bad) *nonfinite = 1;  // every writer stores the same value (the flag may live in host memory)
     if (bad || res <= tol_cycle[s] || hn == 0.0 || j + 1 == m) {
         active[s] = 0;
         kconv[s] = j + 1;
         vscale[s] = 0.0;
     } else {
         vscale[s] = 1.0 / hn;
-        atomicOr(any_active, 1);
+        *any_active = 1;
     }
 }
 
@@ -598,16 +623,24 @@ void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* 
     g_msd_launches += 1;
 }
 
+// Threads of the Givens step: about two rotations per thread, whole warps.
+static int givens_threads(int j) {
+    const int t = ((j + 1) / 2 + 31) / 32 * 32;
+    return std::min(kGivensThreads, std::max(32, t));
+}
+
 void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride, const double2* wn2a,
                const double2* wn2b, const int* skip2, const double* tol_cycle, double2* H, double2* cs,
                double2* sn, double2* g, double* vscale, int* active, int* kconv, int* iters, int* any_active,
                int* nonfinite, double2* rdiag, bool fp32_maps, cudaStream_t s) {
     if (fp32_maps)
-        k_givens<AffF><<<d.S, kThreads, 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H, cs, sn, g,
-                                                vscale, active, kconv, iters, any_active, nonfinite, rdiag);
+        k_givens<AffF><<<d.S, givens_threads(j), 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H,
+                                                         cs, sn, g, vscale, active, kconv, iters, any_active,
+                                                         nonfinite, rdiag);
     else
-        k_givens<Aff><<<d.S, kThreads, 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H, cs, sn, g,
-                                               vscale, active, kconv, iters, any_active, nonfinite, rdiag);
+        k_givens<Aff><<<d.S, givens_threads(j), 0, s>>>(d.m, j, h1, h2, hstride, wn2a, wn2b, skip2, tol_cycle, H,
+                                                        cs, sn, g, vscale, active, kconv, iters, any_active,
+                                                        nonfinite, rdiag);
     g_msd_launches += 1;
 }
 

@@ -195,6 +195,7 @@ struct msd_problem {
     RowChunk* d_chunks_coarse = nullptr;
     int* d_cfg_chunk_off_coarse = nullptr;
     int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags, [10] DORT barrier
+    int* d_hpinned = nullptr;  // the same flags as the device addresses them (mapped host memory)
     cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf xs, part, sbuf[24];
     DBuf gbuf[9];   // gradient work buffers
@@ -1178,14 +1179,20 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h2, cx.hstride, cx.skip2, -1.0, w, s);
         gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s);
-        CK(cudaMemsetAsync(cx.flags, 0, sizeof(int), s));
+        // the Givens step stores its flags (any system still active, a
+        // non-finite coefficient) straight into pinned host memory, in the
+        // ring slot of this step; the host cleared the slot, whose previous
+        // step (j - kRing) it has already read
+        const int slot = j % kRing;
+        volatile int* hf = pb->h_pinned + 2 + 2 * slot;
+        hf[0] = 0;
+        hf[1] = 0;
+        int* df = pb->d_hpinned + 2 + 2 * slot;
         gm_givens(d, j, cx.h1, cx.h2, cx.hstride, cx.wn2, cx.wn2b, cx.skip2, cx.tol_cycle, cx.H, cx.cs, cx.sn,
-                  cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, cx.flags, cx.flags + 1, cx.rdiag,
+                  cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, df, df + 1, cx.rdiag,
                   sizeof(V) == sizeof(float2), s);
         gm_scale<V, V>(d, ch, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
         CK_LAUNCH();
-        const int slot = j % kRing;
-        CK(cudaMemcpyAsync(pb->h_pinned + 2 + 2 * slot, cx.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaEventRecord(pb->ring_ev[slot], s));
     }
     // settle: the last queued steps decide whether any system is still active
@@ -1547,6 +1554,7 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             pb->d_flags = dalloc<int>(4);
             CK(cudaMemsetAsync(pb->d_flags, 0, 4 * sizeof(int), pb->stream));
             CK(cudaMallocHost((void**)&pb->h_pinned, 64));
+            CK(cudaHostGetDevicePointer((void**)&pb->d_hpinned, pb->h_pinned, 0));
             for (auto& e : pb->ring_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             // reduction chunks: at least 512 rows each (two or more rows per
             // thread of a reduction block) and about 256 overall, never
