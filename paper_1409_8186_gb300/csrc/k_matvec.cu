@@ -43,9 +43,35 @@ template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 
-// Shared-memory footprint (elements) of one stage.
-__host__ __device__ inline int stage_g_elems(int L, int KB) { return MSD_TILE_P * (L + 2 * KB); }
-__host__ __device__ inline int stage_x_elems(int n, int RT, int KB) { return ((n + KB - 1) / KB) * KB * RT; }
+// Shared-memory footprint (elements) of one stage: the 32 generator rows
+// contiguous (as in HBM) between kGFront zeros before and kGBack zeros after
+// (the register window reaches up to KB - 1 <= 8 values past either end of a
+// row; past a row's end it reads the next row, which only ever meets zero
+// source values or padded target modes), then the source slab, rounded to
+// 16 bytes.
+constexpr int kGFront = 8, kGBack = 16;
+__host__ __device__ inline int stage_g_elems(int L, int KB) { return MSD_TILE_P * L + kGFront + kGBack; }
+__host__ __device__ inline int stage_x_elems(int n, int RT, int KB) {
+    return (((n + KB - 1) / KB) * KB * RT + 1) & ~1;
+}
+
+__device__ int g_bt_status;  // bit 0: a wait for a bulk copy of generators expired
+constexpr long long kBtWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ bool bt_mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kBtWaitCycles) return false;
+    }
+}
 
 // Complex multiply-accumulate policies over a KB x RB register tile.
 // Mac4: the textbook product, 4 real FMAs per complex MAC (FP32 path).
@@ -147,13 +173,13 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
                                                    const int* __restrict__ live) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* smem = reinterpret_cast<V*>(smem_raw);
+    __shared__ __align__(8) uint64_t gfull[2];  // generator bulk copy of stage s landed
 
     const int wi = blockIdx.x / rtiles;
     const int rt = blockIdx.x % rtiles;
     const MatvecWork w = works[wi];
     const MsdConfig c = cfgs[w.cfg];
     const int N = c.N, n = c.n, L = c.L;
-    const int Ls = L + 2 * KB;
     const int I = (n + KB - 1) / KB;
     const int npad = I * KB;
     const int gsz = stage_g_elems(L, KB), xsz = stage_x_elems(n, RT, KB);
@@ -194,29 +220,41 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
 
     // zero the padding of the stages once (staging never writes it)
     for (int s = 0; s < S; ++s) {
-        for (int t = tid; t < MSD_TILE_P * 2 * KB; t += nthreads) {
-            const int row = t / (2 * KB), j = t % (2 * KB);
-            const int pos = j < KB ? j : (L + j);
-            gbuf[s][row * Ls + pos] = vzero<V>();
-        }
+        for (int t = tid; t < kGFront + kGBack; t += nthreads)
+            gbuf[s][t < kGFront ? t : MSD_TILE_P * L + t] = vzero<V>();
         for (int t = n * RT + tid; t < npad * RT; t += nthreads) xbuf[s][t] = vzero<V>();
     }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gfull[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
 
+    // The 32 generator rows of a source are contiguous in HBM (32 L values):
+    // one thread moves them with a single bulk copy that completes on the
+    // stage's mbarrier.  Tiles that do not start on 16 bytes (never for the
+    // layouts the library builds, whose offsets are even) are staged by
+    // every thread with cp.async instead; alignment is the same for every
+    // source of a CTA, so the choice is made once.
     const V* gsrc_cfg = G + c.gen_off + (long long)w.p0 * L;
+    const unsigned gbytes = (unsigned)(MSD_TILE_P * L * sizeof(V));
+    const bool bulk = (((uintptr_t)gsrc_cfg) & 15) == 0 && (((long long)c.Mp * L * sizeof(V)) & 15) == 0;
     auto stage = [&](int q, int s) {
         const V* src = gsrc_cfg + (long long)q * c.Mp * L;
-        V* dst = gbuf[s] + KB;
-        // row-major walk of the 32 x L tile: (row, j) advanced incrementally
-        int row = tid / L, j = tid - (tid / L) * L;
-        const int drow = nthreads / L, dj = nthreads - drow * L;
-        for (int t = tid; t < MSD_TILE_P * L; t += nthreads) {
-            cp_async(dst + row * Ls + j, src + t);
-            row += drow;
-            j += dj;
-            if (j >= L) {
-                j -= L;
-                ++row;
+        V* dst = gbuf[s] + kGFront;
+        if (bulk) {
+            if (tid == 0) {
+                const uint32_t bar = smem_u32(&gfull[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(gbytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(dst)),
+                    "l"(src), "r"(gbytes), "r"(bar)
+                    : "memory");
             }
+        } else {
+            for (int t = tid; t < MSD_TILE_P * L; t += nthreads) cp_async(dst + t, src + t);
         }
         const V* xsrc = xs + (c.row_off + (long long)q * n) * R + col0;
         V* xd = xbuf[s];
@@ -232,7 +270,8 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
 
     if (S == 2 && w.q0 < w.q1) stage(w.q0, 0);
     cp_commit();
-    const int base = KB + 2 * N - m0;  // smem position of l' = n - m0 + 2N at n = 0
+    const int base = kGFront + 2 * N - m0;  // smem position of l' = n - m0 + 2N at n = 0 (row 0)
+    bool waits_ok = true;
     for (int it = 0, q = w.q0; q < w.q1; ++it, ++q) {
         if (S == 2) {
             if (q + 1 < w.q1) stage(q + 1, (it + 1) & 1);
@@ -243,10 +282,13 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
             cp_commit();
             cp_wait<0>();
         }
-        __syncthreads();
         const int sb = S == 2 ? (it & 1) : 0;
+        // use number of stage sb: it / 2 (two stages) or it (one stage)
+        if (bulk && waits_ok)
+            waits_ok = bt_mbar_wait(smem_u32(&gfull[sb]), (uint32_t)((S == 2 ? (it >> 1) : it) & 1));
+        __syncthreads();
         if (mact) {
-            const V* gs = gbuf[sb] + lane * Ls + base;
+            const V* gs = gbuf[sb] + lane * L + base;
             const V* xsl = xbuf[sb] + c0;
             typename Mac::G win[KB];
 #pragma unroll
@@ -269,6 +311,8 @@ __global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__
         __syncthreads();
     }
     cp_wait<0>();
+    // an expired wait: the partial sums are not valid; the host reports it
+    if (!waits_ok) atomicOr(&g_bt_status, 1);
 
     const int p = w.p0 + lane;
     if (mact && p < c.M) {
@@ -477,6 +521,16 @@ void dispatch(const Choice& c, bool fp64, F&& f) {
 }  // namespace
 
 MatvecChoice matvec_default_choice(int R, int Nmax, bool fp64) { return choose(R, Nmax, fp64); }
+
+int bt_status_and_clear() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bt_status, sizeof(int)) != cudaSuccess) return -1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_bt_status, &z, sizeof(int));
+    }
+    return v;
+}
 
 // Every instantiated tile shape that fits this (R, N): FP64 KB = 4..7 with
 // RT = 1; FP32 KB = 4..9 with each column tile RT in {1, 2, 4, 8, 16} that

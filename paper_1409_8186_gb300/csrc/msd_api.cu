@@ -270,6 +270,7 @@ void check_tc(const char* where) {
     const int t = tc_status_and_clear();
     const int u = tcs_status_and_clear();
     if (t > 0 || u > 0) fail(MSD_ERR_CUDA, std::string(where) + ": a tensor-core pipeline wait expired");
+    if (bt_status_and_clear() > 0) fail(MSD_ERR_CUDA, std::string(where) + ": a generator bulk-copy wait expired");
 }
 
 void check_flags(msd_problem* pb, const char* where) {
@@ -1372,9 +1373,14 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
                 // on the rounding of the inner product)
                 if (relres[i] < (1.0 - 1e-3) * prev[i]) improved = true;
             }
-            // FP32 sweeps aim 20x below the stopping tolerance, so that the
-            // rounding of the FP32 correction cannot leave a system just above it
-            tol_cycle[i] = mixed ? std::max(0.05 * tol_abs[i], o.inner_tol * rn) : tol_abs[i];
+            // An FP32 sweep stops at inner_tol times its starting residual,
+            // and not below the stopping tolerance: deeper, its estimate runs
+            // ahead of the true residual, which FP32 rounding holds back.  A
+            // sweep that starts within 2x of the tolerance aims 20x below it,
+            // so that the rounding of its correction cannot leave the system
+            // just above the tolerance.
+            const double floor_abs = (rn <= 2.0 * tol_abs[i] ? 0.05 : 1.0) * tol_abs[i];
+            tol_cycle[i] = mixed ? std::max(floor_abs, o.inner_tol * rn) : tol_abs[i];
         }
         if (all) break;
         if (mixed && sweeps > 0 && !improved) {

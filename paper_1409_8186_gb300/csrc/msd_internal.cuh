@@ -137,6 +137,8 @@ void launch_tcs_build_gt(const MsdConfig* d_cfg, int C, const long long* d_blk_o
                          const float2* G32, float* GT, cudaStream_t s);
 void launch_tcs_prep_x(const MsdConfig* d_cfg, int C, long long rows4, int R, const float* rf, const float2* x,
                        float* XT, cudaStream_t s);
+// bit 0 set (and cleared): a bulk-copy wait of the CUDA-core product expired
+int bt_status_and_clear();
 int tcs_status_and_clear();
 // Set by msd_test_expire_waits: kernels with bounded waits take their
 // expiry path once per launch (tests of the error path; no fault involved).
