@@ -388,12 +388,12 @@ constexpr int kKbMax32 = 9;
 
 using Choice = MatvecChoice;
 
-// Two FP64 stages of the CUDA-core kernel (32 generator rows of L + 2 KB
-// values and the padded source column, complex128) exceed 227 KB.
+// Two FP64 stages of the CUDA-core kernel (32 generator rows of L values
+// with their guards, and the padded source column, complex128) exceed the
+// shared memory of a CTA.
 bool f64_one_stage(int Nmax, int KB) {
     const int n = 2 * Nmax + 1, L = 4 * Nmax + 1;
-    const int npad = (n + KB - 1) / KB * KB;
-    return 2 * (size_t)(MSD_TILE_P * (L + 2 * KB) + npad) * 16 > 227 * 1024;
+    return 2 * (size_t)(stage_g_elems(L, KB) + stage_x_elems(n, 1, KB)) * 16 > kMatvecSmemCap;
 }
 
 Choice choose(int R, int Nmax, bool fp64) {
@@ -434,7 +434,7 @@ struct Bt {
         static bool done = false;
         if (!done) {
             cudaFuncSetAttribute(k_bt_matvec<V, RT, RB, KB, P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024);
+                                 (int)kMatvecSmemCap);
             done = true;
         }
     }
@@ -483,7 +483,7 @@ void with_f32(const Choice& c, F&& f) {
     else with_f32_p<KB, 0>(c, f);
 }
 
-// FP64: two stages when they fit in 227 KB of shared memory, else one
+// FP64: two stages when they fit in the shared memory of a CTA, else one
 // (choice field I holds ceil(n / KB); c.ONE selects the one-stage kernel).
 template <int KB, typename F>
 void with_f64(const Choice& c, F&& f) {
@@ -551,7 +551,7 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bo
                 if (fp64) c.ONE = f64_one_stage(Nmax, KB) ? 1 : 0;
                 size_t b = 0;
                 dispatch(c, fp64, [&](auto k) { b = decltype(k)::smem(Nmax); });
-                if (b > 227 * 1024) continue;
+                if (b > kMatvecSmemCap) continue;
                 if (cnt < cap) out[cnt] = c;
                 ++cnt;
             }

@@ -887,7 +887,7 @@ void matvec_recompute_dev(msd_problem* pb, int R, bool fp64, const void* x, void
 // product over 2R columns (sqrt(a) J x | sqrt(a) J' x) with the stored
 // generators, then y = x + l1 z1 + l2 z2.
 void matvec_form_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
-    if (matvec_smem_bytes(matvec_default_choice(2 * R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
+    if (matvec_smem_bytes(matvec_default_choice(2 * R, pb->Nmax, fp64), pb->Nmax, fp64) > kMatvecSmemCap)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     ensure_generators(pb, fp64);
     MatvecPlan& plan = get_plan(pb, 2 * R, fp64);
@@ -909,7 +909,7 @@ void matvec_form_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) 
 // y = x + A [z+; z-].
 void pen_matvec(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
     msd_problem* pm = pb->pen_minus;
-    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
+    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > kMatvecSmemCap)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     ensure_generators(pb, fp64);
     ensure_generators(pm, fp64);
@@ -942,7 +942,7 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
         matvec_form_dev(pb, R, fp64, x, y);
         return;
     }
-    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
+    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > kMatvecSmemCap)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     if (pb->gen_mode == MSD_GEN_RECOMPUTE) {
         matvec_recompute_dev(pb, R, fp64, x, y);
@@ -1026,7 +1026,7 @@ void ensure_adjoint(msd_problem* pb, bool fp64) {
 //   raw forward: y = T(r .* x)    raw adjoint: y = T^H(conj(l) .* x)
 void product_dev(msd_problem* pb, int R, bool fp64, bool adjoint, bool raw, const void* x, void* y) {
     if (pb->form) fail(MSD_ERR_ARG, "adjoint and raw products need the default formulation");
-    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > 227 * 1024)
+    if (matvec_smem_bytes(matvec_default_choice(R, pb->Nmax, fp64), pb->Nmax, fp64) > kMatvecSmemCap)
         fail(MSD_ERR_ARG, "truncation order too large for the shared-memory tile of this precision");
     if (adjoint) ensure_adjoint(pb, fp64);
     else ensure_generators(pb, fp64);
@@ -2480,7 +2480,7 @@ extern "C" msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, 
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: the generators of this precision are not built yet "
                               "(call msd_matvec or msd_solve_planewaves once first)");
         const MatvecChoice dc = matvec_default_choice(R, pb->Nmax, fp64);
-        if (matvec_smem_bytes(dc, pb->Nmax, fp64) > 227 * 1024)
+        if (matvec_smem_bytes(dc, pb->Nmax, fp64) > kMatvecSmemCap)
             fail(MSD_ERR_ARG, "msd_matvec_noalloc: truncation order too large for the shared-memory tile");
         unsigned char* base = (unsigned char*)static_scratch_address();
         // layout: [work list][xs][partials], each 256-byte aligned

@@ -137,6 +137,9 @@ void launch_tcs_build_gt(const MsdConfig* d_cfg, int C, const long long* d_blk_o
                          const float2* G32, float* GT, cudaStream_t s);
 void launch_tcs_prep_x(const MsdConfig* d_cfg, int C, long long rows4, int R, const float* rf, const float2* x,
                        float* XT, cudaStream_t s);
+// Dynamic shared memory of one CUDA-core product CTA at most (227 KB per
+// CTA less the kernel's static mbarriers, rounded down to 1 KB).
+constexpr size_t kMatvecSmemCap = 226 * 1024;
 // bit 0 set (and cleared): a bulk-copy wait of the CUDA-core product expired
 int bt_status_and_clear();
 int tcs_status_and_clear();
