@@ -88,7 +88,7 @@ typedef struct {
     int restart;       /* GMRES restart length m          [auto: as long as HBM allows] */
     int maxit;         /* limit on Arnoldi steps over the whole solve       [3000]    */
     int max_refine;    /* MSD_MIXED: limit on FP64 refinement sweeps        [60]      */
-    double inner_tol;  /* MSD_MIXED: relative tolerance of each FP32 sweep  [2e-6]    */
+    double inner_tol;  /* MSD_MIXED: relative tolerance of each FP32 sweep  [5e-6]    */
     int precision;     /* MSD_FP64 (all FP64) or MSD_MIXED                  [FP64]    */
     int gen_mode;      /* MSD_GEN_*: generators stored in HBM or recomputed [auto]    */
 } msd_opts;

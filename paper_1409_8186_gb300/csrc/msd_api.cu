@@ -1260,7 +1260,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
         o.restart = (int)std::max<long long>(m, 10);
     }
     if (o.max_refine <= 0) o.max_refine = 60;
-    if (o.inner_tol <= 0) o.inner_tol = 2e-6;
+    if (o.inner_tol <= 0) o.inner_tol = 5e-6;
     if (o.precision != MSD_FP64 && o.precision != MSD_MIXED) fail(MSD_ERR_ARG, "msd_solve_planewaves: precision");
     const bool mixed = o.precision == MSD_MIXED;
     cudaStream_t s = pb->stream;
@@ -1376,10 +1376,10 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
             // An FP32 sweep stops at inner_tol times its starting residual,
             // and not below the stopping tolerance: deeper, its estimate runs
             // ahead of the true residual, which FP32 rounding holds back.  A
-            // sweep that starts within 2x of the tolerance aims 20x below it,
-            // so that the rounding of its correction cannot leave the system
-            // just above the tolerance.
-            const double floor_abs = (rn <= 2.0 * tol_abs[i] ? 0.05 : 1.0) * tol_abs[i];
+            // sweep that starts within 2x of the tolerance aims at half of
+            // it, so that the rounding of its correction cannot leave the
+            // system just above the tolerance.
+            const double floor_abs = (rn <= 2.0 * tol_abs[i] ? 0.5 : 1.0) * tol_abs[i];
             tol_cycle[i] = mixed ? std::max(floor_abs, o.inner_tol * rn) : tol_abs[i];
         }
         if (all) break;
