@@ -124,78 +124,165 @@ __global__ void k_dots_part(const RowChunk* __restrict__ chunks, int R, const V*
 // per lane (Q = 1) or alternating between two columns (Q = 2, R = 64); lanes
 // that hold the same column are folded by shuffles.  No block-level
 // reduction: blocks are independent groups of eight vectors.
+// Reduction of the chunk partials fused into the projection kernel (few
+// systems): the last block of each group of vectors to finish sums that
+// group's partials into out; with skip2 set, the last group to finish also
+// takes the re-orthogonalisation decision (k_reorth_flags).  Counters start
+// at zero and every last block puts its counter back to zero.
+struct DotsFuse {
+    int* cnt = nullptr;      // [gridDim.y] blocks finished per vector group (nullptr: no fusion)
+    int* cnt_all = nullptr;  // vector groups finished
+    const int* cfg_chunk_off = nullptr;
+    int S = 0;
+    double2* out = nullptr;
+    int ostride = 0;
+    // re-orthogonalisation flags (first projection only)
+    int j = 0;
+    double2* wn2 = nullptr;
+    const int* active = nullptr;
+    int* skip2 = nullptr;
+};
+
+// ||w'||^2 = ||w||^2 - sum_{i <= j} |h_i|^2 and the flag of one system,
+// reduced over the CTA (every thread calls it).
+__device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, int* skip2) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 v = __ldcg(h + i);
+        acc += cabs2(v);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ double red[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ss = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) ss += red[k];
+        const double before = __ldcg(h + j + 1).x;  // ||w||^2 before the projection
+        const double after = before - ss;
+        *wn2 = make_double2(after, 0.0);
+        *skip2 = !(act && after < 0.5 * before);
+    }
+}
+
 template <typename V, int Q>
 __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restrict__ chunks, int R,
                                                         const V* __restrict__ Vb, long long vstride, int nv,
                                                         int self, const V* __restrict__ w,
                                                         const int* __restrict__ skip, int skipval,
-                                                        double2* __restrict__ part) {
+                                                        double2* __restrict__ part, DotsFuse fz) {
     const RowChunk ch = chunks[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.y * (kThreads / 32) + warp;
     const int nvv = nv + self;
-    if (i >= nvv) return;  // a whole warp
-    const V* u = i < nv ? Vb + (long long)i * vstride : w;
     const long long e0 = ch.row0 * R, e1 = ch.row1 * R;
-    // systems with skip set (no second projection) need no sums: a warp whose
-    // columns are all skipped only writes its zeros
-    if (skip) {
-        bool live = false;
+    if (i < nvv) {  // a whole warp
+        const V* u = i < nv ? Vb + (long long)i * vstride : w;
+        // systems with skip set (no second projection) need no sums: a warp
+        // whose columns are all skipped only writes its zeros
+        bool live = true;
+        if (skip) {
+            live = false;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) live |= skip[ch.cfg * R + (int)((e0 + lane + 32 * q) % R)] != skipval;
-        if (!__any_sync(0xffffffffu, live)) {
+            for (int q = 0; q < Q; ++q) live |= skip[ch.cfg * R + (int)((e0 + lane + 32 * q) % R)] != skipval;
+            live = __any_sync(0xffffffffu, live);
+            if (!live) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (Q == 2 || lane < R)
-                    part[((long long)blockIdx.x * nvv + i) * R + (int)((e0 + lane + 32 * q) % R)] =
-                        make_double2(0.0, 0.0);
-            return;
+                for (int q = 0; q < Q; ++q)
+                    if (Q == 2 || lane < R)
+                        part[((long long)blockIdx.x * nvv + i) * R + (int)((e0 + lane + 32 * q) % R)] =
+                            make_double2(0.0, 0.0);
+            }
+        }
+        if (live) {
+            typedef decltype(V{}.x) A;
+            A ax[Q], ay[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) ax[q] = ay[q] = A(0);
+            constexpr int U = 8;  // a multiple of Q: the column phase of k survives the stride
+            long long e = e0 + lane;
+            for (; e + 32LL * (U - 1) < e1; e += 32LL * U) {
+                V uv[U], wv[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    uv[k] = u[e + 32LL * k];
+                    wv[k] = w[e + 32LL * k];
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const int q = k % Q;
+                    ax[q] = fma(uv[k].x, wv[k].x, fma(uv[k].y, wv[k].y, ax[q]));  // conj(u) * w
+                    ay[q] = fma(uv[k].x, wv[k].y, fma(-uv[k].y, wv[k].x, ay[q]));
+                }
+            }
+            for (int k = 0; e < e1; e += 32, ++k) {
+                const V uv = u[e], wv = w[e];
+                if (Q == 2 && (k & 1)) {
+                    ax[Q - 1] = fma(uv.x, wv.x, fma(uv.y, wv.y, ax[Q - 1]));
+                    ay[Q - 1] = fma(uv.x, wv.y, fma(-uv.y, wv.x, ay[Q - 1]));
+                } else {
+                    ax[0] = fma(uv.x, wv.x, fma(uv.y, wv.y, ax[0]));
+                    ay[0] = fma(uv.x, wv.y, fma(-uv.y, wv.x, ay[0]));
+                }
+            }
+            if (Q == 1) {
+                for (int off = 16; off >= R; off >>= 1) {
+                    ax[0] += __shfl_xor_sync(0xffffffffu, ax[0], off);
+                    ay[0] += __shfl_xor_sync(0xffffffffu, ay[0], off);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                if (Q == 1 && lane >= R) break;
+                const int r = (int)((e0 + lane + 32 * q) % R);
+                const bool sk = skip && skip[ch.cfg * R + r] == skipval;
+                part[((long long)blockIdx.x * nvv + i) * R + r] =
+                    sk ? make_double2(0.0, 0.0) : make_double2((double)ax[q], (double)ay[q]);
+            }
         }
     }
-    typedef decltype(V{}.x) A;
-    A ax[Q], ay[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) ax[q] = ay[q] = A(0);
-    constexpr int U = 8;  // a multiple of Q: the column phase of k survives the stride
-    long long e = e0 + lane;
-    for (; e + 32LL * (U - 1) < e1; e += 32LL * U) {
-        V uv[U], wv[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            uv[k] = u[e + 32LL * k];
-            wv[k] = w[e + 32LL * k];
+    if (!fz.cnt) return;
+    // ---- fused reduction of this vector group (last block of the group)
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&fz.cnt[blockIdx.y], 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    constexpr int WPB = kThreads / 32;
+    const int ib = blockIdx.y * WPB;
+    for (int o = warp; o < fz.S * WPB; o += WPB) {
+        const int sy = o / WPB, iv = ib + o % WPB;
+        if (iv >= nvv) continue;  // a whole warp
+        const int c = sy / R, r = sy % R;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = fz.cfg_chunk_off[c] + lane; k < fz.cfg_chunk_off[c + 1]; k += 32) {
+            const double2 v = __ldcg(part + ((long long)k * nvv + iv) * R + r);
+            acc.x += v.x;
+            acc.y += v.y;
         }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int q = k % Q;
-            ax[q] = fma(uv[k].x, wv[k].x, fma(uv[k].y, wv[k].y, ax[q]));  // conj(u) * w
-            ay[q] = fma(uv[k].x, wv[k].y, fma(-uv[k].y, wv[k].x, ay[q]));
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
         }
+        if (lane == 0) fz.out[(long long)sy * fz.ostride + iv] = acc;
     }
-    for (int k = 0; e < e1; e += 32, ++k) {
-        const V uv = u[e], wv = w[e];
-        if (Q == 2 && (k & 1)) {
-            ax[Q - 1] = fma(uv.x, wv.x, fma(uv.y, wv.y, ax[Q - 1]));
-            ay[Q - 1] = fma(uv.x, wv.y, fma(-uv.y, wv.x, ay[Q - 1]));
-        } else {
-            ax[0] = fma(uv.x, wv.x, fma(uv.y, wv.y, ax[0]));
-            ay[0] = fma(uv.x, wv.y, fma(-uv.y, wv.x, ay[0]));
-        }
-    }
-    if (Q == 1) {
-        for (int off = 16; off >= R; off >>= 1) {
-            ax[0] += __shfl_xor_sync(0xffffffffu, ax[0], off);
-            ay[0] += __shfl_xor_sync(0xffffffffu, ay[0], off);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        if (Q == 1 && lane >= R) break;
-        const int r = (int)((e0 + lane + 32 * q) % R);
-        const bool sk = skip && skip[ch.cfg * R + r] == skipval;
-        part[((long long)blockIdx.x * nvv + i) * R + r] =
-            sk ? make_double2(0.0, 0.0) : make_double2((double)ax[q], (double)ay[q]);
-    }
+    if (threadIdx.x == 0) fz.cnt[blockIdx.y] = 0;
+    if (!fz.skip2) return;
+    // ---- re-orthogonalisation flags (last vector group to finish)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(fz.cnt_all, 1) == (int)gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int sy = 0; sy < fz.S; ++sy)
+        reorth_flag_cta(fz.out + (long long)sy * fz.ostride, fz.j, fz.wn2 + (long long)sy * fz.ostride,
+                        fz.active[sy], fz.skip2 + sy);
+    if (threadIdx.x == 0) *fz.cnt_all = 0;
 }
 
 // out[s * ostride + i] = sum over the chunks of cfg(s) of part[chunk][i][r]
@@ -445,6 +532,16 @@ __global__ void __launch_bounds__(kGivensThreads) k_givens(int m, int j, const d
         if (second) v = cadd(v, b[i]);
         return v;
     };
+    // operands of the tail, loaded before the reduction so that their
+    // latency overlaps it (thread 0 finishes the step)
+    double wn = 0.0, tol = 0.0;
+    double2 h0 = make_double2(0.0, 0.0), gj = make_double2(0.0, 0.0);
+    if (tid == 0) {
+        wn = second ? wn2b[(long long)s * hstride].x : wn2a[(long long)s * hstride].x;
+        tol = tol_cycle[s];
+        h0 = hval(0);
+        gj = g[(long long)s * (m + 1) + j];
+    }
     for (int i = tid; i <= j; i += T) Hc[i] = hval(i);  // raw column
     // segment of rotations [lo, hi) owned by this thread
     const int per = (j + T - 1) / T;
@@ -460,41 +557,44 @@ __global__ void __launch_bounds__(kGivensThreads) k_givens(int m, int j, const d
     seg = tid < nw ? red[tid] : AffOps<Map>::id();
     seg = warp_compose(seg);
     if (tid != 0) return;
-    const double2 hjj = AffOps<Map>::apply(seg, hval(0));
-    const double wn = second ? wn2b[(long long)s * hstride].x : wn2a[(long long)s * hstride].x;
-    const double hn = sqrt(fmax(wn, 0.0));
-    const double ajj = sqrt(cabs2(hjj));
-    const double den = hypot(ajj, hn);
+    const double2 hjj = AffOps<Map>::apply(seg, h0);
+    // rotation c = |hjj| / den, s = (hjj / |hjj|) hn / den, den^2 = |hjj|^2 + hn^2,
+    // from reciprocal square roots (the FP64 pipe of this GPU is narrow, and
+    // this chain runs on one thread): 1/|hjj|, 1/den, 1/hn
+    wn = fmax(wn, 0.0);
+    const double a2 = cabs2(hjj);
+    const double rw = wn > 0.0 ? rsqrt(wn) : 0.0;
+    const double hn = wn * rw;
     double2 c, sv;
-    if (den == 0.0) {
+    if (a2 + wn == 0.0) {
         c = make_double2(1.0, 0.0);
         sv = make_double2(0.0, 0.0);
-    } else if (ajj == 0.0) {
+    } else if (a2 == 0.0) {
         c = make_double2(0.0, 0.0);
         sv = make_double2(1.0, 0.0);  // hn real and positive
     } else {
-        const double2 ph = cscale(hjj, 1.0 / ajj);
-        c = make_double2(ajj / den, 0.0);
-        sv = cscale(ph, hn / den);  // ph * conj(hn) / den, hn real
+        const double ra = rsqrt(a2), rd = rsqrt(a2 + wn);
+        c = make_double2(a2 * ra * rd, 0.0);
+        sv = cscale(hjj, hn * ra * rd);  // ph * conj(hn) / den, hn real
     }
     cs[(long long)s * m + j] = c;
     sn[(long long)s * m + j] = sv;
     const double2 rjj = cadd(cscale(hjj, c.x), cscale(sv, hn));
     rdiag[(long long)s * m + j] = make_double2(hn, 0.0);  // R_jj is formed in FP64 at the end of the cycle
     double2* gs = g + (long long)s * (m + 1);
-    const double2 gj = gs[j];
-    gs[j + 1] = cscale(cmul(cconj(sv), gj), -1.0);
+    const double2 gn = cscale(cmul(cconj(sv), gj), -1.0);
+    gs[j + 1] = gn;
     gs[j] = cscale(gj, c.x);
     iters[s] += 1;
-    const double res = sqrt(cabs2(gs[j + 1]));
-    const bool bad = !isfinite(res) || !isfinite(rjj.x) || !isfinite(rjj.y);
+    const double res2 = cabs2(gn);  // squared residual estimate
+    const bool bad = !isfinite(res2) || !isfinite(rjj.x) || !isfinite(rjj.y);
     if (bad) *nonfinite = 1;  // every writer stores the same value (the flag may live in host memory)
-    if (bad || res <= tol_cycle[s] || hn == 0.0 || j + 1 == m) {
+    if (bad || res2 <= tol * tol || hn == 0.0 || j + 1 == m) {
         active[s] = 0;
         kconv[s] = j + 1;
         vscale[s] = 0.0;
     } else {
-        vscale[s] = 1.0 / hn;
+        vscale[s] = rw;
         *any_active = 1;
     }
 }
@@ -574,24 +674,48 @@ inline unsigned rgroups(int R) { return (unsigned)((R + col_lanes(R) - 1) / col_
 // ---------------------------------------------------------------- host wrappers
 
 template <typename V>
-void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
+bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
              int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
-             cudaStream_t s, int skipval) {
+             cudaStream_t s, int skipval, const GmDotsFuse* fuse) {
     const int nvv = nv + self;
     constexpr int WPB = kThreads / 32;
+    const bool warp_kernel = 32 % d.R == 0 || d.R == 64;
+    // fused reduction: few systems (the last block of a vector group sums
+    // S * 8 outputs) and counters for every vector group
+    const bool fused = fuse && warp_kernel && d.S <= kFuseMaxSystems && (nvv + WPB - 1) / WPB <= fuse->ncnt;
+    DotsFuse fz;
+    if (fused) {
+        fz.cnt = fuse->cnt;
+        fz.cnt_all = fuse->cnt + fuse->ncnt;
+        fz.cfg_chunk_off = cfg_chunk_off;
+        fz.S = d.S;
+        fz.out = out;
+        fz.ostride = ostride;
+        if (fuse->skip2) {
+            fz.j = fuse->j;
+            fz.wn2 = fuse->wn2;
+            fz.active = fuse->active;
+            fz.skip2 = fuse->skip2;
+        }
+    }
     if (32 % d.R == 0) {
         k_dots_warp<V, 1><<<dim3(d.nchunk, (nvv + WPB - 1) / WPB), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv,
-                                                                                    self, w, skip, skipval, part);
+                                                                                    self, w, skip, skipval, part, fz);
     } else if (d.R == 64) {
         k_dots_warp<V, 2><<<dim3(d.nchunk, (nvv + WPB - 1) / WPB), kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv,
-                                                                                    self, w, skip, skipval, part);
+                                                                                    self, w, skip, skipval, part, fz);
     } else {
         dim3 g(d.nchunk, rgroups(d.R), (nvv + kI - 1) / kI);
         k_dots_part<V><<<g, kThreads, 0, s>>>(chunks, d.R, Vb, vstride, nv, self, w, skip, skipval, part);
     }
+    if (fused) {
+        g_msd_launches += 1;
+        return true;
+    }
     const long long tot = (long long)d.S * nvv;
     k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
     g_msd_launches += 2;
+    return false;
 }
 
 template <typename V, typename W>
@@ -661,10 +785,12 @@ void gm_zero(long long n, double2* x, cudaStream_t s) {
     g_msd_launches += 1;
 }
 
-template void gm_dots<double2>(const GmresDims&, const RowChunk*, const int*, const double2*, long long, int, int,
-                               const double2*, const int*, double2*, double2*, int, cudaStream_t, int);
-template void gm_dots<float2>(const GmresDims&, const RowChunk*, const int*, const float2*, long long, int, int,
-                              const float2*, const int*, double2*, double2*, int, cudaStream_t, int);
+template bool gm_dots<double2>(const GmresDims&, const RowChunk*, const int*, const double2*, long long, int, int,
+                               const double2*, const int*, double2*, double2*, int, cudaStream_t, int,
+                               const GmDotsFuse*);
+template bool gm_dots<float2>(const GmresDims&, const RowChunk*, const int*, const float2*, long long, int, int,
+                              const float2*, const int*, double2*, double2*, int, cudaStream_t, int,
+                              const GmDotsFuse*);
 template void gm_update<double2, double2>(const GmresDims&, const RowChunk*, const double2*, long long, int,
                                           const double2*, int, const int*, double, double2*, cudaStream_t, int);
 template void gm_update<float2, float2>(const GmresDims&, const RowChunk*, const float2*, long long, int,

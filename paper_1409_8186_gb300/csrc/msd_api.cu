@@ -1102,6 +1102,8 @@ struct SolveCtx {
     double2 *h1, *h2, *wn2, *wn2b, *H, *cs, *sn, *g, *y, *lsq_work, *rdiag;
     double *beta, *vscale, *tol_abs, *tol_cycle;
     int *active, *kconv, *iters, *skip2, *flags;  // flags[0] any_active, flags[1] nonfinite
+    int* cnt = nullptr;  // ncnt + 1 counters of the fused projection reductions (zero between launches)
+    int ncnt = 0;
     int hstride;
     double2* part;  // [nchunk][m + 2][R] reduction partials
     bool adjoint = false;  // solve with (P^-1 A)^H
@@ -1112,6 +1114,10 @@ void norm2_f64(SolveCtx& cx, const double2* u, double2* out) {
     gm_dots<double2>(cx.d, cx.pb->d_chunks, cx.pb->d_cfg_chunk_off, nullptr, 0, 0, 1, u, nullptr, cx.part, out,
                      cx.hstride, cx.pb->stream);
 }
+
+// Counters of the fused projection reductions: one per group of eight
+// basis vectors (bases of up to 4000 vectors plus w), and one more.
+constexpr int kDotsCounters = 512;
 
 // Basis size from which projections run over the coarse row chunks.
 constexpr int kCoarseFrom = 64;
@@ -1173,13 +1179,23 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         const int* cob = coarse ? pb->d_cfg_chunk_off_coarse : co;
         // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1;
         // systems that have converged (zero vectors from here on) are skipped
-        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, cx.active, cx.part, cx.h1, cx.hstride, s, 0);
+        // (few systems: the reductions, and the flags of the second
+        // projection, run inside the projection kernels)
+        GmDotsFuse fz1, fz;
+        fz1.cnt = fz.cnt = cx.cnt;
+        fz1.ncnt = fz.ncnt = cx.ncnt;
+        fz1.j = j;
+        fz1.wn2 = cx.wn2;
+        fz1.active = cx.active;
+        fz1.skip2 = cx.skip2;
+        const bool flags_done =
+            gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, cx.active, cx.part, cx.h1, cx.hstride, s, 0, &fz1);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, cx.active, -1.0, w, s, 0);
         // second projection only where the first removed more than half of ||w||^2
-        gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
-        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s);
+        if (!flags_done) gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
+        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s, 1, &fz);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h2, cx.hstride, cx.skip2, -1.0, w, s);
-        gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s);
+        gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s, 1, &fz);
         // the Givens step stores its flags (any system still active, a
         // non-finite coefficient) straight into pinned host memory, in the
         // ring slot of this step; the host cleared the slot, whose previous
@@ -1300,12 +1316,15 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     cx.vscale = dsys + S;
     cx.tol_abs = dsys + 2 * S;
     cx.tol_cycle = dsys + 3 * S;
-    int* isys = (int*)sb((size_t)(S * 4 + 2) * 4);
+    int* isys = (int*)sb((size_t)(S * 4 + 2 + kDotsCounters + 1) * 4);
     cx.active = isys;
     cx.kconv = isys + S;
     cx.iters = isys + 2 * S;
     cx.skip2 = isys + 3 * S;
     cx.flags = isys + 4 * S;
+    cx.cnt = isys + 4 * S + 2;
+    cx.ncnt = kDotsCounters;
+    CK(cudaMemsetAsync(cx.cnt, 0, (size_t)(cx.ncnt + 1) * sizeof(int), s));
     const size_t velem = mixed ? 8 : 16;
     void* Vb = sb((size_t)(m + 1) * nv * velem);
     void* w = sb(nv * velem);

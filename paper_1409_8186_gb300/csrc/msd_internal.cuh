@@ -382,10 +382,26 @@ struct GmresDims {
 // (and w itself when self = 1); systems with skip[s] == skipval get zeros
 // (skipval 1 with a skip-flag array, 0 with the active flags: inactive
 // systems have zero vectors, so skipping them changes no value).
+//
+// With `fuse` (and at most kFuseMaxSystems systems, R dividing 32 or R = 64)
+// the chunk partials are summed inside the projection kernel, and, when
+// fuse->skip2 is set, the re-orthogonalisation flags of gm_reorth_flags are
+// formed there too (from out = h1 with ||w||^2 at index j + 1); the call
+// then returns true.  fuse->cnt: ncnt + 1 zeroed device counters, left
+// zeroed by every fused launch.
+constexpr int kFuseMaxSystems = 8;
+struct GmDotsFuse {
+    int* cnt = nullptr;
+    int ncnt = 0;
+    int j = 0;
+    double2* wn2 = nullptr;
+    const int* active = nullptr;
+    int* skip2 = nullptr;
+};
 template <typename V>
-void gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
+bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
              int nv, int self, const V* w, const int* skip, double2* part, double2* out, int ostride,
-             cudaStream_t s, int skipval = 1);
+             cudaStream_t s, int skipval = 1, const GmDotsFuse* fuse = nullptr);
 // w += sign * sum_i V_i h[s][i]  (skip[s] == skipval: unchanged)
 template <typename V, typename W>
 void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long long vstride, int nv, const double2* h,
