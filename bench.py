@@ -190,6 +190,9 @@ def aggregate(local_ms: float, local_bytes: float, dist, device="cpu"):
 def profile_only(what: str):
     """Minimal runs for ncu captures: 'matvec' = three FP64 then three FP32
     products of the 400-disk operator; 'fp64' / 'mixed' = one solve;
+    'sweep600' = one FP32 sweep of the mixed solve capped at 600 Arnoldi
+    steps (after a 5-step solve that builds the plans), with its wall time
+    per step;
     'tc' / 'tcs' = three tensor-core FP32 products with 64 columns on the
     first 800 sites of the 4000-disk lattice (generators 0.31 GB, above L2;
     the expanding kernel / the shift-GEMM kernel);
@@ -215,6 +218,17 @@ def profile_only(what: str):
         return
     cl = W.random_cluster_400()
     pb = msd.Problem(cl)
+    if what == "sweep600":
+        import time
+        beta = [cl.meta["beta"]]
+        pb.solve(beta, tol=1e-10, precision=msd.MSD_MIXED, maxit=5, max_refine=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = pb.solve(beta, tol=1e-10, precision=msd.MSD_MIXED, maxit=600, max_refine=1)
+        torch.cuda.synchronize()
+        steps = max(1, int(res.iters.max()))
+        print(json.dumps({"steps": steps, "wall_us_per_step": round((time.perf_counter() - t0) * 1e6 / steps, 1)}))
+        return
     if what == "matvec":
         g = torch.Generator(device="cpu").manual_seed(0)
         x64 = torch.randn(cl.ntot, 1, dtype=torch.complex128, generator=g).cuda()
@@ -653,7 +667,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed", "tc", "tcs", "recompute"], default=None,
+    ap.add_argument("--profile-only", choices=["matvec", "fp64", "mixed", "sweep600", "tc", "tcs", "recompute"],
+                    default=None,
                     help="run a minimal workload for a profiler capture and print no JSON line")
     ap.add_argument("--products", action="store_true",
                     help="print a table (JSON lines) of block-product kernels over the workloads instead")

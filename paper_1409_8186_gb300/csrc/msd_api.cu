@@ -586,15 +586,17 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64, bool allow_sh
     double best_ms = 1e300;
     MatvecChoice best = plan.ch;
     int best_div = 1;
-    // every shape at the wave model's split count and at a quarter of it
-    // (fewer, longer source ranges: less partial-sum traffic and per-CTA
-    // set-up, at some cost in wave fill)
+    // every shape at the wave model's split count and at a half, a quarter
+    // and an eighth of it (fewer, longer source ranges: less partial-sum
+    // traffic and per-CTA set-up, at some cost in wave fill)
+    constexpr int kDivs[4] = {1, 2, 4, 8};
     int model_ns = 1;
-    for (int i = 0; i < 2 * nc; ++i) {
-        if ((i & 1) && model_ns == 1) continue;  // a quarter of one split is the same plan
+    for (int i = 0; i < 4 * nc; ++i) {
+        const int dv = kDivs[i & 3];
+        if (dv > 1 && model_ns / (dv / 2) <= 1) continue;  // the same plan as a smaller divisor
         MatvecPlan trial;
-        trial.ch = cand[i / 2];
-        trial.ns_div = (i & 1) ? 4 : 1;
+        trial.ch = cand[i / 4];
+        trial.ns_div = dv;
         float* XT = nullptr;
         if (trial.ch.SH) {
             if (!ensure_gt(pb)) continue;
@@ -602,7 +604,7 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64, bool allow_sh
             CK(cudaMemsetAsync(XT, 0, (size_t)pb->xrows * 4 * R * sizeof(float), pb->stream));
         }
         build_work(pb, trial, R, fp64);
-        if (!(i & 1)) model_ns = trial.nsplit;
+        if (dv == 1) model_ns = trial.nsplit;
         const int nfull = (int)trial.work.size();
         const int nw = std::max(1, std::min(nfull, (int)std::ceil(frac * nfull)));
         MatvecWork* dw = (MatvecWork*)dwork.get(nfull * sizeof(MatvecWork));
@@ -614,7 +616,7 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64, bool allow_sh
             if (trial.ch.SH)
                 launch_bt_tcs(pb->d_cfg, dw, nw, pb->Nmax, pb->d_GT, XT, (float2*)part, pb->Ntot, R, pb->stream);
             else
-                launch_bt_only(cand[i / 2], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
+                launch_bt_only(cand[i / 4], fp64, pb->d_cfg, dw, nw, pb->Nmax, G, xs, part, pb->Ntot, R, pb->stream);
             CK_LAUNCH();
             CK(cudaEventRecord(e1, pb->stream));
             CK(cudaEventSynchronize(e1));
@@ -625,7 +627,7 @@ void autotune(msd_problem* pb, MatvecPlan& plan, int R, bool fp64, bool allow_sh
         }
         if (t < best_ms) {
             best_ms = t;
-            best = cand[i / 2];
+            best = cand[i / 4];
             best_div = trial.ns_div;
         }
     }
