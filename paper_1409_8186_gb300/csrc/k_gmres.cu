@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
             A ax[Q], ay[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) ax[q] = ay[q] = A(0);
-            constexpr int U = 8;  // a multiple of Q: the column phase of k survives the stride
+            // loads in flight per lane: a multiple of Q (the column phase of k
+            // survives the stride); 16 complex64 = the whole 512-row chunk of
+            // one column in a single round trip
+            constexpr int U = sizeof(V) == 8 ? 16 : 8;
             long long e = e0 + lane;
             for (; e + 32LL * (U - 1) < e1; e += 32LL * U) {
                 V uv[U], wv[U];
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
     if (!fz.cnt) return;
     // ---- fused reduction of this vector group (last block of the group)
     __shared__ int last;
-    __threadfence();
+    if (Q == 2 || lane < R) __threadfence();  // the lanes that wrote partial sums
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&fz.cnt[blockIdx.y], 1) == (int)gridDim.x - 1;
     __syncthreads();

@@ -166,7 +166,7 @@ template <int KB, int RB> struct MacFor<float2, KB, RB, 1> { typedef Mac2<KB, RB
 // current one is summed); S = 1: one stage, staged and then summed, for
 // truncation orders whose two FP64 stages exceed the shared memory of a CTA.
 template <typename V, int RT, int RB, int KB, int P, int S>
-__global__ void __launch_bounds__(512) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
+__global__ void __launch_bounds__(512, (RB == 1 && sizeof(V) == 8) ? 2 : 1) k_bt_matvec(const MsdConfig* __restrict__ cfgs,
                                                    const MatvecWork* __restrict__ works,
                                                    const V* __restrict__ G, const V* __restrict__ xs,
                                                    V* __restrict__ part, long long Ntot, int R, int rtiles,
