@@ -136,15 +136,17 @@ struct DotsFuse {
     int S = 0;
     double2* out = nullptr;
     int ostride = 0;
-    // re-orthogonalisation flags (first projection only)
+    // after the reduction, with wn2 set: wn2 = out[j + 1] - sum_{i <= j} |out[i]|^2
+    // (||w - V h||^2 when out = V^H w with ||w||^2 at j + 1), and with skip2
+    // also set the re-orthogonalisation flags (first projection)
     int j = 0;
     double2* wn2 = nullptr;
     const int* active = nullptr;
     int* skip2 = nullptr;
 };
 
-// ||w'||^2 = ||w||^2 - sum_{i <= j} |h_i|^2 and the flag of one system,
-// reduced over the CTA (every thread calls it).
+// ||w'||^2 = ||w||^2 - sum_{i <= j} |h_i|^2 and (skip2 != nullptr) the flag
+// of one system, reduced over the CTA (every thread calls it).
 __device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, int* skip2) {
     double acc = 0.0;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
@@ -163,7 +165,7 @@ __device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, 
         const double before = __ldcg(h + j + 1).x;  // ||w||^2 before the projection
         const double after = before - ss;
         *wn2 = make_double2(after, 0.0);
-        *skip2 = !(act && after < 0.5 * before);
+        if (skip2) *skip2 = !(act && after < 0.5 * before);
     }
 }
 
@@ -274,8 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
         if (lane == 0) fz.out[(long long)sy * fz.ostride + iv] = acc;
     }
     if (threadIdx.x == 0) fz.cnt[blockIdx.y] = 0;
-    if (!fz.skip2) return;
-    // ---- re-orthogonalisation flags (last vector group to finish)
+    if (!fz.wn2) return;
+    // ---- norm after the projection, re-orthogonalisation flags (last vector group to finish)
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(fz.cnt_all, 1) == (int)gridDim.y - 1;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restri
     __threadfence();
     for (int sy = 0; sy < fz.S; ++sy)
         reorth_flag_cta(fz.out + (long long)sy * fz.ostride, fz.j, fz.wn2 + (long long)sy * fz.ostride,
-                        fz.active[sy], fz.skip2 + sy);
+                        fz.active ? fz.active[sy] : 1, fz.skip2 ? fz.skip2 + sy : nullptr);
     if (threadIdx.x == 0) *fz.cnt_all = 0;
 }
 
@@ -694,7 +696,7 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
         fz.S = d.S;
         fz.out = out;
         fz.ostride = ostride;
-        if (fuse->skip2) {
+        if (fuse->wn2) {
             fz.j = fuse->j;
             fz.wn2 = fuse->wn2;
             fz.active = fuse->active;

@@ -1183,10 +1183,10 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         // systems that have converged (zero vectors from here on) are skipped
         // (few systems: the reductions, and the flags of the second
         // projection, run inside the projection kernels)
-        GmDotsFuse fz1, fz;
-        fz1.cnt = fz.cnt = cx.cnt;
-        fz1.ncnt = fz.ncnt = cx.ncnt;
-        fz1.j = j;
+        GmDotsFuse fz1, fz2;
+        fz1.cnt = fz2.cnt = cx.cnt;
+        fz1.ncnt = fz2.ncnt = cx.ncnt;
+        fz1.j = fz2.j = j;
         fz1.wn2 = cx.wn2;
         fz1.active = cx.active;
         fz1.skip2 = cx.skip2;
@@ -1195,9 +1195,14 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, cx.active, -1.0, w, s, 0);
         // second projection only where the first removed more than half of ||w||^2
         if (!flags_done) gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
-        gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 0, w, cx.skip2, cx.part, cx.h2, cx.hstride, s, 1, &fz);
+        // its norm: ||w1 - V h2||^2 = ||w1||^2 - |h2|^2 (w1 measured by the
+        // projection itself; h2 is small after the first pass, so no
+        // cancellation), formed inside the fused kernel, else measured
+        fz2.wn2 = cx.wn2b;
+        const bool norm_done =
+            gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, cx.skip2, cx.part, cx.h2, cx.hstride, s, 1, &fz2);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h2, cx.hstride, cx.skip2, -1.0, w, s);
-        gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s, 1, &fz);
+        if (!norm_done) gm_dots<V>(d, ch, co, nullptr, 0, 0, 1, w, cx.skip2, cx.part, cx.wn2b, cx.hstride, s);
         // the Givens step stores its flags (any system still active, a
         // non-finite coefficient) straight into pinned host memory, in the
         // ring slot of this step; the host cleared the slot, whose previous

@@ -384,11 +384,12 @@ struct GmresDims {
 // systems have zero vectors, so skipping them changes no value).
 //
 // With `fuse` (and at most kFuseMaxSystems systems, R dividing 32 or R = 64)
-// the chunk partials are summed inside the projection kernel, and, when
-// fuse->skip2 is set, the re-orthogonalisation flags of gm_reorth_flags are
-// formed there too (from out = h1 with ||w||^2 at index j + 1); the call
-// then returns true.  fuse->cnt: ncnt + 1 zeroed device counters, left
-// zeroed by every fused launch.
+// the chunk partials are summed inside the projection kernel; the call then
+// returns true.  With fuse->wn2 set (self = 1, ||w||^2 lands at index j + 1)
+// the kernel also writes wn2[s * ostride] = ||w||^2 - sum_{i <= j} |out_i|^2,
+// the squared norm after the projection, and with fuse->skip2 set the
+// re-orthogonalisation flags of gm_reorth_flags.  fuse->cnt: ncnt + 1 zeroed
+// device counters, left zeroed by every fused launch.
 constexpr int kFuseMaxSystems = 8;
 struct GmDotsFuse {
     int* cnt = nullptr;
