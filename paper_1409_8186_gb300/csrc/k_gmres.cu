@@ -170,7 +170,7 @@ __device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, 
 }
 
 template <typename V, int Q>
-__global__ void __launch_bounds__(kThreads) k_dots_warp(const RowChunk* __restrict__ chunks, int R,
+__global__ void __launch_bounds__(kThreads, 4) k_dots_warp(const RowChunk* __restrict__ chunks, int R,
                                                         const V* __restrict__ Vb, long long vstride, int nv,
                                                         int self, const V* __restrict__ w,
                                                         const int* __restrict__ skip, int skipval,
