@@ -292,25 +292,52 @@ __global__ void __launch_bounds__(kThreads, 4) k_dots_warp(const RowChunk* __res
 
 // out[s * ostride + i] = sum over the chunks of cfg(s) of part[chunk][i][r]
 // (one warp per output: the lanes stride over the chunks, then shuffle-add)
+// With tail.cnt set (few systems), the last block to finish also forms
+// wn2[s] = out[s][j + 1] - sum_{i <= j} |out[s][i]|^2 and, with tail.skip2,
+// the re-orthogonalisation flags (k_reorth_flags), and puts the counter back
+// to zero.
+struct FinTail {
+    int* cnt = nullptr;
+    int j = 0;
+    double2* wn2 = nullptr;
+    const int* active = nullptr;
+    int* skip2 = nullptr;
+};
 __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_chunk_off,
-                           const double2* __restrict__ part, double2* __restrict__ out, int ostride) {
+                           const double2* __restrict__ part, double2* __restrict__ out, int ostride, FinTail tail) {
     const long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (idx >= (long long)C * R * nvv) return;  // uniform across the warp
-    const int i = (int)(idx % nvv);
-    const int s = (int)(idx / nvv);
-    const int c = s / R, r = s % R;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = cfg_chunk_off[c] + lane; k < cfg_chunk_off[c + 1]; k += 32) {
-        const double2 v = part[((long long)k * nvv + i) * R + r];
-        acc.x += v.x;
-        acc.y += v.y;
+    if (idx < (long long)C * R * nvv) {  // uniform across the warp
+        const int i = (int)(idx % nvv);
+        const int s = (int)(idx / nvv);
+        const int c = s / R, r = s % R;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = cfg_chunk_off[c] + lane; k < cfg_chunk_off[c + 1]; k += 32) {
+            const double2 v = part[((long long)k * nvv + i) * R + r];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) {
+            out[(long long)s * ostride + i] = acc;
+            if (tail.cnt) __threadfence();
+        }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
-    if (lane == 0) out[(long long)s * ostride + i] = acc;
+    if (!tail.cnt) return;
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(tail.cnt, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int S = C * R;
+    for (int sy = 0; sy < S; ++sy)
+        reorth_flag_cta(out + (long long)sy * ostride, tail.j, tail.wn2 + (long long)sy * ostride,
+                        tail.active ? tail.active[sy] : 1, tail.skip2 ? tail.skip2 + sy : nullptr);
+    if (threadIdx.x == 0) *tail.cnt = 0;
 }
 
 // w[row][r] += sign * sum_{i in block's group, i < nv} V_i[row][r] h[s][i].
@@ -685,9 +712,12 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
     const int nvv = nv + self;
     constexpr int WPB = kThreads / 32;
     const bool warp_kernel = 32 % d.R == 0 || d.R == 64;
-    // fused reduction: few systems (the last block of a vector group sums
-    // S * 8 outputs) and counters for every vector group
-    const bool fused = fuse && warp_kernel && d.S <= kFuseMaxSystems && (nvv + WPB - 1) / WPB <= fuse->ncnt;
+    // fused reduction inside the projection kernel: few systems and one
+    // group of vectors (a fence and an atomic per block only pay off for
+    // small grids); otherwise the reduction kernel takes the norm and the
+    // flags in its last block
+    const bool few = fuse && d.S <= kFuseMaxSystems;
+    const bool fused = few && warp_kernel && (nvv + WPB - 1) / WPB == 1;
     DotsFuse fz;
     if (fused) {
         fz.cnt = fuse->cnt;
@@ -718,9 +748,18 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
         return true;
     }
     const long long tot = (long long)d.S * nvv;
-    k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride);
+    FinTail tail;
+    const bool tail_done = few && fuse->wn2;
+    if (tail_done) {
+        tail.cnt = fuse->cnt + fuse->ncnt;
+        tail.j = fuse->j;
+        tail.wn2 = fuse->wn2;
+        tail.active = fuse->active;
+        tail.skip2 = fuse->skip2;
+    }
+    k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
     g_msd_launches += 2;
-    return false;
+    return tail_done;
 }
 
 template <typename V, typename W>

@@ -383,13 +383,14 @@ struct GmresDims {
 // (skipval 1 with a skip-flag array, 0 with the active flags: inactive
 // systems have zero vectors, so skipping them changes no value).
 //
-// With `fuse` (and at most kFuseMaxSystems systems, R dividing 32 or R = 64)
-// the chunk partials are summed inside the projection kernel; the call then
-// returns true.  With fuse->wn2 set (self = 1, ||w||^2 lands at index j + 1)
-// the kernel also writes wn2[s * ostride] = ||w||^2 - sum_{i <= j} |out_i|^2,
-// the squared norm after the projection, and with fuse->skip2 set the
-// re-orthogonalisation flags of gm_reorth_flags.  fuse->cnt: ncnt + 1 zeroed
-// device counters, left zeroed by every fused launch.
+// With `fuse` and at most kFuseMaxSystems systems, and fuse->wn2 set (self =
+// 1, ||w||^2 lands at index j + 1), the reduction also writes
+// wn2[s * ostride] = ||w||^2 - sum_{i <= j} |out_i|^2, the squared norm after
+// the projection, and with fuse->skip2 set the re-orthogonalisation flags of
+// gm_reorth_flags; the call then returns true.  For a single group of eight
+// vectors (R dividing 32 or R = 64) the reduction runs inside the projection
+// kernel, else in its reduction kernel.  fuse->cnt: ncnt + 1 zeroed device
+// counters, left zeroed by every launch that uses them.
 constexpr int kFuseMaxSystems = 8;
 struct GmDotsFuse {
     int* cnt = nullptr;
