@@ -194,6 +194,11 @@ struct msd_problem {
     std::vector<RowChunk> chunks_coarse;
     RowChunk* d_chunks_coarse = nullptr;
     int* d_cfg_chunk_off_coarse = nullptr;
+    // medium chunks (>= 1024 rows) for the warp-per-vector projections onto
+    // many basis vectors: each warp streams twice the rows of a fine chunk
+    std::vector<RowChunk> chunks_mid;
+    RowChunk* d_chunks_mid = nullptr;
+    int* d_cfg_chunk_off_mid = nullptr;
     int* h_pinned = nullptr;  // small pinned host flags: [0..1] sync reads, [2..9] ring of step flags, [10] DORT barrier
     int* d_hpinned = nullptr;  // the same flags as the device addresses them (mapped host memory)
     cudaEvent_t ring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -1172,13 +1177,22 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
             operator_dev(pb, d.R, fp64, cx.adjoint, vj, w);
         }
         // projections onto many basis vectors: the coarse row chunks when the
-        // block-reduction kernel serves this column count (warp-per-vector
-        // kernels need no reduction and run on the fine chunks: more warps)
-        const bool coarse = j + 1 >= kCoarseFrom && !(32 % d.R == 0 || d.R == 64);
+        // block-reduction kernel serves this column count, the medium ones for
+        // the warp-per-vector kernels (no block reduction; longer-lived warps)
+        const bool many = j + 1 >= kCoarseFrom;
+        const bool warpk = 32 % d.R == 0 || d.R == 64;
         GmresDims db = d;
-        if (coarse) db.nchunk = (int)pb->chunks_coarse.size();
-        const RowChunk* chb = coarse ? pb->d_chunks_coarse : ch;
-        const int* cob = coarse ? pb->d_cfg_chunk_off_coarse : co;
+        const RowChunk* chb = ch;
+        const int* cob = co;
+        if (many && !warpk) {
+            db.nchunk = (int)pb->chunks_coarse.size();
+            chb = pb->d_chunks_coarse;
+            cob = pb->d_cfg_chunk_off_coarse;
+        } else if (many) {
+            db.nchunk = (int)pb->chunks_mid.size();
+            chb = pb->d_chunks_mid;
+            cob = pb->d_cfg_chunk_off_mid;
+        }
         // first projection h1 = V^H w (with ||w||^2 at h1[j+1]), w -= V h1;
         // systems that have converged (zero vectors from here on) are skipped
         // (few systems: the reductions, and the flags of the second
@@ -1613,6 +1627,8 @@ msd_status msd_create(int C, const int* disk_off, const double* centres, const d
             make_chunks(std::max<long long>(512, row / 256), pb->chunks, &pb->d_chunks, &pb->d_cfg_chunk_off);
             make_chunks(std::max<long long>(4096, row / 64), pb->chunks_coarse, &pb->d_chunks_coarse,
                         &pb->d_cfg_chunk_off_coarse);
+            make_chunks(std::max<long long>(1024, row / 128), pb->chunks_mid, &pb->d_chunks_mid,
+                        &pb->d_cfg_chunk_off_mid);
             launch_disk_diagonals(pb->d_cfg, Mtot, pb->d_disk_cfg, pb->d_radius, pb->d_bc, pb->Nmax, pb->d_J,
                                   pb->d_dJ, pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                                   pb->d_rhs_scale, pb->d_flags, pb->stream);
@@ -1633,7 +1649,7 @@ void msd_destroy(msd_problem* pb) {
     void* ptrs[] = {pb->d_cfg, pb->d_centre, pb->d_radius, pb->d_bc, pb->d_disk_cfg, pb->d_J, pb->d_dJ,
                     pb->d_H, pb->d_dH, pb->d_lf64, pb->d_rhs_scale, pb->d_rf64, pb->d_lf32, pb->d_rf32,
                     pb->d_flags, pb->d_G64, pb->d_G32, pb->d_chunks, pb->d_cfg_chunk_off,
-                    pb->d_chunks_coarse, pb->d_cfg_chunk_off_coarse,
+                    pb->d_chunks_coarse, pb->d_cfg_chunk_off_coarse, pb->d_chunks_mid, pb->d_cfg_chunk_off_mid,
                     pb->d_GA64, pb->d_GA32, pb->d_clf64, pb->d_clf32, pb->d_GT, pb->d_gt_blk, pb->d_Np};
     for (void* p : ptrs)
         if (p) cudaFree(p);
