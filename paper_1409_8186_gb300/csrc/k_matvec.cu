@@ -11,14 +11,14 @@
 // Work decomposition: a CTA owns a tile of 32 target disks (one per lane),
 // a contiguous range of source disks q, and RT columns.  Warps split the
 // target modes into blocks of KB consecutive m (and the columns into groups
-// of RB).  Per source q the CTA stages, with cp.async and double buffering,
-// the 32 generator rows g^{p q}_{.} (contiguous in the [q][p][l] layout) and
-// the RT-column slab of xs^q into shared memory.  Each thread then sweeps n
-// with a register window of KB generator values (one new value per n, since
-// neighbouring m need neighbouring l = n - m) and accumulates KB x RB
-// complex sums.  Generator rows are padded in shared memory to an odd
-// length so the 32 lanes (32 different rows) hit 32 different banks; the
-// xs slab is a broadcast.  KB is chosen per truncation order so that
+// of RB).  Per source q the CTA stages, double-buffered, the 32 generator
+// rows g^{p q}_{.} (contiguous in the [q][p][l] layout: one bulk copy on an
+// mbarrier) and the RT-column slab of xs^q (cp.async) into shared memory.
+// Each thread then sweeps n with a register window of KB generator values
+// (one new value per n, since neighbouring m need neighbouring l = n - m)
+// and accumulates KB x RB complex sums.  The rows keep their odd length
+// L = 4N + 1, so the 32 lanes (32 different rows) hit 32 different banks;
+// the xs slab is a broadcast.  KB is chosen per truncation order so that
 // ceil(n / KB) * KB wastes as few padded modes as possible.  Raw sums go to a
 // per-split partial buffer; a finalize kernel adds the splits, applies
 // l^p_m and adds x.
