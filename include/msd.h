@@ -515,8 +515,11 @@ msd_status msd_set_generator_mode(msd_problem* pb, int mode, int64_t chunk_bytes
  *   of this problem, replacing any plan made before.  MSD_ERR_ARG if
  *   (KB, RT) is not one of the instantiated shapes that fit (FP64: KB 4..7,
  *   RT 1; FP32: KB 4..9, RT in {1,2,4,8,16} dividing R, at most 16 warps
- *   per CTA, shared memory <= 227 KB; FP32 KB + 100 selects the same window
- *   with each complex multiply-add issued as two paired FP32 FMAs; KB = 0,
+ *   per CTA, shared memory <= 226 KB; FP32 KB + 100 selects the same window
+ *   with each complex multiply-add issued as two paired FP32 FMAs, and with
+ *   RT = 1, KB + 200 / KB + 300 the same windows in a kernel without CTA
+ *   barriers in its source loop (stages released per warp, source values
+ *   read from global memory); KB = 0,
  *   RT in {16, 32, 64} dividing R: the tensor-core kernel that expands the
  *   Toeplitz blocks in shared memory; RT = 8 with KB = 0 or 1, R a multiple
  *   of 8: the shift-GEMM tensor-core kernel, one dense GEMM over the source

@@ -338,6 +338,154 @@ __global__ void __launch_bounds__(512, (RB == 1 && sizeof(V) == 8) ? 2 : 1) k_bt
     }
 }
 
+// The single-column FP32 product without CTA barriers in the source loop:
+// the generator stages are filled by bulk copies (full mbarriers) and
+// released by every warp once it has swept them (empty mbarriers, one
+// arrival per warp), and each thread reads the source values xs^q_n straight
+// from global memory (one address for the whole warp: a broadcast from L1),
+// zero for the padded modes n >= 2N+1.  Warps therefore drift apart by up to
+// a stage instead of meeting twice per source.  Same window, sums and output
+// as k_bt_matvec<float2, 1, 1, KB, P, 2>.
+template <int KB, int P>
+__global__ void __launch_bounds__(512, P ? 1 : 2) k_bt_matvec1(const MsdConfig* __restrict__ cfgs,
+                                                       const MatvecWork* __restrict__ works,
+                                                       const float2* __restrict__ G,
+                                                       const float2* __restrict__ xs, float2* __restrict__ part,
+                                                       long long Ntot, int R, int rtiles,
+                                                       const int* __restrict__ live) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* smem = reinterpret_cast<float2*>(smem_raw);
+    __shared__ __align__(8) uint64_t gfull[2], gempty[2];
+
+    const int wi = blockIdx.x / rtiles;
+    const int rt = blockIdx.x % rtiles;
+    const MatvecWork w = works[wi];
+    const MsdConfig c = cfgs[w.cfg];
+    const int N = c.N, n = c.n, L = c.L;
+    const int I = (n + KB - 1) / KB;
+    const int npad = I * KB;
+    const int gsz = stage_g_elems(L, KB);
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int nwarps = blockDim.y;
+    const int tid = warp * 32 + lane;
+    const bool mact = warp < I;
+    const int m0 = warp * KB;
+    const int col0 = rt;
+
+    if (live && live[w.cfg * R + col0] == 0) {
+        const int p = w.p0 + lane;
+        if (!w.pad && mact && p < c.M) {
+            float2* out = part + (long long)w.split * Ntot * R;
+            for (int b = 0; b < KB; ++b)
+                if (m0 + b < n) out[(c.row_off + (long long)p * n + m0 + b) * R + col0] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
+    float2* gbuf[2] = {smem, smem + gsz};
+    for (int s = 0; s < 2; ++s)
+        for (int t = tid; t < kGFront + kGBack; t += nwarps * 32)
+            gbuf[s][t < kGFront ? t : MSD_TILE_P * L + t] = make_float2(0.f, 0.f);
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gfull[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&gempty[s])), "r"(nwarps));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+
+    const float2* gsrc_cfg = G + c.gen_off + (long long)w.p0 * L;
+    const unsigned gbytes = (unsigned)(MSD_TILE_P * L * sizeof(float2));
+    // alignment is the same for every source of a CTA (the plan builder only
+    // offers this kernel where it holds; an unaligned tile is not staged and
+    // the expired wait below reports the failure)
+    const bool aligned = (((uintptr_t)gsrc_cfg) & 15) == 0 && (((long long)c.Mp * L * sizeof(float2)) & 15) == 0;
+    auto issue = [&](int q, int s) {
+        const uint32_t bar = smem_u32(&gfull[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(gbytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(gbuf[s] + kGFront)),
+                     "l"(gsrc_cfg + (long long)q * c.Mp * L), "r"(gbytes), "r"(bar)
+                     : "memory");
+    };
+
+    typedef typename MacFor<float2, KB, 1, P>::type Mac;
+    Mac acc;
+    acc.init();
+    bool ok = aligned;
+    int pending = -1;  // (thread 0) the last iteration whose stage was issued
+    if (tid == 0 && ok && w.q0 < w.q1) {
+        issue(w.q0, 0);
+        pending = 0;
+    }
+    const int base = kGFront + 2 * N - m0;
+    for (int it = 0, q = w.q0; q < w.q1; ++it, ++q) {
+        const int sb = it & 1;
+        // producer: the next source into the other stage once every warp has
+        // released it (its use at it - 1)
+        if (tid == 0 && ok && q + 1 < w.q1) {
+            if (it >= 1) ok = bt_mbar_wait(smem_u32(&gempty[sb ^ 1]), (uint32_t)(((it - 1) >> 1) & 1));
+            if (ok) {
+                issue(q + 1, sb ^ 1);
+                pending = it + 1;
+            }
+        }
+        __syncwarp();
+        bool here = ok;
+        if (here) here = bt_mbar_wait(smem_u32(&gfull[sb]), (uint32_t)((it >> 1) & 1));
+        here = __all_sync(0xffffffffu, here);
+        if (!here) ok = false;
+        if (ok && mact) {
+            const float2* gs = gbuf[sb] + lane * L + base;
+            const float2* xq = xs + (c.row_off + (long long)q * n) * R + col0;
+            typename Mac::G win[KB];
+#pragma unroll
+            for (int j = 1; j < KB; ++j) win[KB - j] = Mac::gen(gs[-j]);
+            for (int nb = 0; nb < npad; nb += KB) {
+                float2 xr[KB];
+#pragma unroll
+                for (int u = 0; u < KB; ++u) xr[u] = nb + u < n ? __ldg(xq + (long long)(nb + u) * R) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    win[u] = Mac::gen(gs[nb + u]);
+                    const typename Mac::X xv = Mac::src(xr[u]);
+#pragma unroll
+                    for (int b = 0; b < KB; ++b) acc.mac(b, 0, win[(u - b + KB) % KB], xv);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&gempty[sb])) : "memory");
+        if (!ok) break;
+    }
+    if (!ok && w.q0 < w.q1) {
+        atomicOr(&g_bt_status, 1);
+        // a copy issued for a stage nobody waited for: let it land (bounded)
+        // before the CTA's shared memory is given up
+        if (tid == 0 && pending >= 0)
+            bt_mbar_wait(smem_u32(&gfull[pending & 1]), (uint32_t)((pending >> 1) & 1));
+    }
+
+    const int p = w.p0 + lane;
+    if (mact && p < c.M) {
+        float2* out = part + (long long)w.split * Ntot * R;
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            const int mi = m0 + b;
+            if (mi < n) {
+                const long long o = (c.row_off + (long long)p * n + mi) * R + col0;
+                const float2 v = acc.result(b, 0);
+                if (w.pad) {
+                    const float2 u = out[o];
+                    out[o] = make_float2(u.x + v.x, u.y + v.y);
+                } else {
+                    out[o] = v;
+                }
+            }
+        }
+    }
+}
+
 // xs = rf .* x   (columns scaled by the column factor r^q_n of their row)
 template <typename V, typename S>
 __global__ void k_scale_cols(long long Ntot, int R, const S* __restrict__ rf, const V* __restrict__ x,
@@ -466,6 +614,38 @@ struct Bt {
     }
 };
 
+template <int KB, int P>
+struct Bt1 {
+    static void attr() {
+        static bool done = false;
+        if (!done) {
+            cudaFuncSetAttribute(k_bt_matvec1<KB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMatvecSmemCap);
+            done = true;
+        }
+    }
+    static size_t smem(int Nmax) { return 2 * (size_t)stage_g_elems(4 * Nmax + 1, KB) * sizeof(float2); }
+    static dim3 block(int Nmax) { return dim3(32, (2 * Nmax + 1 + KB - 1) / KB); }
+    static void launch(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax, const float2* G,
+                       const float2* xs, float2* part, long long Ntot, int R, cudaStream_t s,
+                       const int* live = nullptr) {
+        attr();
+        k_bt_matvec1<KB, P><<<(unsigned)(nwork * R), block(Nmax), smem(Nmax), s>>>(d_cfg, d_work, G, xs, part, Ntot,
+                                                                                   R, R, live);
+    }
+    static int occupancy(int Nmax) {
+        attr();
+        const dim3 b = block(Nmax);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bt_matvec1<KB, P>, b.x * b.y, smem(Nmax)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        return nb < 1 ? 1 : nb;
+    }
+};
+
 // Dispatch on (RT, RB) for a fixed KB (FP32), or KB alone (FP64).
 template <int KB, int P, typename F>
 void with_f32_p(const Choice& c, F&& f) {
@@ -477,10 +657,17 @@ void with_f32_p(const Choice& c, F&& f) {
         default: f(Bt<float2, 16, 4, KB, P>()); break;
     }
 }
+// P2 bit 0: paired FMAs; bit 1: the barrier-free single-column kernel
 template <int KB, typename F>
 void with_f32(const Choice& c, F&& f) {
-    if (c.P2) with_f32_p<KB, 1>(c, f);
-    else with_f32_p<KB, 0>(c, f);
+    if (c.P2 & 2) {
+        if (c.P2 & 1) f(Bt1<KB, 1>());
+        else f(Bt1<KB, 0>());
+    } else if (c.P2) {
+        with_f32_p<KB, 1>(c, f);
+    } else {
+        with_f32_p<KB, 0>(c, f);
+    }
 }
 
 // FP64: two stages when they fit in the shared memory of a CTA, else one
@@ -534,8 +721,9 @@ int bt_status_and_clear() {
 
 // Every instantiated tile shape that fits this (R, N): FP64 KB = 4..7 with
 // RT = 1; FP32 KB = 4..9 with each column tile RT in {1, 2, 4, 8, 16} that
-// divides R and keeps I * RT / RB <= 16 warps per CTA, and the tensor-core
-// kernel with TC in {16, 32, 64} columns dividing R (n <= 128).
+// divides R and keeps I * RT / RB <= 16 warps per CTA, four-FFMA and
+// paired-FMA forms, for RT = 1 also in the barrier-free kernel, and the
+// tensor-core kernel with TC in {16, 32, 64} columns dividing R (n <= 128).
 int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bool allow_sh) {
     const int n = 2 * Nmax + 1;
     int cnt = 0;
@@ -546,7 +734,7 @@ int matvec_candidates(int R, int Nmax, bool fp64, MatvecChoice* out, int cap, bo
             if (R % rt) break;
             const int rb = rt < 4 ? rt : 4;
             if (I * (rt / rb) > 16) continue;
-            for (int p2 = 0; p2 <= (fp64 ? 0 : 1); ++p2) {
+            for (int p2 = 0; p2 <= (fp64 ? 0 : (rt == 1 ? 3 : 1)); ++p2) {
                 Choice c{KB, rt, rb, I, 0, p2};
                 if (fp64) c.ONE = f64_one_stage(Nmax, KB) ? 1 : 0;
                 size_t b = 0;

@@ -173,9 +173,10 @@ def test_matvec_fp32(msd, name, R):
 @pytest.mark.parametrize("fp64", [True, False])
 def test_matvec_every_tile_shape(msd, fp64):
     """Each instantiated tile shape (register window KB, column tile RT; FP32
-    also in the paired-FMA form KB + 100), pinned with msd_set_tile, against
-    the oracle; rand70 spans three target tiles with a ragged tail and R = 16
-    admits every column tile."""
+    also in the paired-FMA form KB + 100, and for RT = 1 the barrier-free
+    single-column kernel KB + 200 / KB + 300), pinned with msd_set_tile,
+    against the oracle; rand70 spans three target tiles with a ragged tail and
+    R = 16 admits every column tile."""
     cl = CASES["rand70"]()
     R = 16
     prec = msd.MSD_FP64 if fp64 else msd.MSD_FP32
@@ -186,7 +187,7 @@ def test_matvec_every_tile_shape(msd, fp64):
     xd = torch.from_numpy(x).cuda()
     pb = msd.Problem(cl)
     tried = 0
-    for KB in list(range(4, 10)) + ([] if fp64 else list(range(104, 110))):
+    for KB in list(range(4, 10)) + ([] if fp64 else [b + k for b in (100, 200, 300) for k in range(4, 10)]):
         for RT in (1, 2, 4, 8, 16):
             try:
                 pb.set_tile(R, prec, KB, RT)
@@ -201,8 +202,11 @@ def test_matvec_every_tile_shape(msd, fp64):
     expect = 0
     for KB in range(4, 8 if fp64 else 10):
         I = -(-n // KB)
-        expect += sum(1 for RT in ((1,) if fp64 else (1, 2, 4, 8, 16)) if I * (RT // min(RT, 4)) <= 16)
-    assert tried == expect * (1 if fp64 else 2)  # FP32: four-FFMA and paired-FMA forms
+        shapes = sum(1 for RT in ((1,) if fp64 else (1, 2, 4, 8, 16)) if I * (RT // min(RT, 4)) <= 16)
+        # FP32: four-FFMA and paired-FMA forms, and both again for RT = 1 in
+        # the barrier-free kernel
+        expect += shapes if fp64 else 2 * shapes + (2 if I <= 16 else 0)
+    assert tried == expect
 
 
 def test_autotuned_plan(msd):
