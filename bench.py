@@ -31,11 +31,12 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 TF32_OVER_BF16 = 1.1 / 2.25                    # nominal dense TF32 / bf16 tensor rate
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
-# product kernel (window length 7) on this workload, from an ncu capture
-# (216.42 MB read + 5.75 MB written); the algorithmic stream is 207.7 MB
-K3_FP64_DRAM_BYTES_PER_LAUNCH = 222170624
+# product kernel (window length 7, generator rows staged by bulk copies) on
+# this workload, from an ncu capture (216.05 MB read + 5.78 MB written); the
+# algorithmic stream is 207.7 MB
+K3_FP64_DRAM_BYTES_PER_LAUNCH = 221831168
 K3_FP64_TRAFFIC_SOURCE = ("copied from an ncu capture of the same kernel on this workload "
-                          "(profiles/k_bt_matvec_random400.md), not measured in this run")
+                          "(profiles/k_bt_matvec_random400.md, current kernel), not measured in this run")
 WORKLOAD = ("random400_k2pi: M=400 sound-soft disks, a~U[0.5,1.5], centres U[-50,50]^2 gap 0.2, "
             "k=2pi, N=20 (16400 unknowns), 1 plane wave, GMRES (restart length sized to HBM) to relres 1e-10, "
             "far field T=360")
