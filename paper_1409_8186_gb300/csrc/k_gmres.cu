@@ -154,7 +154,7 @@ __device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, 
         acc += cabs2(v);
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[32];  // one slot per warp (blocks of up to 1024 threads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[warp] = acc;
@@ -346,6 +346,34 @@ __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_ch
 // basis: the correction it builds only needs the accuracy of the FP32
 // sweep).  With more than one vector group the groups meet in atomics;
 // with one group the result is stored directly.
+// The same reduction in one CTA of 1024 threads, for few outputs (S * nvv
+// small): no counters and no fences; the norm after the projection and the
+// re-orthogonalisation flags follow after a CTA barrier.
+constexpr int kFin1Threads = 1024;
+constexpr int kFin1MaxOutputs = 4096;
+__global__ void __launch_bounds__(kFin1Threads) k_dots_fin1(int C, int R, int nvv, const int* __restrict__ cfg_chunk_off,
+                                                              const double2* __restrict__ part, double2* __restrict__ out,
+                                                              int ostride, FinTail tail) {
+    const int S = C * R;
+    for (int o = threadIdx.x; o < S * nvv; o += blockDim.x) {
+        const int sy = o / nvv, i = o - sy * nvv;
+        const int c = sy / R, r = sy - c * R;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = cfg_chunk_off[c]; k < cfg_chunk_off[c + 1]; ++k) {
+            const double2 v = part[((long long)k * nvv + i) * R + r];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        out[(long long)sy * ostride + i] = acc;
+    }
+    if (!tail.wn2) return;
+    __threadfence_block();
+    __syncthreads();
+    for (int sy = 0; sy < S; ++sy)
+        reorth_flag_cta(out + (long long)sy * ostride, tail.j, tail.wn2 + (long long)sy * ostride,
+                        tail.active ? tail.active[sy] : 1, tail.skip2 ? tail.skip2 + sy : nullptr);
+}
+
 template <typename V, typename W>
 __global__ void __launch_bounds__(kThreads, 4)
     k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
@@ -757,7 +785,12 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
         tail.active = fuse->active;
         tail.skip2 = fuse->skip2;
     }
-    k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
+    if (few && tot <= kFin1MaxOutputs) {
+        tail.cnt = nullptr;  // one CTA: no counter
+        k_dots_fin1<<<1, kFin1Threads, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
+    } else {
+        k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
+    }
     g_msd_launches += 2;
     return tail_done;
 }
