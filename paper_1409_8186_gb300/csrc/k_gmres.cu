@@ -346,34 +346,6 @@ __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_ch
 // basis: the correction it builds only needs the accuracy of the FP32
 // sweep).  With more than one vector group the groups meet in atomics;
 // with one group the result is stored directly.
-// The same reduction in one CTA of 1024 threads, for few outputs (S * nvv
-// small): no counters and no fences; the norm after the projection and the
-// re-orthogonalisation flags follow after a CTA barrier.
-constexpr int kFin1Threads = 1024;
-constexpr int kFin1MaxOutputs = 4096;
-__global__ void __launch_bounds__(kFin1Threads) k_dots_fin1(int C, int R, int nvv, const int* __restrict__ cfg_chunk_off,
-                                                              const double2* __restrict__ part, double2* __restrict__ out,
-                                                              int ostride, FinTail tail) {
-    const int S = C * R;
-    for (int o = threadIdx.x; o < S * nvv; o += blockDim.x) {
-        const int sy = o / nvv, i = o - sy * nvv;
-        const int c = sy / R, r = sy - c * R;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int k = cfg_chunk_off[c]; k < cfg_chunk_off[c + 1]; ++k) {
-            const double2 v = part[((long long)k * nvv + i) * R + r];
-            acc.x += v.x;
-            acc.y += v.y;
-        }
-        out[(long long)sy * ostride + i] = acc;
-    }
-    if (!tail.wn2) return;
-    __threadfence_block();
-    __syncthreads();
-    for (int sy = 0; sy < S; ++sy)
-        reorth_flag_cta(out + (long long)sy * ostride, tail.j, tail.wn2 + (long long)sy * ostride,
-                        tail.active ? tail.active[sy] : 1, tail.skip2 ? tail.skip2 + sy : nullptr);
-}
-
 template <typename V, typename W>
 __global__ void __launch_bounds__(kThreads, 4)
     k_update(const RowChunk* __restrict__ chunks, int R, const V* __restrict__ Vb, long long vstride,
@@ -425,11 +397,13 @@ __global__ void __launch_bounds__(kThreads, 4)
     }
 }
 
-// v = w * scale[s] for active systems, 0 otherwise.
+// v = w * scale[s] for active systems, 0 otherwise; with xs (FP32 basis),
+// also xs = rf .* v, the scaled columns the next product reads (the
+// arithmetic of k_scale_cols on the stored v).
 template <typename Vin, typename Vout>
 __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* __restrict__ w,
                         const double* __restrict__ scale, const int* __restrict__ active,
-                        Vout* __restrict__ v) {
+                        Vout* __restrict__ v, const float* __restrict__ rf, float2* __restrict__ xs) {
     const RowChunk ch = chunks[blockIdx.x];
     const int RC = col_lanes(R);
     const int RY = blockDim.x / RC;
@@ -442,7 +416,12 @@ __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* _
     const A f = (A)(active[s] ? scale[s] : 0.0);
     for (long long row = ch.row0 + ty; row < ch.row1; row += RY) {
         const Vin a = w[row * R + r];
-        v[row * R + r] = Vout{(decltype(Vout{}.x))((A)a.x * f), (decltype(Vout{}.x))((A)a.y * f)};
+        const Vout o = Vout{(decltype(Vout{}.x))((A)a.x * f), (decltype(Vout{}.x))((A)a.y * f)};
+        v[row * R + r] = o;
+        if (xs) {
+            const float c = rf[row];
+            xs[row * R + r] = make_float2(c * (float)o.x, c * (float)o.y);
+        }
     }
 }
 
@@ -785,12 +764,7 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
         tail.active = fuse->active;
         tail.skip2 = fuse->skip2;
     }
-    if (few && tot <= kFin1MaxOutputs) {
-        tail.cnt = nullptr;  // one CTA: no counter
-        k_dots_fin1<<<1, kFin1Threads, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
-    } else {
-        k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
-    }
+    k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
     g_msd_launches += 2;
     return tail_done;
 }
@@ -806,8 +780,8 @@ void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long lon
 
 template <typename Vin, typename Vout>
 void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale, const int* active,
-              Vout* v, cudaStream_t s) {
-    k_scale<Vin, Vout><<<dim3(d.nchunk, rgroups(d.R)), kThreads, 0, s>>>(chunks, d.R, w, scale, active, v);
+              Vout* v, cudaStream_t s, const float* rf, float2* xs) {
+    k_scale<Vin, Vout><<<dim3(d.nchunk, rgroups(d.R)), kThreads, 0, s>>>(chunks, d.R, w, scale, active, v, rf, xs);
     g_msd_launches += 1;
 }
 
@@ -875,8 +849,8 @@ template void gm_update<float2, float2>(const GmresDims&, const RowChunk*, const
 template void gm_update<float2, double2>(const GmresDims&, const RowChunk*, const float2*, long long, int,
                                          const double2*, int, const int*, double, double2*, cudaStream_t, int);
 template void gm_scale<double2, double2>(const GmresDims&, const RowChunk*, const double2*, const double*,
-                                         const int*, double2*, cudaStream_t);
+                                         const int*, double2*, cudaStream_t, const float*, float2*);
 template void gm_scale<double2, float2>(const GmresDims&, const RowChunk*, const double2*, const double*,
-                                        const int*, float2*, cudaStream_t);
+                                        const int*, float2*, cudaStream_t, const float*, float2*);
 template void gm_scale<float2, float2>(const GmresDims&, const RowChunk*, const float2*, const double*, const int*,
-                                       float2*, cudaStream_t);
+                                       float2*, cudaStream_t, const float*, float2*);

@@ -835,11 +835,13 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
 void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const float2* G, const float* rf, const float2* lf, long long Ntot, int R,
                        const float2* x, float2* xs, float2* part, int nsplit, float2* y, cudaStream_t s,
-                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch, const int* live) {
+                       cudaEvent_t ev0, cudaEvent_t ev1, const MatvecChoice* ch, const int* live,
+                       bool xs_ready) {
     const long long tot = Ntot * R;
     const int th = 256;
     const unsigned blocks = (unsigned)((tot + th - 1) / th);
-    k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
+    if (!xs_ready) k_scale_cols<float2, float><<<blocks, th, 0, s>>>(Ntot, R, rf, x, xs);
+    else g_msd_launches -= 1;  // counted below with the product and the reduction
     if (ev0) cudaEventRecord(ev0, s);
     const Choice c = ch ? *ch : choose(R, Nmax, false);
     if (c.TC) {

@@ -236,6 +236,10 @@ struct msd_problem {
     // the tiles none of whose columns are active (converged systems, whose
     // columns of the step are never read) and leave zero sums there
     const int* live = nullptr;
+    // the product input whose scaled columns rf .* x the last Arnoldi step
+    // already wrote into xs (FP32 products of the default rows only; nullptr
+    // otherwise); consumed by the next product
+    const void* xs_src = nullptr;
     // per-disk truncation orders (msd_set_truncation); d_Np == nullptr: N of
     // the configuration on every disk
     std::vector<int> Np;
@@ -960,6 +964,8 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
     if (plan.ch.SH && !ensure_gt(pb)) fail(MSD_ERR_OOM, "shift-GEMM generators do not fit in device memory");
     const size_t elem = fp64 ? 16 : 8;
     void* xs = plan.ch.SH ? nullptr : pb->xs.get((size_t)pb->Ntot * R * elem);
+    const bool xs_ready = !fp64 && !plan.ch.SH && x == pb->xs_src;
+    pb->xs_src = nullptr;
     void* part = pb->part.get((size_t)plan.nsplit * pb->Ntot * R * elem);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (pb->timing) {
@@ -994,7 +1000,7 @@ void matvec_dev(msd_problem* pb, int R, bool fp64, const void* x, void* y) {
     else
         launch_matvec_f32(pb->d_cfg, plan.d_work, (int)plan.work.size(), pb->Nmax, pb->d_G32, pb->d_rf32,
                           pb->d_lf32, pb->Ntot, R, (const float2*)x, (float2*)xs, (float2*)part,
-                          plan.nsplit, (float2*)y, pb->stream, e0, e1, &plan.ch, pb->live);
+                          plan.nsplit, (float2*)y, pb->stream, e0, e1, &plan.ch, pb->live, xs_ready);
     CK_LAUNCH();
 }
 
@@ -1141,6 +1147,12 @@ struct LiveScope {
 template <typename V>
 void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* steps_taken) {
     msd_problem* pb = cx.pb;
+    // scaled columns prepared by a step are for that step's successor only
+    struct XsReset {
+        msd_problem* pb;
+        ~XsReset() { pb->xs_src = nullptr; }
+    } xs_reset{pb};
+    pb->xs_src = nullptr;
     cudaStream_t s = pb->stream;
     const GmresDims& d = cx.d;
     const long long vstride = pb->Ntot * d.R;
@@ -1229,7 +1241,16 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         gm_givens(d, j, cx.h1, cx.h2, cx.hstride, cx.wn2, cx.wn2b, cx.skip2, cx.tol_cycle, cx.H, cx.cs, cx.sn,
                   cx.g, cx.vscale, cx.active, cx.kconv, cx.iters, df, df + 1, cx.rdiag,
                   sizeof(V) == sizeof(float2), s);
-        gm_scale<V, V>(d, ch, w, cx.vscale, cx.active, Vb + (long long)(j + 1) * vstride, s);
+        // the next basis vector; for the FP32 product of the default rows,
+        // also its scaled columns rf .* v, which that product then reads
+        V* vnext = Vb + (long long)(j + 1) * vstride;
+        float2* xs_next = nullptr;
+        if (sizeof(V) == sizeof(float2) && !cx.adjoint && !pb->form && !pb->pen_parent &&
+            pb->gen_mode != MSD_GEN_RECOMPUTE && !get_plan(pb, d.R, false, true).ch.SH) {
+            xs_next = (float2*)pb->xs.get((size_t)pb->Ntot * d.R * sizeof(float2));
+            pb->xs_src = vnext;
+        }
+        gm_scale<V, V>(d, ch, w, cx.vscale, cx.active, vnext, s, xs_next ? pb->d_rf32 : nullptr, xs_next);
         CK_LAUNCH();
         CK(cudaEventRecord(pb->ring_ev[slot], s));
     }

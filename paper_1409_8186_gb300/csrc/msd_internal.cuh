@@ -334,11 +334,12 @@ void launch_matvec_f64(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwo
                        int R, const double2* x, double2* xs, double2* part, int nsplit,
                        double2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
                        const MatvecChoice* ch = nullptr, const int* live = nullptr);
+// xs_ready: xs already holds rf .* x (written by the step that made x)
 void launch_matvec_f32(const MsdConfig* d_cfg, const MatvecWork* d_work, int nwork, int Nmax,
                        const float2* G, const float* rf, const float2* lf, long long Ntot,
                        int R, const float2* x, float2* xs, float2* part, int nsplit,
                        float2* y, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                       const MatvecChoice* ch = nullptr, const int* live = nullptr);
+                       const MatvecChoice* ch = nullptr, const int* live = nullptr, bool xs_ready = false);
 
 // K6: far field.
 // Time reversal (section 7): T = conj(F)^T F for C far-field matrices
@@ -410,8 +411,9 @@ void gm_update(const GmresDims& d, const RowChunk* chunks, const V* Vb, long lon
                int hstride, const int* skip, double sign, W* w, cudaStream_t s, int skipval = 1);
 // v = w * scale[s] for active systems, 0 otherwise
 template <typename Vin, typename Vout>
+// (rf, xs: also xs = rf .* v, the scaled input of the next FP32 product)
 void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const double* scale, const int* active,
-              Vout* v, cudaStream_t s);
+              Vout* v, cudaStream_t s, const float* rf = nullptr, float2* xs = nullptr);
 // ||w'||^2 estimate (written to wn2) and the re-orthogonalisation flags
 void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, double2* wn2,
                      const int* active, int* skip2, cudaStream_t s);
