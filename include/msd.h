@@ -188,7 +188,11 @@ msd_status msd_matvec_noalloc(msd_problem* pb, int R, int precision, const void*
 /* Section 5 / section 6.2: solve A rho = -U for R plane waves per
  * configuration with left-preconditioned restarted GMRES on the device
  * (x0 = 0), FP64 throughout (MSD_FP64) or FP32 inner sweeps with FP64
- * residuals and corrections (MSD_MIXED).
+ * residuals and corrections (MSD_MIXED).  A mixed sweep stops when its
+ * residual estimate falls below inner_tol times its starting FP64 residual,
+ * but not below opts->tol (relative), or below half of it when the sweep
+ * started within twice the tolerance; systems that have converged drop out
+ * of the remaining products and projections of the batch.
  *   betas_host  [C][R] incidence angles
  *   opts        may be NULL (defaults)
  *   rho_out     host or device, complex128 [N_tot][R]: the density
