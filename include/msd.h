@@ -91,6 +91,8 @@ typedef struct {
     double inner_tol;  /* MSD_MIXED: relative tolerance of each FP32 sweep  [5e-6]    */
     int precision;     /* MSD_FP64 (all FP64) or MSD_MIXED                  [FP64]    */
     int gen_mode;      /* MSD_GEN_*: generators stored in HBM or recomputed [auto]    */
+    double reorth;     /* second Gram-Schmidt pass when the first leaves less than
+                          this fraction of ||w||^2 (in (0, 1]; 1: always)  [0.5]     */
 } msd_opts;
 
 /* Per-system statistics (one per configuration and right-hand side). */

@@ -143,11 +143,12 @@ struct DotsFuse {
     double2* wn2 = nullptr;
     const int* active = nullptr;
     int* skip2 = nullptr;
+    double eta2 = 0.5;  // second pass when ||w'||^2 < eta2 ||w||^2
 };
 
 // ||w'||^2 = ||w||^2 - sum_{i <= j} |h_i|^2 and (skip2 != nullptr) the flag
 // of one system, reduced over the CTA (every thread calls it).
-__device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, int* skip2) {
+__device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, int* skip2, double eta2) {
     double acc = 0.0;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 v = __ldcg(h + i);
@@ -165,7 +166,7 @@ __device__ void reorth_flag_cta(const double2* h, int j, double2* wn2, int act, 
         const double before = __ldcg(h + j + 1).x;  // ||w||^2 before the projection
         const double after = before - ss;
         *wn2 = make_double2(after, 0.0);
-        if (skip2) *skip2 = !(act && after < 0.5 * before);
+        if (skip2) *skip2 = !(act && after < eta2 * before);
     }
 }
 
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_dots_warp(const RowChunk* __res
     __threadfence();
     for (int sy = 0; sy < fz.S; ++sy)
         reorth_flag_cta(fz.out + (long long)sy * fz.ostride, fz.j, fz.wn2 + (long long)sy * fz.ostride,
-                        fz.active ? fz.active[sy] : 1, fz.skip2 ? fz.skip2 + sy : nullptr);
+                        fz.active ? fz.active[sy] : 1, fz.skip2 ? fz.skip2 + sy : nullptr, fz.eta2);
     if (threadIdx.x == 0) *fz.cnt_all = 0;
 }
 
@@ -302,6 +303,7 @@ struct FinTail {
     double2* wn2 = nullptr;
     const int* active = nullptr;
     int* skip2 = nullptr;
+    double eta2 = 0.5;  // second pass when ||w'||^2 < eta2 ||w||^2
 };
 __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_chunk_off,
                            const double2* __restrict__ part, double2* __restrict__ out, int ostride, FinTail tail) {
@@ -336,7 +338,7 @@ __global__ void k_dots_fin(int C, int R, int nvv, const int* __restrict__ cfg_ch
     const int S = C * R;
     for (int sy = 0; sy < S; ++sy)
         reorth_flag_cta(out + (long long)sy * ostride, tail.j, tail.wn2 + (long long)sy * ostride,
-                        tail.active ? tail.active[sy] : 1, tail.skip2 ? tail.skip2 + sy : nullptr);
+                        tail.active ? tail.active[sy] : 1, tail.skip2 ? tail.skip2 + sy : nullptr, tail.eta2);
     if (threadIdx.x == 0) *tail.cnt = 0;
 }
 
@@ -433,7 +435,7 @@ __global__ void k_scale(const RowChunk* __restrict__ chunks, int R, const Vin* _
 // the norm itself.
 __global__ void k_reorth_flags(int S, const double2* __restrict__ h1, int hstride, int j,
                                double2* __restrict__ wn2, const int* __restrict__ active,
-                               int* __restrict__ skip2) {
+                               int* __restrict__ skip2, double eta2) {
     const int s = blockIdx.x;
     const double2* h = h1 + (long long)s * hstride;
     double acc = 0.0;
@@ -449,7 +451,7 @@ __global__ void k_reorth_flags(int S, const double2* __restrict__ h1, int hstrid
     const double before = h[j + 1].x;  // ||w||^2 before the projection
     const double after = before - ss;
     wn2[(long long)s * hstride] = make_double2(after, 0.0);
-    skip2[s] = !(active[s] && after < 0.5 * before);
+    skip2[s] = !(active[s] && after < eta2 * before);
 }
 
 // Start of a cycle: beta = ||r||; systems whose residual already meets
@@ -738,6 +740,7 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
             fz.wn2 = fuse->wn2;
             fz.active = fuse->active;
             fz.skip2 = fuse->skip2;
+            fz.eta2 = fuse->eta2;
         }
     }
     if (32 % d.R == 0) {
@@ -763,6 +766,7 @@ bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_of
         tail.wn2 = fuse->wn2;
         tail.active = fuse->active;
         tail.skip2 = fuse->skip2;
+        tail.eta2 = fuse->eta2;
     }
     k_dots_fin<<<blocks_for(tot * 32, 128), 128, 0, s>>>(d.C, d.R, nvv, cfg_chunk_off, part, out, ostride, tail);
     g_msd_launches += 2;
@@ -786,8 +790,8 @@ void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const do
 }
 
 void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, double2* wn2,
-                     const int* active, int* skip2, cudaStream_t s) {
-    k_reorth_flags<<<d.S, 128, 0, s>>>(d.S, h1, hstride, j, wn2, active, skip2);
+                     const int* active, int* skip2, cudaStream_t s, double eta2) {
+    k_reorth_flags<<<d.S, 128, 0, s>>>(d.S, h1, hstride, j, wn2, active, skip2, eta2);
     g_msd_launches += 1;
 }
 

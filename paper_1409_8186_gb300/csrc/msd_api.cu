@@ -1117,6 +1117,7 @@ struct SolveCtx {
     int *active, *kconv, *iters, *skip2, *flags;  // flags[0] any_active, flags[1] nonfinite
     int* cnt = nullptr;  // ncnt + 1 counters of the fused projection reductions (zero between launches)
     int ncnt = 0;
+    double eta2 = 0.5;  // second Gram-Schmidt pass when ||w'||^2 < eta2 ||w||^2
     int hstride;
     double2* part;  // [nchunk][m + 2][R] reduction partials
     bool adjoint = false;  // solve with (P^-1 A)^H
@@ -1216,11 +1217,12 @@ void arnoldi_cycle(SolveCtx& cx, V* Vb, V* w, bool fp64, int maxit_left, int* st
         fz1.wn2 = cx.wn2;
         fz1.active = cx.active;
         fz1.skip2 = cx.skip2;
+        fz1.eta2 = cx.eta2;
         const bool flags_done =
             gm_dots<V>(db, chb, cob, Vb, vstride, j + 1, 1, w, cx.active, cx.part, cx.h1, cx.hstride, s, 0, &fz1);
         gm_update<V, V>(d, ch, Vb, vstride, j + 1, cx.h1, cx.hstride, cx.active, -1.0, w, s, 0);
         // second projection only where the first removed more than half of ||w||^2
-        if (!flags_done) gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s);
+        if (!flags_done) gm_reorth_flags(d, cx.h1, cx.hstride, j, cx.wn2, cx.active, cx.skip2, s, cx.eta2);
         // its norm: ||w1 - V h2||^2 = ||w1||^2 - |h2|^2 (w1 measured by the
         // projection itself; h2 is small after the first pass, so no
         // cancellation), formed inside the fused kernel, else measured
@@ -1319,6 +1321,8 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     }
     if (o.max_refine <= 0) o.max_refine = 60;
     if (o.inner_tol <= 0) o.inner_tol = 5e-6;
+    if (o.reorth == 0) o.reorth = 0.5;
+    if (!(o.reorth > 0 && o.reorth <= 1)) fail(MSD_ERR_ARG, "msd_solve_planewaves: reorth outside (0, 1]");
     if (o.precision != MSD_FP64 && o.precision != MSD_MIXED) fail(MSD_ERR_ARG, "msd_solve_planewaves: precision");
     const bool mixed = o.precision == MSD_MIXED;
     cudaStream_t s = pb->stream;
@@ -1326,6 +1330,7 @@ msd_status solve_impl(msd_problem* pb, int R, const double* betas_host, const ms
     SolveCtx cx;
     cx.pb = pb;
     cx.m = o.restart;
+    cx.eta2 = o.reorth;
     cx.d.Ntot = pb->Ntot;
     cx.d.R = R;
     cx.d.C = pb->C;

@@ -400,6 +400,7 @@ struct GmDotsFuse {
     double2* wn2 = nullptr;
     const int* active = nullptr;
     int* skip2 = nullptr;
+    double eta2 = 0.5;  // re-orthogonalisation threshold (msd_opts.reorth)
 };
 template <typename V>
 bool gm_dots(const GmresDims& d, const RowChunk* chunks, const int* cfg_chunk_off, const V* Vb, long long vstride,
@@ -416,7 +417,7 @@ void gm_scale(const GmresDims& d, const RowChunk* chunks, const Vin* w, const do
               Vout* v, cudaStream_t s, const float* rf = nullptr, float2* xs = nullptr);
 // ||w'||^2 estimate (written to wn2) and the re-orthogonalisation flags
 void gm_reorth_flags(const GmresDims& d, const double2* h1, int hstride, int j, double2* wn2,
-                     const int* active, int* skip2, cudaStream_t s);
+                     const int* active, int* skip2, cudaStream_t s, double eta2 = 0.5);
 void gm_start(const GmresDims& d, const double2* rr, int hstride, const double* tol_abs, double* beta,
               double* vscale, double2* g, int* active, int* kconv, int* any_active, cudaStream_t s);
 void gm_givens(const GmresDims& d, int j, const double2* h1, const double2* h2, int hstride, const double2* wn2a,

@@ -43,7 +43,7 @@ class MsdError(RuntimeError):
 class msd_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("precision", ctypes.c_int), ("gen_mode", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("gen_mode", ctypes.c_int), ("reorth", ctypes.c_double)]
 
 
 class msd_stats(ctypes.Structure):
@@ -496,11 +496,11 @@ class Problem:
         msd_set_generator_mode(self.handle, mode, chunk_bytes)
 
     def solve(self, betas, tol=1e-10, restart=0, maxit=3000, precision=MSD_FP64, max_refine=0,
-              inner_tol=0.0, out=None, gen_mode=MSD_GEN_AUTO) -> SolveResult:
+              inner_tol=0.0, out=None, gen_mode=MSD_GEN_AUTO, reorth=0.0) -> SolveResult:
         import torch
         b = self._betas(betas)
         R = b.shape[1]
-        o = msd_opts(tol, restart, maxit, max_refine, inner_tol, precision, gen_mode)
+        o = msd_opts(tol, restart, maxit, max_refine, inner_tol, precision, gen_mode, reorth)
         rho = torch.empty((self.ntot, R), dtype=torch.complex128, device="cuda") if out is None else out
         stats = (msd_stats * (self.C * R))()
         st = msd_solve_planewaves(self.handle, R, b, o, rho, stats)
