@@ -8,7 +8,8 @@
 //
 // Orthogonalisation is classical Gram-Schmidt with one selective
 // re-orthogonalisation pass (Daniel-Gragg-Kaufman-Stewart criterion: repeat
-// the projection when it removed more than half of ||w||^2).  Per-thread
+// the projection when it left less than a fraction eta2 of ||w||^2, by
+// default one half; the solver option reorth sets eta2).  Per-thread
 // sums of dot products and updates run in the storage precision of the
 // basis (FP32 for the inner sweeps of a mixed solve, whose FP64 pipe would
 // otherwise bound them) and cross-thread reductions in FP64.  Vectors are
@@ -20,8 +21,9 @@
 // The Givens rotations of a new Hessenberg column form the first-order
 // linear recurrence z_{i+1} = -conj(s_i) z_i + c_i h_{i+1} (z_0 = h_0,
 // rotated entry i = c_i z_i + s_i h_{i+1}); it is evaluated with a
-// parallel scan of affine maps over one CTA per system, so a step costs
-// O(j / threads + log threads) instead of a j-long dependency chain.
+// parallel scan of affine maps over one CTA per system (warp shuffles, then
+// across warps), so a step costs O(j / threads + log threads) instead of a
+// j-long dependency chain.
 #include "msd_internal.cuh"
 
 namespace {
